@@ -1,0 +1,431 @@
+#!/usr/bin/env python
+"""Benchmark of the KK beamforming hot path on GB300.
+
+One step = one frame through the whole path, inputs resident in HBM: the
+far-field decomposition (analytic FFT, per-bin shear contraction, inverse
+FFT) and KK image formation with coherent intensity, for the 128-element,
+75-transmit, 2048-sample int16 frame on a 512 x 512 grid with the full
+75 x 128 pair set (9600 pairs), FP32.  Each rank processes its own frames
+(frames are independent: weak scaling, no collective on the data path).
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
+oracle on bounded samples of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOAD = "L128_N75_T2048_i16_grid512x512_pairs75x128"
+METRIC = "KK frames/s"
+UNIT = "frames/s"
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--quick", action="store_true", help="skip the side measurements")
+    return ap.parse_args()
+
+
+def _dist():
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    elif torch.cuda.is_available():
+        torch.cuda.set_device(local)
+    return rank, world, local
+
+
+def _barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def _max_over_ranks(v: float, world: int) -> float:
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return d, "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def _traffic(kernel: str, source: str):
+    """Per-launch DRAM bytes recorded from an ncu capture of the current source
+    (profiles/traffic.txt: kernel sha256(source) bytes); None when stale."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    try:
+        sha = hashlib.sha256(open(source, "rb").read()).hexdigest()[:16]
+        for ln in open(path):
+            parts = ln.split()
+            if len(parts) >= 3 and parts[0] == kernel and parts[1] == sha:
+                return float(parts[2])
+    except Exception:
+        pass
+    return None
+
+
+def _workload(rank: int):
+    import kksynth
+    return kksynth.workload_large(seed=2000 + rank)
+
+
+def _full_pairs(w):
+    import numpy as np
+    rx = np.linspace(-w.theta_max_deg, w.theta_max_deg, 128) * np.pi / 180.0
+    pairs = np.array([(i, o) for i in range(w.n_tx) for o in range(128)], dtype=np.int32)
+    return rx, pairs
+
+
+def _vernier_pairs(w, kb):
+    import numpy as np
+    sub = [2 + 10 * a for a in range(8)]           # 8 transmits at stride 10 about the centre
+    dth = (w.tx_angles[sub[-1]] - w.tx_angles[sub[0]]) / 7
+    rx = kb.kk_scheme_angles(kb.KK_SCHEME_VERNIER, 8, dth, 16)
+    pairs = np.array([(i, o) for i in sub for o in range(16)], dtype=np.int32)
+    return rx, pairs
+
+
+def _time_loop(fn, reps, flush=None):
+    """Mean ms of fn() over reps, CUDA events on the current stream, L2 flushed
+    before each rep outside the events."""
+    import torch
+    evs = []
+    for _ in range(reps):
+        if flush is not None:
+            flush()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        fn()
+        b.record()
+        evs.append((a, b))
+    torch.cuda.synchronize()
+    return sum(a.elapsed_time(b) for a, b in evs) / reps
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    rank, world, local = _dist()
+    from paper_2603_22496_gb300 import build as kbuild
+    if rank == 0:
+        kbuild.build()
+    _barrier(world)
+    import paper_2603_22496_gb300 as kb
+    kb.load()
+    dev = torch.device(f"cuda:{local}")
+    peaks, peak_src = _peaks()
+    props = torch.cuda.get_device_properties(dev)
+    n_sm = props.multi_processor_count
+
+    w = _workload(rank)
+    rx, pairs = _full_pairs(w)
+    plan = kb.Plan(w.elem_x, w.tx_angles, w.grid, w.c, w.fs, w.n_samples, kb.KK_RF_I16,
+                   rx_angles=rx, pairs=pairs, compound=kb.KK_COMPOUND_COHERENT, device=local)
+    info = plan.info
+    d_rf = torch.from_numpy(w.rf).to(dev)
+    ws, rt, B, I = plan.empty_workspace(), plan.empty_rf_theta(), plan.empty_image(), plan.empty_intensity()
+    flush_buf = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+
+    def flush():
+        flush_buf.fill_(1)
+
+    def step():
+        plan.decompose(d_rf, rt, ws)
+        plan.beamform(rt, B, I, ws)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    _barrier(world)
+    torch.cuda.synchronize()
+    evs = []
+    for _ in range(args.steps):
+        flush()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        step()
+        b.record()
+        evs.append((a, b))
+    torch.cuda.synchronize()
+    _barrier(world)
+    clk = clocks.stop()
+    ms_total = sum(a.elapsed_time(b) for a, b in evs)
+    ms_total = _max_over_ranks(ms_total, world)
+    ms_step = ms_total / args.steps
+    frames = args.steps * world
+    value = frames / (ms_total / 1e3)
+    launches = args.steps * (info.launches_decompose + info.launches_beamform)
+
+    P, T, npix = info.n_pairs, info.n_samples, info.nx * info.nz
+    out = {"metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": round(ms_step, 4),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+           "data": "synthetic (seeded phantom: 20 wires, 3 cysts, 50k speckle; int16 at 30 dB SNR)",
+           "config": {"workload": WORKLOAD, "elements": info.n_elem, "transmits": info.n_tx,
+                      "samples": T, "rf": "int16", "grid": [info.nx, info.nz], "pairs": P,
+                      "receive_angles": info.n_rx_used, "compound": "coherent",
+                      "form": "plain FP32 (decomposition on CUDA cores)",
+                      "l2": "flushed between steps (256 MB write outside the timed events)",
+                      "parallelism": f"frames per rank (x{world})"},
+           "gpu_launches": launches, "clocks": clk}
+
+    if rank == 0 and not args.quick:
+        side = {}
+        reps = 10
+        F = info.n_bins
+        X = torch.empty((F, info.n_tx_used, info.n_elem, 2), device=dev)
+        Y = torch.empty((F, info.n_tx_used, info.n_rx_used, 2), device=dev)
+        ms_spec = _time_loop(lambda: plan.spectrum(d_rf, X), reps, flush)
+        ms_shear = _time_loop(lambda: plan.shear(X, Y), reps, flush)
+        ms_inv = _time_loop(lambda: plan.inverse(Y, rt), reps, flush)
+        ms_bf = _time_loop(lambda: plan.beamform(rt, B, I, ws), reps, flush)
+        pp = float(P) * npix
+        side["stages_ms"] = {"spectrum": round(ms_spec, 4), "shear_contraction_f32": round(ms_shear, 4),
+                             "inverse": round(ms_inv, 4), "kk_image": round(ms_bf, 4)}
+        side["gpixel_pairs_per_s"] = round(pp / (ms_bf / 1e3) / 1e9, 2)
+        # roofline of the dominant kernel: the KK gather, bound by the SM's
+        # shared-memory pipe: one 16-byte (y, dy) load per pixel-pair at
+        # 128 B/clk/SM -> 8 pixel-pairs per clock per SM
+        sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+        peak_pp = 8.0 * n_sm * sm_max * 1e6 / 1e9
+        ach_pp = pp / (ms_bf / 1e3) / 1e9
+        hbm_bytes = P * T * 8 + npix * 8 + npix * 4
+        out["roofline"] = {
+            "kernel": "k_kk_gather (+ slice reduce)", "bound": "alu",
+            "achieved": round(ach_pp, 2), "peak": round(peak_pp, 1), "unit": "Gpixel-pairs/s",
+            "frac": round(ach_pp / peak_pp, 4),
+            "peak_basis": f"8 pixel-pairs/clk/SM (shared-memory 128 B/clk / 16 B per lerp) x {n_sm} SMs x {sm_max:.0f} MHz ({peak_src} sm_max_mhz)",
+            "traffic": _traffic("k_kk_gather", os.path.join(ROOT, "paper_2603_22496_gb300", "csrc", "kk_beamform.cu")),
+            "algorithmic_hbm_bytes": hbm_bytes,
+            "hbm_gbs": round(hbm_bytes / (ms_bf / 1e3) / 1e9, 1),
+            "hbm_frac_of_" + peak_src: round(hbm_bytes / (ms_bf / 1e3) / 1e9 / float(peaks["hbm_gbs"]), 4)}
+        # decomposition contraction (FP32 on CUDA cores): ALU roofline
+        flops = 8.0 * F * info.n_rx_used * info.n_elem * info.n_tx_used
+        fp32_peak = 2.0 * 128 * n_sm * sm_max * 1e6 / 1e12
+        side["shear_contraction"] = {"tflops": round(flops / (ms_shear / 1e3) / 1e12, 2),
+                                     "fp32_peak_tflops": round(fp32_peak, 1),
+                                     "frac": round(flops / (ms_shear / 1e3) / 1e12 / fp32_peak, 3)}
+        spec_bytes = info.rf_bytes + F * info.n_tx_used * info.n_elem * 8
+        inv_bytes = F * info.n_tx_used * info.n_rx_used * 8 + P * T * 8
+        side["spectrum_hbm_gbs"] = round(spec_bytes / (ms_spec / 1e3) / 1e9, 1)
+        side["inverse_hbm_gbs"] = round(inv_bytes / (ms_inv / 1e3) / 1e9, 1)
+        # vernier 8 x 16 pair subset (128 pairs) and DAS on the same frame
+        vrx, vpairs = _vernier_pairs(w, kb)
+        vplan = kb.Plan(w.elem_x, w.tx_angles, w.grid, w.c, w.fs, w.n_samples, kb.KK_RF_I16,
+                        rx_angles=vrx, pairs=vpairs, compound=kb.KK_COMPOUND_COHERENT, device=local)
+        vws, vrt, vB, vI = vplan.empty_workspace(), vplan.empty_rf_theta(), vplan.empty_image(), vplan.empty_intensity()
+        ms_v = _time_loop(lambda: (vplan.decompose(d_rf, vrt, vws), vplan.beamform(vrt, vB, vI, vws)), reps, flush)
+        side["kk_vernier_8x16"] = {"frames_per_s": round(1e3 / ms_v, 1), "pairs": 128,
+                                   "compression": round(vplan.info.compression_factor, 2)}
+        dplan = kb.Plan(w.elem_x, w.tx_angles, w.grid, w.c, w.fs, w.n_samples, kb.KK_RF_I16,
+                        das=True, device=local)
+        dws, dB, dI = dplan.empty_workspace(), dplan.empty_image(), dplan.empty_intensity()
+        ms_d = _time_loop(lambda: dplan.das(d_rf, dB, dI, dws), 5, flush)
+        side["das_75x128"] = {"frames_per_s": round(1e3 / ms_d, 1),
+                              "gpixel_pairs_per_s": round(75 * 128 * npix / (ms_d / 1e3) / 1e9, 2)}
+        out["breakdown"] = side
+
+        # end to end through the C ABI from pinned host memory
+        h_rf = torch.from_numpy(w.rf).pin_memory()
+        h_B = torch.empty((1, info.nz, info.nx, 2), dtype=torch.float32).pin_memory()
+        h_I = torch.empty((info.nz, info.nx), dtype=torch.float32).pin_memory()
+        scratch = torch.empty(plan.scratch_bytes(), dtype=torch.uint8, device=dev)
+        for _ in range(3):
+            plan.run_host(h_rf, h_B, h_I, scratch)
+        torch.cuda.synchronize()
+        k_e2e = max(5, args.steps // 2)
+        t0 = time.perf_counter()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(k_e2e):
+            plan.run_host(h_rf, h_B, h_I, scratch)
+        b.record()
+        torch.cuda.synchronize()
+        ms_e2e = a.elapsed_time(b) / k_e2e
+        out["e2e"] = {"value": round(1e3 / ms_e2e, 3), "unit": UNIT,
+                      "h2d_bytes_per_step": int(info.rf_bytes),
+                      "d2h_bytes_per_step": int(info.image_bytes + info.intensity_bytes),
+                      "wall_ms_per_step": round((time.perf_counter() - t0) * 1e3 / k_e2e, 3)}
+        if world == 1 and not args.no_cpu_baseline:
+            out["cpu_baseline"] = cpu_baseline(w, rx, pairs)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def _oracle_frame_seconds(w, rx, pairs, rx_keep, rows):
+    """Oracle time for the decomposition of the pairs whose receive angle is in
+    rx_keep (every decomposition cost but the small analytic FFT scales with
+    the number of receive angles) and image formation of `rows` grid rows over
+    all pairs, scaled to one full frame."""
+    import numpy as np
+    from oracle import kk, schemes
+    ps = schemes.PairSet(w.tx_angles, rx, pairs[:, 0].astype(np.int64),
+                         pairs[:, 1].astype(np.int64), np.zeros(pairs.shape[0], np.int64), 1)
+    keep = np.isin(ps.rx_index, rx_keep)
+    sub = schemes.PairSet(ps.tx_angles, ps.rx_angles, ps.tx_index[keep], ps.rx_index[keep],
+                          ps.group[keep], 1)
+    t0 = time.perf_counter()
+    kk.analytic_spectrum(w.rf)                         # the part that does not scale
+    t_fft = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    y = kk.decompose(w.rf, w.elem_x, sub, w.fs, w.c)
+    t_dec = time.perf_counter() - t0
+    nx, nz = w.grid[0], w.grid[1]
+    pix = np.array([(ix, iz) for iz in range(rows) for ix in range(nx)])
+    yy = np.zeros((ps.n_pairs, w.n_samples), np.complex128)
+    yy[keep] = y
+    t0 = time.perf_counter()
+    kk.kk_beamform(yy, w.elem_x, ps, w.grid, w.fs, w.c, pixels=pix)
+    t_bf = time.perf_counter() - t0
+    frac_dec = keep.sum() / ps.n_pairs
+    t_dec_frame = t_fft + max(t_dec - t_fft, 0.0) / frac_dec
+    return t_dec_frame + t_bf * (nz / rows), t_dec, t_bf
+
+
+def cpu_baseline(w, rx, pairs):
+    import numpy as np
+    cores = os.cpu_count()
+    rx_keep = np.arange(128)                          # the whole decomposition
+    rows = 32
+    sec, t_dec, t_bf = _oracle_frame_seconds(w, rx, pairs, rx_keep, rows)
+    return {"value": round(1.0 / sec, 5), "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"FP64 oracle: decomposition of all 9600 pairs "
+                      f"({t_dec:.2f} s) and image formation of {rows}/512 rows over all 9600 pairs "
+                      f"({t_bf:.2f} s), scaled to one frame"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import numpy as np
+    w = _workload(0)
+    rx, pairs = _full_pairs(w)
+    rx_keep = np.arange(0, 128, 16)                   # 8 of 128 receive angles
+    rows = 8
+    for _ in range(max(args.warmup, 1)):
+        _oracle_frame_seconds(w, rx, pairs, rx_keep, rows)
+    secs = []
+    for _ in range(args.steps):
+        s, _, _ = _oracle_frame_seconds(w, rx, pairs, rx_keep, rows)
+        secs.append(s)
+    tot = sum(secs)
+    value = args.steps / tot
+    cores = os.cpu_count()
+    sample = ("FP64 oracle per step: decomposition of the 600 pairs of 8/128 receive angles and image "
+              "formation of 8/512 rows over all 9600 pairs, scaled to one frame")
+    out = {"impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": UNIT,
+           "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": round(1e3 * tot / args.steps, 2), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "pairs": 9600, "grid": [512, 512]},
+           "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": cores,
+                            "kind": "oracle", "sample": sample},
+           "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    a = _args()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)

@@ -1,0 +1,237 @@
+/*
+ * kkbeam.h -- C ABI of the GB300 (sm_103a) KK beamforming library.
+ *
+ * KK beamforming (Khetan & Mertz, "Far-field compressive ultrasound
+ * beamforming") forms a plane-wave-compounded ultrasound image in two steps:
+ *   1. a far-field decomposition of each transmit angle's channel data into
+ *      virtual receive plane waves, Eq. (compression), applied through the
+ *      Fourier shift theorem on the analytic spectrum (Section II-F);
+ *   2. image formation, Eq. (KK): every pixel interpolates each virtual
+ *      plane wave's record at its (transmit + receive) delay and sums over the
+ *      (transmit, receive) pairs of the chosen k-space sampling scheme
+ *      (Eq. (uniform), Eq. (confocal)), with optional coherent / incoherent
+ *      compounding of J groups (Eqs. (coherent), (incoherent)).
+ * A delay-and-sum reference, Eq. (DAS), runs on the same plan type.
+ *
+ * Conventions (all calls):
+ *  - Units: metres, seconds, radians.  Element l sits at (elem_x[l], 0).
+ *    Image x is lateral, z is depth.  Sample n of a record is at time n/fs;
+ *    a transmit plane wave passes the origin at t = 0.
+ *  - Arrays are row-major, last index fastest.  Complex values are
+ *    interleaved (re, im) float32 pairs ("cfloat", 8 bytes).
+ *  - Ownership: the caller owns every buffer passed in (device buffers may
+ *    come from any allocator).  A plan owns its look-up tables, which are
+ *    immutable after creation; a plan may be used from several streams at
+ *    once provided each stream has its own workspace.
+ *  - Execution: every call taking a stream only enqueues work on that
+ *    stream (a cudaStream_t passed as void*, NULL = legacy default stream)
+ *    and returns without synchronising.  Plan creation synchronises.
+ *  - Errors: no call throws.  Each returns a kk_status; on failure
+ *    kk_last_error() gives a message (thread-local).  A failed call leaves
+ *    the output buffers in an unspecified state and the plan unchanged.
+ *  - Every enqueue call checks for launch errors before returning
+ *    (KK_ERR_CUDA); errors of the asynchronous work surface at the caller's
+ *    next synchronisation.
+ */
+#ifndef KKBEAM_H
+#define KKBEAM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum kk_status {
+  KK_OK = 0,
+  KK_ERR_INVALID_ARG = 1, /* null pointer, size out of range, bad index */
+  KK_ERR_UNSUPPORTED = 2, /* valid but not implemented (e.g. an FFT length) */
+  KK_ERR_CUDA = 3,        /* a CUDA runtime call or launch failed */
+  KK_ERR_OOM = 4,         /* device allocation failed at plan time */
+  KK_ERR_TIMEOUT = 5      /* a bounded device-side wait gave up */
+} kk_status;
+
+typedef enum kk_rf_dtype { KK_RF_I16 = 0, KK_RF_F32 = 1 } kk_rf_dtype;
+
+/* Operand precision of the decomposition contraction (step 1).  FFTs,
+ * interpolation and summation always run in FP32. */
+typedef enum kk_precision {
+  KK_PREC_F32 = 0,
+  KK_PREC_BF16 = 1,
+  KK_PREC_F16 = 2,
+  KK_PREC_F8E4M3 = 3
+} kk_precision;
+
+typedef enum kk_compound {
+  KK_COMPOUND_NONE = 0,       /* I is not written */
+  KK_COMPOUND_COHERENT = 1,   /* I = |sum_j B_j|^2, Eq. (coherent) */
+  KK_COMPOUND_INCOHERENT = 2  /* I = sum_j |B_j|^2, Eq. (incoherent) */
+} kk_compound;
+
+typedef enum kk_scheme {
+  KK_SCHEME_SAME = 0,     /* theta_o = theta_i (Section II-C, redundant) */
+  KK_SCHEME_VERNIER = 1,  /* theta_o = 2 o dtheta_i / M (Section II-C) */
+  KK_SCHEME_SHIFTED = 2,  /* Eq. (uniform) with shift j */
+  KK_SCHEME_CONFOCAL = 3  /* Eq. (confocal) */
+} kk_scheme;
+
+/* Pixel (ix, iz) sits at (x0 + ix*dx, z0 + iz*dz).  dz > 0, z0 >= 0. */
+typedef struct kk_grid {
+  int32_t nx, nz;
+  double x0, dx, z0, dz;
+} kk_grid;
+
+/* Everything a plan needs.  Pointers are host pointers, read during plan
+ * creation only. */
+typedef struct kk_plan_desc {
+  int32_t n_elem;             /* L >= 1 */
+  const double *elem_x;       /* [L] lateral element positions */
+  int32_t n_tx;               /* N >= 1: acquired transmit angles (rows of rf) */
+  const double *tx_angles;    /* [N], |angle| < 80 deg */
+  int32_t n_rx;               /* number of receive angles (KK only) */
+  const double *rx_angles;    /* [n_rx], |angle| < 80 deg (KK only) */
+  int32_t n_pairs;            /* P >= 1 (KK only) */
+  const int32_t *pairs;       /* [P][2] = (tx index, rx index) (KK only) */
+  const int32_t *group_of_pair; /* [P] in [0, n_groups); NULL = all 0 */
+  int32_t n_groups;           /* J >= 1 */
+  int32_t compound;           /* kk_compound */
+  kk_grid grid;
+  double c;                   /* speed of sound > 0 */
+  double fs;                  /* sampling rate > 0 */
+  int32_t n_samples;          /* T: even, T/2 in {128,256,512,768,1024,1536,2048} */
+  int32_t rf_dtype;           /* kk_rf_dtype */
+  int32_t precision;          /* kk_precision (KK only; DAS is FP32) */
+  int32_t device;             /* CUDA device ordinal the plan lives on */
+} kk_plan_desc;
+
+typedef struct kk_plan kk_plan;
+
+/* Sizes a caller needs to allocate buffers for a plan. */
+typedef struct kk_plan_info {
+  int32_t n_elem, n_tx, n_samples, n_bins; /* L, N, T, F = T/2 */
+  int32_t n_tx_used, n_rx_used;            /* transmits / receive angles in use */
+  int32_t n_pairs, n_groups;               /* P, J */
+  int32_t nx, nz;
+  int32_t is_das;
+  size_t workspace_bytes;                  /* for kk_decompose/kk_beamform/das_beamform */
+  size_t rf_bytes;                         /* N*L*T*sizeof(sample) */
+  size_t rf_theta_bytes;                   /* P*T*8 */
+  size_t image_bytes;                      /* J*nz*nx*8 (B) */
+  size_t intensity_bytes;                  /* nz*nx*4 (I) */
+  double compression_factor;               /* L / (number of receive angles in use) */
+  int32_t launches_decompose;              /* kernels one kk_decompose enqueues */
+  int32_t launches_beamform;               /* kernels one kk_beamform / das_beamform enqueues */
+} kk_plan_info;
+
+/*
+ * KK plan.  Validates the description, sorts pairs by group, and builds on
+ * the device (FP64 on the host, then stored as integer / FP32 tables):
+ *   - shear phases phi[o][l] = frac(fs * delta_l(theta_o) / T) in 0.64 fixed
+ *     point, delta_l(theta_o) = (x_ref - u_l) sin(theta_o) / c with x_ref the
+ *     array end that makes the shear a non-negative advance (Eq. (compression));
+ *   - per-pair affine delay coefficients s(ix, iz) = A ix + B iz + C in 32.32
+ *     fixed point, s = fs [x sin_i + z cos_i + (x - x_ref) sin_o + z cos_o] / c
+ *     (Eq. (KK) with the time origin of the sheared record at x_ref);
+ *   - FFT twiddles.
+ * Returns KK_ERR_INVALID_ARG / KK_ERR_UNSUPPORTED / KK_ERR_OOM / KK_ERR_CUDA.
+ * On success *out owns device memory on d->device until kk_plan_destroy.
+ */
+kk_status kk_plan_create(kk_plan **out, const kk_plan_desc *d);
+
+/* DAS plan (Eq. (DAS)): receive/pair/group/precision fields are ignored,
+ * every transmit of rf is used, J = 1. */
+kk_status das_plan_create(kk_plan **out, const kk_plan_desc *d);
+
+/* Frees the plan's device tables.  NULL is a no-op.  The caller must make
+ * sure no work using the plan is still in flight. */
+void kk_plan_destroy(kk_plan *p);
+
+kk_status kk_plan_get_info(const kk_plan *p, kk_plan_info *info);
+
+/* Workspace bytes needed by kk_decompose / kk_beamform / das_beamform. */
+kk_status kk_plan_workspace_size(const kk_plan *p, size_t *bytes);
+
+/*
+ * Step 1, the far-field decomposition (Eq. (compression), Section II-F):
+ *   X[k][c]  = h_k sum_t rf[i][l][t] exp(-2 pi i k t / T)   (c = iu*L + l)
+ *   Y[k][q]  = sum_l X[k][iu][l] exp(+2 pi i k phi[o][l])    (q = iu*Mu + ou)
+ *   y[p][t]  = (1/T) sum_{k<T/2} Y[k][q(p)] exp(+2 pi i k t / T)
+ * h_0 = 1, h_k = 2 (negative frequencies and the Nyquist bin dropped).
+ *
+ * d_rf        device [N][L][T] int16 or float32 (plan's rf_dtype)
+ * d_rf_theta  device [P][T] cfloat, row p = pair p in the caller's order
+ * d_workspace device, >= workspace_bytes, 256-byte aligned
+ */
+kk_status kk_decompose(const kk_plan *p, const void *d_rf, void *d_rf_theta,
+                       void *d_workspace, void *stream);
+
+/* Stage calls of kk_decompose, for inspection and testing (FP32 plans only).
+ * d_X: [F][Nu][L] cfloat (h_k applied).  d_Y: [F][Nu][Mu] cfloat. */
+kk_status kk_spectrum(const kk_plan *p, const void *d_rf, void *d_X, void *stream);
+kk_status kk_shear(const kk_plan *p, const void *d_X, void *d_Y, void *stream);
+kk_status kk_inverse(const kk_plan *p, const void *d_Y, void *d_rf_theta,
+                     void *stream);
+
+/*
+ * Step 2, image formation (Eq. (KK)) and compounding:
+ *   B_j(ix, iz) = sum_{p in group j} lerp(y_p, s_p(ix, iz))
+ * lerp(y, s): k = floor(s), f = s - k, (1-f) y[k] + f y[k+1] when
+ * 0 <= k and k+1 <= T-1, else 0.
+ * d_rf_theta  device [P][T] cfloat (as written by kk_decompose)
+ * d_B         device [J][nz][nx] cfloat (always written)
+ * d_I         device [nz][nx] float, written when the plan's compound mode is
+ *             COHERENT or INCOHERENT; may be NULL otherwise
+ * d_workspace device, >= workspace_bytes
+ */
+kk_status kk_beamform(const kk_plan *p, const void *d_rf_theta, void *d_B,
+                      float *d_I, void *d_workspace, void *stream);
+
+/*
+ * DAS reference path (Eq. (DAS)): analytic signal of every channel (same FFT,
+ * mask and inverse as step 1, no shear), then
+ *   B(ix, iz) = sum_{i,l} lerp(y_il, fs (tau_in + |r - (u_l, 0)| / c))
+ * d_rf [N][L][T], d_B [nz][nx] cfloat, d_I [nz][nx] float (|B|^2) or NULL.
+ */
+kk_status das_beamform(const kk_plan *p, const void *d_rf, void *d_B,
+                       float *d_I, void *d_workspace, void *stream);
+
+/*
+ * End to end from host memory: copies h_rf to the device, runs
+ * kk_decompose + kk_beamform (or das_beamform for a DAS plan), copies B and
+ * I back.  All on `stream`; returns after enqueueing (the caller
+ * synchronises before reading h_B / h_I).  Host buffers should be pinned
+ * for the copies to be asynchronous.
+ * d_scratch   device, >= kk_run_host_scratch_size bytes (holds rf, rf_theta,
+ *             B, I and the workspace)
+ * h_I may be NULL.
+ */
+kk_status kk_run_host_scratch_size(const kk_plan *p, size_t *bytes);
+kk_status kk_run_host(const kk_plan *p, const void *h_rf, void *h_B, float *h_I,
+                      void *d_scratch, void *stream);
+
+/*
+ * Receive angles of one scheme (pure host, FP64):
+ *   o = -(M-1)/2 .. (M-1)/2 in unit steps (the paper's -floor(M/2)..floor(M/2)
+ *   for odd M; half-integers for even M), dtheta = transmit spacing,
+ *   SAME:     out[m] = tx_angles_sub[m] (requires M == n_tx; uses `tx`)
+ *   VERNIER:  2 o dtheta / M
+ *   SHIFTED:  sgn(o) dtheta (2|o|/M + j)                Eq. (uniform)
+ *   CONFOCAL: sgn(o) dtheta (2|o|/M + mod(floor|o|, floor(n_tx/2)))  Eq. (confocal)
+ * tx: [n_tx] transmit angles of the subset in use (SAME only; may be NULL
+ * otherwise).  out_rx: [M].
+ */
+kk_status kk_scheme_angles(int32_t kind, int32_t n_tx, const double *tx,
+                           double dtheta, int32_t M, double j, double *out_rx);
+
+/* Thread-local message of the last failed call on this thread ("" if none). */
+const char *kk_last_error(void);
+
+/* Library version string. */
+const char *kk_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KKBEAM_H */

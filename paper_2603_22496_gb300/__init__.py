@@ -1,0 +1,324 @@
+"""KK beamforming on GB300: thin Python binding of the C ABI in include/kkbeam.h.
+
+Every step of the path runs in the CUDA library ``_build/libkkbeam.so``;
+this module only marshals arguments (torch tensors -> device pointers,
+numpy arrays -> host pointers, torch streams -> cudaStream_t).  It fails
+loudly when the library has not been built; there is no CPU fallback.
+
+The functions carry the ABI's names (``kk_plan_create``, ``kk_decompose``,
+``kk_beamform``, ``das_plan_create``, ``das_beamform``, ``kk_scheme_angles``,
+...).  ``Plan`` is a small owner of a plan handle with the same calls as
+methods.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+KK_OK, KK_ERR_INVALID_ARG, KK_ERR_UNSUPPORTED, KK_ERR_CUDA, KK_ERR_OOM, KK_ERR_TIMEOUT = range(6)
+KK_RF_I16, KK_RF_F32 = 0, 1
+KK_PREC_F32, KK_PREC_BF16, KK_PREC_F16, KK_PREC_F8E4M3 = 0, 1, 2, 3
+KK_COMPOUND_NONE, KK_COMPOUND_COHERENT, KK_COMPOUND_INCOHERENT = 0, 1, 2
+KK_SCHEME_SAME, KK_SCHEME_VERNIER, KK_SCHEME_SHIFTED, KK_SCHEME_CONFOCAL = 0, 1, 2, 3
+
+_STATUS = {0: "KK_OK", 1: "KK_ERR_INVALID_ARG", 2: "KK_ERR_UNSUPPORTED", 3: "KK_ERR_CUDA",
+           4: "KK_ERR_OOM", 5: "KK_ERR_TIMEOUT"}
+
+# every symbol declared in include/kkbeam.h
+EXPORTS = ["kk_plan_create", "das_plan_create", "kk_plan_destroy", "kk_plan_get_info",
+           "kk_plan_workspace_size", "kk_decompose", "kk_spectrum", "kk_shear", "kk_inverse",
+           "kk_beamform", "das_beamform", "kk_run_host_scratch_size", "kk_run_host",
+           "kk_scheme_angles", "kk_last_error", "kk_version"]
+
+
+class KKError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class kk_grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("nz", ctypes.c_int32), ("x0", ctypes.c_double),
+                ("dx", ctypes.c_double), ("z0", ctypes.c_double), ("dz", ctypes.c_double)]
+
+
+_dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.POINTER(ctypes.c_int32)
+
+
+class kk_plan_desc(ctypes.Structure):
+    _fields_ = [("n_elem", ctypes.c_int32), ("elem_x", _dp),
+                ("n_tx", ctypes.c_int32), ("tx_angles", _dp),
+                ("n_rx", ctypes.c_int32), ("rx_angles", _dp),
+                ("n_pairs", ctypes.c_int32), ("pairs", _ip),
+                ("group_of_pair", _ip), ("n_groups", ctypes.c_int32),
+                ("compound", ctypes.c_int32), ("grid", kk_grid),
+                ("c", ctypes.c_double), ("fs", ctypes.c_double),
+                ("n_samples", ctypes.c_int32), ("rf_dtype", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("device", ctypes.c_int32)]
+
+
+class kk_plan_info(ctypes.Structure):
+    _fields_ = [("n_elem", ctypes.c_int32), ("n_tx", ctypes.c_int32),
+                ("n_samples", ctypes.c_int32), ("n_bins", ctypes.c_int32),
+                ("n_tx_used", ctypes.c_int32), ("n_rx_used", ctypes.c_int32),
+                ("n_pairs", ctypes.c_int32), ("n_groups", ctypes.c_int32),
+                ("nx", ctypes.c_int32), ("nz", ctypes.c_int32), ("is_das", ctypes.c_int32),
+                ("workspace_bytes", ctypes.c_size_t), ("rf_bytes", ctypes.c_size_t),
+                ("rf_theta_bytes", ctypes.c_size_t), ("image_bytes", ctypes.c_size_t),
+                ("intensity_bytes", ctypes.c_size_t), ("compression_factor", ctypes.c_double),
+                ("launches_decompose", ctypes.c_int32), ("launches_beamform", ctypes.c_int32)]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False):
+    """Load the CUDA library; raise if it is missing (never falls back)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise RuntimeError(f"KK CUDA library not built ({path}); run "
+                               "`python -m paper_2603_22496_gb300.build` or __graft_entry__.build()")
+        _build.build()
+    lib = ctypes.CDLL(path)
+    vp, st = ctypes.c_void_p, ctypes.c_int
+    pp = ctypes.POINTER(ctypes.c_void_p)
+    sig = {
+        "kk_plan_create": ([pp, ctypes.POINTER(kk_plan_desc)], st),
+        "das_plan_create": ([pp, ctypes.POINTER(kk_plan_desc)], st),
+        "kk_plan_destroy": ([vp], None),
+        "kk_plan_get_info": ([vp, ctypes.POINTER(kk_plan_info)], st),
+        "kk_plan_workspace_size": ([vp, ctypes.POINTER(ctypes.c_size_t)], st),
+        "kk_decompose": ([vp, vp, vp, vp, vp], st),
+        "kk_spectrum": ([vp, vp, vp, vp], st),
+        "kk_shear": ([vp, vp, vp, vp], st),
+        "kk_inverse": ([vp, vp, vp, vp], st),
+        "kk_beamform": ([vp, vp, vp, vp, vp, vp], st),
+        "das_beamform": ([vp, vp, vp, vp, vp, vp], st),
+        "kk_run_host_scratch_size": ([vp, ctypes.POINTER(ctypes.c_size_t)], st),
+        "kk_run_host": ([vp, vp, vp, vp, vp, vp], st),
+        "kk_scheme_angles": ([ctypes.c_int32, ctypes.c_int32, _dp, ctypes.c_double,
+                              ctypes.c_int32, ctypes.c_double, _dp], st),
+        "kk_last_error": ([], ctypes.c_char_p),
+        "kk_version": ([], ctypes.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = lib
+    return lib
+
+
+def _check(status: int):
+    if status != KK_OK:
+        raise KKError(status, load().kk_last_error().decode())
+
+
+def _ptr(t) -> ctypes.c_void_p:
+    """Device pointer of a torch tensor (None -> NULL)."""
+    if t is None:
+        return ctypes.c_void_p(0)
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream) -> ctypes.c_void_p:
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def kk_version() -> str:
+    return load().kk_version().decode()
+
+
+def kk_scheme_angles(kind: int, n_tx: int, dtheta: float, M: int, j: float = 0.0, tx=None):
+    """Receive angles of one scheme (host call into the library)."""
+    out = np.empty(M, dtype=np.float64)
+    txa = _f64(tx) if tx is not None else None
+    _check(load().kk_scheme_angles(int(kind), int(n_tx),
+                                   txa.ctypes.data_as(_dp) if txa is not None else None,
+                                   float(dtheta), int(M), float(j), out.ctypes.data_as(_dp)))
+    return out
+
+
+def _desc(elem_x, tx_angles, grid, c, fs, n_samples, rf_dtype, rx_angles=None, pairs=None,
+          group_of_pair=None, n_groups=1, compound=KK_COMPOUND_NONE, precision=KK_PREC_F32,
+          device=0):
+    keep = []
+    ex = _f64(elem_x); keep.append(ex)
+    tx = _f64(tx_angles); keep.append(tx)
+    d = kk_plan_desc()
+    d.n_elem = ex.shape[0]
+    d.elem_x = ex.ctypes.data_as(_dp)
+    d.n_tx = tx.shape[0]
+    d.tx_angles = tx.ctypes.data_as(_dp)
+    if rx_angles is not None:
+        rx = _f64(rx_angles); keep.append(rx)
+        d.n_rx = rx.shape[0]
+        d.rx_angles = rx.ctypes.data_as(_dp)
+    if pairs is not None:
+        pr = np.ascontiguousarray(pairs, dtype=np.int32).reshape(-1, 2); keep.append(pr)
+        d.n_pairs = pr.shape[0]
+        d.pairs = pr.ctypes.data_as(_ip)
+    if group_of_pair is not None:
+        gp = np.ascontiguousarray(group_of_pair, dtype=np.int32); keep.append(gp)
+        d.group_of_pair = gp.ctypes.data_as(_ip)
+    d.n_groups = int(n_groups)
+    d.compound = int(compound)
+    nx, nz, x0, dx, z0, dz = grid
+    d.grid = kk_grid(int(nx), int(nz), float(x0), float(dx), float(z0), float(dz))
+    d.c, d.fs = float(c), float(fs)
+    d.n_samples = int(n_samples)
+    d.rf_dtype = int(rf_dtype)
+    d.precision = int(precision)
+    d.device = int(device)
+    return d, keep
+
+
+def kk_plan_create(desc: kk_plan_desc) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    _check(load().kk_plan_create(ctypes.byref(h), ctypes.byref(desc)))
+    return h
+
+
+def das_plan_create(desc: kk_plan_desc) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    _check(load().das_plan_create(ctypes.byref(h), ctypes.byref(desc)))
+    return h
+
+
+def kk_plan_destroy(h):
+    if h:
+        load().kk_plan_destroy(h)
+
+
+def kk_plan_get_info(h) -> kk_plan_info:
+    info = kk_plan_info()
+    _check(load().kk_plan_get_info(h, ctypes.byref(info)))
+    return info
+
+
+def kk_decompose(h, rf, rf_theta, workspace, stream=None):
+    _check(load().kk_decompose(h, _ptr(rf), _ptr(rf_theta), _ptr(workspace), _stream(stream)))
+
+
+def kk_spectrum(h, rf, X, stream=None):
+    _check(load().kk_spectrum(h, _ptr(rf), _ptr(X), _stream(stream)))
+
+
+def kk_shear(h, X, Y, stream=None):
+    _check(load().kk_shear(h, _ptr(X), _ptr(Y), _stream(stream)))
+
+
+def kk_inverse(h, Y, rf_theta, stream=None):
+    _check(load().kk_inverse(h, _ptr(Y), _ptr(rf_theta), _stream(stream)))
+
+
+def kk_beamform(h, rf_theta, B, I=None, workspace=None, stream=None):
+    _check(load().kk_beamform(h, _ptr(rf_theta), _ptr(B), _ptr(I), _ptr(workspace),
+                              _stream(stream)))
+
+
+def das_beamform(h, rf, B, I=None, workspace=None, stream=None):
+    _check(load().das_beamform(h, _ptr(rf), _ptr(B), _ptr(I), _ptr(workspace), _stream(stream)))
+
+
+def kk_run_host_scratch_size(h) -> int:
+    n = ctypes.c_size_t()
+    _check(load().kk_run_host_scratch_size(h, ctypes.byref(n)))
+    return int(n.value)
+
+
+def kk_run_host(h, h_rf, h_B, h_I, scratch, stream=None):
+    """h_rf/h_B/h_I: CPU tensors (pinned for asynchronous copies)."""
+    _check(load().kk_run_host(h, ctypes.c_void_p(h_rf.data_ptr()), ctypes.c_void_p(h_B.data_ptr()),
+                              ctypes.c_void_p(h_I.data_ptr()) if h_I is not None else None,
+                              _ptr(scratch), _stream(stream)))
+
+
+class Plan:
+    """Owner of a KK or DAS plan handle, with device buffers sized from it."""
+
+    def __init__(self, elem_x, tx_angles, grid, c, fs, n_samples, rf_dtype=KK_RF_F32,
+                 rx_angles=None, pairs=None, group_of_pair=None, n_groups=1,
+                 compound=KK_COMPOUND_NONE, precision=KK_PREC_F32, device=0, das=False):
+        self.desc, self._keep = _desc(elem_x, tx_angles, grid, c, fs, n_samples, rf_dtype,
+                                      rx_angles, pairs, group_of_pair, n_groups, compound,
+                                      precision, device)
+        self.handle = das_plan_create(self.desc) if das else kk_plan_create(self.desc)
+        self.info = kk_plan_get_info(self.handle)
+        self.is_das = das
+        self.device = device
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h:
+            try:
+                kk_plan_destroy(h)
+            except Exception:
+                pass
+            self.handle = None
+
+    # buffer helpers (torch allocations; torch is plumbing for device memory)
+    def empty_workspace(self):
+        import torch
+        n = max(int(self.info.workspace_bytes), 256)
+        return torch.empty(n, dtype=torch.uint8, device=f"cuda:{self.device}")
+
+    def empty_rf_theta(self):
+        import torch
+        return torch.empty((self.info.n_pairs, self.info.n_samples, 2), dtype=torch.float32,
+                           device=f"cuda:{self.device}")
+
+    def empty_image(self):
+        import torch
+        J = 1 if self.is_das else self.info.n_groups
+        return torch.empty((J, self.info.nz, self.info.nx, 2), dtype=torch.float32,
+                           device=f"cuda:{self.device}")
+
+    def empty_intensity(self):
+        import torch
+        return torch.empty((self.info.nz, self.info.nx), dtype=torch.float32,
+                           device=f"cuda:{self.device}")
+
+    def decompose(self, rf, rf_theta, workspace, stream=None):
+        kk_decompose(self.handle, rf, rf_theta, workspace, stream)
+
+    def beamform(self, rf_theta, B, I=None, workspace=None, stream=None):
+        kk_beamform(self.handle, rf_theta, B, I, workspace, stream)
+
+    def das(self, rf, B, I=None, workspace=None, stream=None):
+        das_beamform(self.handle, rf, B, I, workspace, stream)
+
+    def spectrum(self, rf, X, stream=None):
+        kk_spectrum(self.handle, rf, X, stream)
+
+    def shear(self, X, Y, stream=None):
+        kk_shear(self.handle, X, Y, stream)
+
+    def inverse(self, Y, rf_theta, stream=None):
+        kk_inverse(self.handle, Y, rf_theta, stream)
+
+    def run_host(self, h_rf, h_B, h_I, scratch, stream=None):
+        kk_run_host(self.handle, h_rf, h_B, h_I, scratch, stream)
+
+    def scratch_bytes(self) -> int:
+        return kk_run_host_scratch_size(self.handle)

@@ -1,0 +1,197 @@
+// das_beamform.cu -- CPWC delay-and-sum reference, Eq. (DAS).
+//
+//   B(ix, iz) = sum_{i,l} lerp(y_il, s_in(i; ix, iz) + R_l(ix, iz)),
+//   s_in = fs (x sin theta_i + z cos theta_i) / c     (affine, 32.32 fixed point)
+//   R_l  = fs sqrt((x - u_l)^2 + z^2) / c              (per pixel and element)
+//
+// Same tile, staging and floor scheme as the KK gather.  The receive delay
+// R_l is not affine, so it is computed once per (pixel, element) in
+// double-float arithmetic (FP32 hi + lo words; square root with one Newton
+// correction), split into an integer and a fraction, and reused across all
+// transmit angles: the transmit loop is the inner loop, so this costs
+// ~30 FP32 operations per pixel per element against N gathers.
+// Index bound: W0 = floor(min s_in) + floor(min R) - 2 over the tile and the
+// staged window length >= span_in + span_out + 6 keep every read in [0, win).
+#include "kk_internal.h"
+
+namespace kk {
+
+namespace {
+
+constexpr int kMaxStage = 32;
+
+struct __align__(8) WarpChan {
+  unsigned off;
+  float phi;
+};
+
+__device__ __forceinline__ float2 two_sum(float a, float b) {
+  const float s = a + b;
+  const float bb = s - a;
+  const float e = (a - (s - bb)) + (b - bb);
+  return make_float2(s, e);
+}
+
+// (a_hi + a_lo) - (b_hi + b_lo)
+__device__ __forceinline__ float2 df_sub(float2 a, float2 b) {
+  float2 s = two_sum(a.x, -b.x);
+  s.y += a.y - b.y;
+  const float h = s.x + s.y;
+  return make_float2(h, s.y - (h - s.x));
+}
+
+// (h + l)^2 as double-float
+__device__ __forceinline__ float2 df_sqr(float2 a) {
+  const float p = a.x * a.x;
+  float e = fmaf(a.x, a.x, -p);
+  e = fmaf(2.f * a.x, a.y, e);
+  return make_float2(p, e);
+}
+
+__device__ __forceinline__ float2 df_add(float2 a, float2 b) {
+  float2 s = two_sum(a.x, b.x);
+  s.y += a.y + b.y;
+  const float h = s.x + s.y;
+  return make_float2(h, s.y - (h - s.x));
+}
+
+__global__ void __launch_bounds__(kGatherThreads)
+    k_das_gather(const float2 *__restrict__ y, int N, int L, int T, const long long *__restrict__ dA,
+                 const long long *__restrict__ dB, const long long *__restrict__ dC,
+                 const float *__restrict__ dAf, const float *__restrict__ dBf,
+                 const float2 *__restrict__ xs, const float2 *__restrict__ zs,
+                 const float2 *__restrict__ us, int nx, int nz, int tiles_x, int win, int stage,
+                 float2 *__restrict__ B, float *__restrict__ I) {
+  extern __shared__ float4 sw[];
+  __shared__ WarpChan s_wc[4][kMaxStage];
+  __shared__ float2 s_ab[kMaxStage];
+  __shared__ int s_w0[kMaxStage];
+  __shared__ int s_row[kMaxStage];
+
+  const int tid = threadIdx.x;
+  const int warp = tid >> 5, lane = tid & 31;
+  const int tile = blockIdx.x;
+  const int ix0 = (tile % tiles_x) * kTileX;
+  const int iz0 = (tile / tiles_x) * kTileZ;
+  const int ix = ix0 + lane;
+  const int izb = iz0 + warp * kRowsPerThread;
+  const float dl = (float)(lane - 16);
+
+  const float2 xq = __ldg(xs + ix);
+  float2 z2[kRowsPerThread];
+#pragma unroll
+  for (int r = 0; r < kRowsPerThread; ++r) z2[r] = df_sqr(__ldg(zs + izb + r));
+  const float xlo = __ldg(xs + ix0).x, xhi = __ldg(xs + ix0 + kTileX - 1).x;
+  const float zlo = __ldg(zs + iz0).x;
+
+  float2 acc[kRowsPerThread];
+#pragma unroll
+  for (int r = 0; r < kRowsPerThread; ++r) acc[r] = make_float2(0.f, 0.f);
+
+  for (int l = 0; l < L; ++l) {
+    const float2 u = __ldg(us + l);
+    // receive delay of this thread's pixels: integer part (x16 bytes) + fraction
+    const float2 dx2 = df_sqr(df_sub(xq, u));
+    unsigned kout16[kRowsPerThread];
+    float fout[kRowsPerThread];
+#pragma unroll
+    for (int r = 0; r < kRowsPerThread; ++r) {
+      const float2 S = df_add(dx2, z2[r]);
+      const float rh = sqrtf(S.x);
+      const float t = fmaf(-rh, rh, S.x) + S.y;
+      const float corr = (rh > 0.f) ? t / (2.f * rh) : 0.f;
+      const float kf = floorf(rh);
+      kout16[r] = (unsigned)(int)kf * 16u;
+      fout[r] = (rh - kf) + corr;
+    }
+    // smallest receive delay over the tile (lower bound for the window)
+    const float xc = fminf(fmaxf(u.x, xlo), xhi) - u.x;
+    const int kout_min = (int)floorf(sqrtf(fmaf(xc, xc, zlo * zlo)));
+
+    for (int ps = 0; ps < N; ps += stage) {
+      const int ns = min(stage, N - ps);
+      __syncthreads();
+      {
+        const int j = tid & 31, w = tid >> 5;
+        if (j < ns) {
+          const int i = ps + j;
+          const long long A = __ldg(dA + i), Bq = __ldg(dB + i), Cq = __ldg(dC + i);
+          const long long smin = Cq + Bq * (long long)iz0 + A * (long long)(A >= 0 ? ix0 : ix0 + kTileX - 1);
+          const int w0 = (int)(smin >> 32) + kout_min - 2;
+          const long long sref = Cq + Bq * (long long)(iz0 + w * kRowsPerThread + kRowsPerThread / 2) +
+                                 A * (long long)(ix0 + 16);
+          const int kref = (int)(sref >> 32);
+          WarpChan wc;
+          wc.phi = (float)(unsigned)(sref & 0xffffffffLL) * 0x1p-32f;
+          wc.off = (unsigned)(j * win + (kref - w0)) * 16u - (unsigned)kFloorMagicBits * 16u;
+          s_wc[w][j] = wc;
+          if (w == 0) {
+            s_ab[j] = make_float2(__ldg(dAf + i), __ldg(dBf + i));
+            s_w0[j] = w0;
+            s_row[j] = i * L + l;
+          }
+        }
+      }
+      __syncthreads();
+      for (int e = tid; e < ns * win; e += kGatherThreads) {
+        const int j = e / win, m = e - j * win;
+        const int k = s_w0[j] + m;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (k >= 0 && k <= T - 2) {
+          const float2 *yr = y + (size_t)s_row[j] * T;
+          const float2 a = __ldg(yr + k), b = __ldg(yr + k + 1);
+          v = make_float4(a.x, a.y, b.x - a.x, b.y - a.y);
+        }
+        sw[e] = v;
+      }
+      __syncthreads();
+      float2 sacc[kRowsPerThread];
+#pragma unroll
+      for (int r = 0; r < kRowsPerThread; ++r) sacc[r] = make_float2(0.f, 0.f);
+      const char *swb = reinterpret_cast<const char *>(sw);
+      for (int j = 0; j < ns; ++j) {
+        const float2 ab = s_ab[j];
+        const WarpChan wc = s_wc[warp][j];
+        const float base = fmaf(ab.x, dl, wc.phi);
+#pragma unroll
+        for (int r = 0; r < kRowsPerThread; ++r) {
+          const float s = fmaf(ab.y, (float)(r - kRowsPerThread / 2), base) + fout[r];
+          const float t = __fadd_rd(s, kFloorMagic);
+          const float f = s - (t - kFloorMagic);
+          const unsigned addr = wc.off + kout16[r] + ((unsigned)__float_as_int(t) << 4);
+          const float4 e = *reinterpret_cast<const float4 *>(swb + addr);
+          sacc[r].x += fmaf(f, e.z, e.x);
+          sacc[r].y += fmaf(f, e.w, e.y);
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < kRowsPerThread; ++r) {
+        acc[r].x += sacc[r].x;
+        acc[r].y += sacc[r].y;
+      }
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < kRowsPerThread; ++r) {
+    const int iz = izb + r;
+    if (ix < nx && iz < nz) {
+      B[(size_t)iz * nx + ix] = acc[r];
+      if (I != nullptr) I[(size_t)iz * nx + ix] = fmaf(acc[r].x, acc[r].x, acc[r].y * acc[r].y);
+    }
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_das_gather(const kk_plan &p, const float2 *y, float2 *B, float *I,
+                              cudaStream_t s) {
+  const size_t smem = sizeof(float4) * (size_t)p.bf_stage * p.bf_win;
+  cudaFuncSetAttribute(k_das_gather, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const dim3 grid(p.tiles_x * p.tiles_z);
+  k_das_gather<<<grid, kGatherThreads, smem, s>>>(
+      y, p.N, p.L, p.T, p.t.das_A, p.t.das_B, p.t.das_C, p.t.das_Af, p.t.das_Bf, p.t.xs, p.t.zs,
+      p.t.us, p.grid.nx, p.grid.nz, p.tiles_x, p.bf_win, p.bf_stage, B, I);
+  return cudaGetLastError();
+}
+
+}  // namespace kk

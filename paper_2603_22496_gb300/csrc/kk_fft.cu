@@ -1,0 +1,309 @@
+// kk_fft.cu -- analytic spectrum (forward) and half-spectrum inverse.
+//
+// Section II-F of the paper: the RF records are made complex (analytic) by a
+// temporal Fourier transform with the negative frequencies set to zero, and
+// the receive shear of Eq. (compression) is applied in that frequency domain.
+//
+//  * k_spectrum: one T-sample real record per channel -> X[k] for k < F = T/2,
+//    with weights h_0 = 1, h_k = 2 (the Nyquist bin is dropped).  The record
+//    is packed as F complex points z[n] = x[2n] + i x[2n+1], transformed with
+//    an F-point Stockham FFT in shared memory, and split into the T-point
+//    spectrum by X[k] = E[k] + e^{-2 pi i k / T} O[k].
+//    Output layout X[k][c] (bin-major) feeds the per-bin contraction.
+//  * k_inverse: y[t] = (1/T) sum_{k<F} Y[k] e^{+2 pi i k t / T} for t < T,
+//    computed as two F-point inverse transforms (even t from Y[k], odd t from
+//    Y[k] e^{+2 pi i k / T}), written as one contiguous T-sample row.
+//
+// Each CTA transforms several records at once (C per CTA), so that a
+// bin-major global access touches C consecutive complex values.  The
+// transform runs in place in shared memory: every pass reads its butterfly
+// inputs into registers, synchronises, then writes the outputs.
+#include "kk_internal.h"
+
+namespace kk {
+
+// ---- radix plan (shared by host and device) --------------------------------
+__host__ __device__ constexpr int fft_npass(int F) {
+  int n = 0;
+  while (F % 4 == 0) { F /= 4; ++n; }
+  while (F % 2 == 0) { F /= 2; ++n; }
+  while (F % 3 == 0) { F /= 3; ++n; }
+  return n;
+}
+__host__ __device__ constexpr int fft_radix(int F, int i) {
+  int n = 0;
+  while (F % 4 == 0) { if (n == i) return 4; F /= 4; ++n; }
+  while (F % 2 == 0) { if (n == i) return 2; F /= 2; ++n; }
+  while (F % 3 == 0) { if (n == i) return 3; F /= 3; ++n; }
+  return 1;
+}
+__host__ __device__ constexpr int fft_ns(int F, int i) {
+  int ns = 1;
+  for (int k = 0; k < i; ++k) ns *= fft_radix(F, k);
+  return ns;
+}
+__host__ __device__ constexpr int fft_twoff(int F, int i) {
+  int off = 0;
+  for (int k = 0; k < i; ++k) off += fft_ns(F, k) * (fft_radix(F, k) - 1);
+  return off;
+}
+
+bool fft_size_supported(int F) {
+  return F == 128 || F == 256 || F == 512 || F == 768 || F == 1024 || F == 1536 || F == 2048;
+}
+
+FftPlan make_fft_plan(int F) {
+  FftPlan p;
+  p.F = F;
+  p.npass = fft_npass(F);
+  for (int i = 0; i < p.npass; ++i) {
+    p.radix[i] = fft_radix(F, i);
+    p.ns[i] = fft_ns(F, i);
+    p.tw_off[i] = fft_twoff(F, i);
+  }
+  p.tw_count = fft_twoff(F, p.npass);
+  return p;
+}
+
+// ---- complex helpers --------------------------------------------------------
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+
+// forward DFT of size R in registers (kernel e^{-2 pi i / R})
+template <int R> __device__ __forceinline__ void dft(float2 *v);
+template <> __device__ __forceinline__ void dft<2>(float2 *v) {
+  float2 a = v[0], b = v[1];
+  v[0] = cadd(a, b);
+  v[1] = csub(a, b);
+}
+template <> __device__ __forceinline__ void dft<3>(float2 *v) {
+  const float h = 0.866025403784438646763723170752936183f;  // sqrt(3)/2
+  float2 a = v[0], s = cadd(v[1], v[2]), d = csub(v[1], v[2]);
+  float2 m = make_float2(fmaf(-0.5f, s.x, a.x), fmaf(-0.5f, s.y, a.y));
+  v[0] = cadd(a, s);
+  // -i * h * d = (h d.y, -h d.x)
+  v[1] = make_float2(fmaf(h, d.y, m.x), fmaf(-h, d.x, m.y));
+  v[2] = make_float2(fmaf(-h, d.y, m.x), fmaf(h, d.x, m.y));
+}
+template <> __device__ __forceinline__ void dft<4>(float2 *v) {
+  float2 t0 = cadd(v[0], v[2]), t1 = csub(v[0], v[2]);
+  float2 t2 = cadd(v[1], v[3]), t3 = csub(v[1], v[3]);
+  v[0] = cadd(t0, t2);
+  v[2] = csub(t0, t2);
+  v[1] = make_float2(t1.x + t3.y, t1.y - t3.x);  // t1 - i t3
+  v[3] = make_float2(t1.x - t3.y, t1.y + t3.x);  // t1 + i t3
+}
+
+// One Stockham pass over NTR transforms of F points stored with row stride FS.
+template <int R, int NS, int F, int FS, int NTR, int NT>
+__device__ __forceinline__ void stockham_pass(float2 *buf, const float2 *__restrict__ tw, int tid) {
+  constexpr int NBF = NTR * (F / R);
+  constexpr int NB = (NBF + NT - 1) / NT;
+  float2 v[NB][R];
+#pragma unroll
+  for (int b = 0; b < NB; ++b) {
+    const int j = tid + b * NT;
+    if (NBF % NT == 0 || j < NBF) {
+      const int tr = j / (F / R);
+      const int jj = j - tr * (F / R);
+      const int k = jj % NS;
+      const float2 *src = buf + tr * FS + jj;
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[b][r] = src[r * (F / R)];
+      if (NS > 1) {
+#pragma unroll
+        for (int r = 1; r < R; ++r) v[b][r] = cmul(v[b][r], __ldg(tw + k * (R - 1) + (r - 1)));
+      }
+      dft<R>(v[b]);
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int b = 0; b < NB; ++b) {
+    const int j = tid + b * NT;
+    if (NBF % NT == 0 || j < NBF) {
+      const int tr = j / (F / R);
+      const int jj = j - tr * (F / R);
+      const int k = jj % NS;
+      float2 *dst = buf + tr * FS + (jj - k) * R + k;
+#pragma unroll
+      for (int r = 0; r < R; ++r) dst[r * NS] = v[b][r];
+    }
+  }
+  __syncthreads();
+}
+
+template <int F, int FS, int NTR, int NT, int I>
+__device__ __forceinline__ void run_passes(float2 *buf, const float2 *__restrict__ tw, int tid) {
+  if constexpr (I < fft_npass(F)) {
+    constexpr int R = fft_radix(F, I);
+    constexpr int NS = fft_ns(F, I);
+    constexpr int OFF = fft_twoff(F, I);
+    stockham_pass<R, NS, F, FS, NTR, NT>(buf, tw + OFF, tid);
+    run_passes<F, FS, NTR, NT, I + 1>(buf, tw, tid);
+  }
+}
+
+__device__ __forceinline__ float2 load_pair(const int16_t *p) {
+  const short2 v = *reinterpret_cast<const short2 *>(p);
+  return make_float2((float)v.x, (float)v.y);
+}
+__device__ __forceinline__ float2 load_pair(const float *p) {
+  return *reinterpret_cast<const float2 *>(p);
+}
+
+// ---- forward: analytic spectrum -------------------------------------------
+// X[k][c] for channel c = iu * L + l (row tx_rows[iu] * L + l of rf).
+template <int F, int C, int NT, typename TIn>
+__global__ void __launch_bounds__(NT) k_spectrum(const TIn *__restrict__ rf,
+                                                 const int32_t *__restrict__ tx_rows, int L,
+                                                 int n_ch, const float2 *__restrict__ tw,
+                                                 const float2 *__restrict__ rw,
+                                                 float2 *__restrict__ X) {
+  constexpr int FS = F + 1;
+  constexpr int T = 2 * F;
+  extern __shared__ float2 sm[];
+  const int tid = threadIdx.x;
+  const int c0 = blockIdx.x * C;
+  for (int idx = tid; idx < C * F; idx += NT) {
+    const int cc = idx / F, n = idx - cc * F;
+    const int c = c0 + cc;
+    float2 z = make_float2(0.f, 0.f);
+    if (c < n_ch) {
+      const int iu = c / L, l = c - iu * L;
+      const size_t row = (size_t)__ldg(tx_rows + iu) * L + l;
+      z = load_pair(rf + row * T + 2 * n);
+    }
+    sm[cc * FS + n] = z;
+  }
+  __syncthreads();
+  run_passes<F, FS, C, NT, 0>(sm, tw, tid);
+  for (int idx = tid; idx < C * F; idx += NT) {
+    const int k = idx / C, cc = idx - k * C;
+    const int c = c0 + cc;
+    if (c >= n_ch) continue;
+    const float2 zk = sm[cc * FS + k];
+    const float2 zm = sm[cc * FS + (k == 0 ? 0 : F - k)];
+    // E = (Z[k] + conj Z[F-k]) / 2,  O = (Z[k] - conj Z[F-k]) / (2i)
+    const float2 e = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
+    const float2 o = make_float2(0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
+    float2 x = cadd(e, cmul(__ldg(rw + k), o));
+    const float h = (k == 0) ? 1.f : 2.f;
+    x.x *= h;
+    x.y *= h;
+    X[(size_t)k * n_ch + c] = x;
+  }
+}
+
+// ---- inverse of a half spectrum -------------------------------------------
+// out[row][t], row < nrow, from Y[k][col(row)] (col = identity if null).
+template <int F, int C, int NT>
+__global__ void __launch_bounds__(NT) k_inverse(const float2 *__restrict__ Y, int ncol,
+                                                const int32_t *__restrict__ col_of_row, int nrow,
+                                                const float2 *__restrict__ tw,
+                                                const float2 *__restrict__ rw,
+                                                float2 *__restrict__ out, float scale) {
+  constexpr int FS = F + 1;
+  constexpr int T = 2 * F;
+  extern __shared__ float2 sm[];
+  const int tid = threadIdx.x;
+  const int r0 = blockIdx.x * C;
+  for (int idx = tid; idx < C * F; idx += NT) {
+    const int k = idx / C, rr = idx - k * C;
+    const int row = r0 + rr;
+    float2 y = make_float2(0.f, 0.f);
+    if (row < nrow) {
+      const int q = col_of_row ? __ldg(col_of_row + row) : row;
+      y = Y[(size_t)k * ncol + q];
+    }
+    // inverse via conj(FFT(conj(.))): even samples from conj(Y),
+    // odd samples from conj(Y e^{+2 pi i k/T}) = conj(Y) e^{-2 pi i k/T}
+    const float2 a = make_float2(y.x, -y.y);
+    sm[(2 * rr) * FS + k] = a;
+    sm[(2 * rr + 1) * FS + k] = cmul(a, __ldg(rw + k));
+  }
+  __syncthreads();
+  run_passes<F, FS, 2 * C, NT, 0>(sm, tw, tid);
+  for (int idx = tid; idx < C * F; idx += NT) {
+    const int rr = idx / F, m = idx - rr * F;
+    const int row = r0 + rr;
+    if (row >= nrow) continue;
+    const float2 ev = sm[(2 * rr) * FS + m];
+    const float2 od = sm[(2 * rr + 1) * FS + m];
+    const float4 o = make_float4(ev.x * scale, -ev.y * scale, od.x * scale, -od.y * scale);
+    *reinterpret_cast<float4 *>(out + (size_t)row * T + 2 * m) = o;
+  }
+}
+
+// ---- dispatch ----------------------------------------------------------------
+template <int F>
+struct FftCfg {
+  static constexpr int CS = (F >= 1536) ? 4 : 8;   // records per CTA, forward
+  static constexpr int CI = (F >= 1536) ? 2 : 4;   // records per CTA, inverse (2 transforms each)
+  static constexpr int NT = (F <= 256) ? 256 : 512;
+};
+
+template <int F>
+static cudaError_t spectrum_f(const kk_plan &p, const void *rf, float2 *X, int n_rows,
+                              const int32_t *rows, cudaStream_t s) {
+  using Cfg = FftCfg<F>;
+  const int n_ch = n_rows * p.L;
+  const size_t smem = sizeof(float2) * Cfg::CS * (F + 1);
+  const dim3 grid((n_ch + Cfg::CS - 1) / Cfg::CS);
+  if (p.rf_dtype == KK_RF_I16) {
+    auto k = k_spectrum<F, Cfg::CS, Cfg::NT, int16_t>;
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k<<<grid, Cfg::NT, smem, s>>>((const int16_t *)rf, rows, p.L, n_ch, p.t.fft_tw, p.t.rfft_w, X);
+  } else {
+    auto k = k_spectrum<F, Cfg::CS, Cfg::NT, float>;
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k<<<grid, Cfg::NT, smem, s>>>((const float *)rf, rows, p.L, n_ch, p.t.fft_tw, p.t.rfft_w, X);
+  }
+  return cudaGetLastError();
+}
+
+template <int F>
+static cudaError_t inverse_f(const kk_plan &p, const float2 *Y, int ncol, const int32_t *col,
+                             int nrow, float2 *out, cudaStream_t s) {
+  using Cfg = FftCfg<F>;
+  const size_t smem = sizeof(float2) * 2 * Cfg::CI * (F + 1);
+  auto k = k_inverse<F, Cfg::CI, Cfg::NT>;
+  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const dim3 grid((nrow + Cfg::CI - 1) / Cfg::CI);
+  k<<<grid, Cfg::NT, smem, s>>>(Y, ncol, col, nrow, p.t.fft_tw, p.t.rfft_w, out,
+                                (float)(1.0 / (double)(2 * F)));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_spectrum(const kk_plan &p, const void *rf, float2 *X, int n_rows,
+                            const int32_t *rows, cudaStream_t s) {
+  switch (p.F) {
+    case 128: return spectrum_f<128>(p, rf, X, n_rows, rows, s);
+    case 256: return spectrum_f<256>(p, rf, X, n_rows, rows, s);
+    case 512: return spectrum_f<512>(p, rf, X, n_rows, rows, s);
+    case 768: return spectrum_f<768>(p, rf, X, n_rows, rows, s);
+    case 1024: return spectrum_f<1024>(p, rf, X, n_rows, rows, s);
+    case 1536: return spectrum_f<1536>(p, rf, X, n_rows, rows, s);
+    case 2048: return spectrum_f<2048>(p, rf, X, n_rows, rows, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_inverse(const kk_plan &p, const float2 *Y, int ncol, const int32_t *col,
+                           int nrow, float2 *out, cudaStream_t s) {
+  switch (p.F) {
+    case 128: return inverse_f<128>(p, Y, ncol, col, nrow, out, s);
+    case 256: return inverse_f<256>(p, Y, ncol, col, nrow, out, s);
+    case 512: return inverse_f<512>(p, Y, ncol, col, nrow, out, s);
+    case 768: return inverse_f<768>(p, Y, ncol, col, nrow, out, s);
+    case 1024: return inverse_f<1024>(p, Y, ncol, col, nrow, out, s);
+    case 1536: return inverse_f<1536>(p, Y, ncol, col, nrow, out, s);
+    case 2048: return inverse_f<2048>(p, Y, ncol, col, nrow, out, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace kk

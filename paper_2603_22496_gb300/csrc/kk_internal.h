@@ -1,0 +1,106 @@
+// kk_internal.h -- plan layout and launch declarations shared by the library's
+// translation units.  Not part of the public ABI (see include/kkbeam.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/kkbeam.h"
+
+namespace kk {
+
+// Tile of the gather kernels: 32 pixels along x (one warp, lane = x offset)
+// by 32 along z (4 warps x 8 rows per thread).
+constexpr int kTileX = 32;
+constexpr int kTileZ = 32;
+constexpr int kRowsPerThread = 8;
+constexpr int kGatherThreads = 128;
+
+// 1.5 * 2^23: adding it with round-down leaves floor(s) in the low mantissa
+// bits for |s| < 2^22.
+constexpr float kFloorMagic = 12582912.0f;
+constexpr int kFloorMagicBits = 0x4B400000;
+
+// Supported FFT lengths for the analytic spectrum (F = T/2 points, complex).
+bool fft_size_supported(int F);
+
+// Radix plan of an F-point Stockham FFT: radices applied in order, each pass
+// with Ns = product of earlier radices, twiddle table offsets per pass.
+struct FftPlan {
+  int F = 0;
+  int npass = 0;
+  int radix[12] = {};
+  int ns[12] = {};
+  int tw_off[12] = {};
+  int tw_count = 0;
+};
+FftPlan make_fft_plan(int F);
+
+// Device-side plan tables, all inside one allocation.
+struct DevTables {
+  // FFT
+  float2 *fft_tw = nullptr;   // Stockham twiddles e^{-2 pi i r k / (Ns R)}
+  float2 *rfft_w = nullptr;   // [F] e^{-2 pi i k / T}
+  int32_t *tx_used = nullptr; // [Nu] row of rf for used transmit iu
+  // decomposition
+  unsigned long long *phase = nullptr; // [Mu][L] frac(D/T) * 2^64
+  int32_t *pair_q = nullptr;           // [P] (caller order) column of Y
+  // KK gather (pairs in group-sorted order)
+  int32_t *bf_row = nullptr;           // [P] row of rf_theta
+  long long *bf_A = nullptr, *bf_B = nullptr, *bf_C = nullptr; // 32.32 samples
+  float *bf_Af = nullptr, *bf_Bf = nullptr;                    // samples per pixel
+  int32_t *group_start = nullptr;      // [J+1]
+  // DAS
+  long long *das_A = nullptr, *das_B = nullptr, *das_C = nullptr; // [N] tau_in 32.32
+  float *das_Af = nullptr, *das_Bf = nullptr;                     // [N]
+  float2 *xs = nullptr;                // [nx] x fs / c as (hi, lo)
+  float2 *zs = nullptr;                // [nz] z fs / c as (hi, lo)
+  float2 *us = nullptr;                // [L]  u fs / c as (hi, lo)
+};
+
+}  // namespace kk
+
+struct kk_plan {
+  bool is_das = false;
+  int device = 0;
+  int L = 0, N = 0, T = 0, F = 0, P = 0, J = 1, Nu = 0, Mu = 0;
+  int compound = KK_COMPOUND_NONE;
+  int rf_dtype = KK_RF_F32;
+  int precision = KK_PREC_F32;
+  kk_grid grid{};
+  double c = 0, fs = 0;
+  kk::FftPlan fft;
+  kk::DevTables t;
+  void *dev_block = nullptr;     // the one allocation holding DevTables
+  std::vector<int32_t> h_group_start;
+  // gather kernel configuration
+  int bf_win = 0;      // window entries staged per pair / channel
+  int bf_stage = 0;    // pairs (KK) or transmits (DAS) per stage
+  int bf_split = 1;    // pair-range splits (KK), partial images reduced after
+  int tiles_x = 0, tiles_z = 0;
+  // workspace layout (bytes from the workspace base)
+  size_t ws_X = 0, ws_Y = 0, ws_part = 0, ws_total = 0;
+  double compression = 0;
+};
+
+namespace kk {
+
+// thread-local error message
+void set_error(const std::string &msg);
+kk_status cuda_fail(cudaError_t e, const char *what);
+
+// ---- launches (each returns cudaGetLastError() after the launch) ----------
+cudaError_t launch_spectrum(const kk_plan &p, const void *rf, float2 *X, int n_tx_rows,
+                            const int32_t *tx_rows, cudaStream_t s);
+cudaError_t launch_inverse(const kk_plan &p, const float2 *Y, int ncol, const int32_t *col_of_row,
+                           int nrow, float2 *out, cudaStream_t s);
+cudaError_t launch_shear_f32(const kk_plan &p, const float2 *X, float2 *Y, cudaStream_t s);
+cudaError_t launch_kk_gather(const kk_plan &p, const float2 *rf_theta, float2 *B, float *I,
+                             float2 *partial, cudaStream_t s);
+cudaError_t launch_das_gather(const kk_plan &p, const float2 *y, float2 *B, float *I,
+                              cudaStream_t s);
+
+}  // namespace kk

@@ -1,0 +1,634 @@
+// kk_plan.cpp -- host side of the C ABI: validation, FP64 plan tables,
+// workspace layout and the enqueue entry points.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "kk_internal.h"
+
+namespace kk {
+
+static thread_local std::string g_err;
+
+void set_error(const std::string &msg) { g_err = msg; }
+
+kk_status cuda_fail(cudaError_t e, const char *what) {
+  set_error(std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")");
+  return KK_ERR_CUDA;
+}
+
+namespace {
+
+constexpr double kTwoPi = 6.283185307179586476925286766559;
+constexpr double kTwo32 = 4294967296.0;
+constexpr double kMaxAngle = 80.0 * 3.14159265358979323846 / 180.0;
+constexpr size_t kAlign = 256;
+
+size_t align_up(size_t v, size_t a = kAlign) { return (v + a - 1) / a * a; }
+
+// Keeps the caller's current device and restores it on exit.
+struct DeviceGuard {
+  int old = -1;
+  bool ok = true;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&old) != cudaSuccess) old = -1;
+    if (old != dev) ok = cudaSetDevice(dev) == cudaSuccess;
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (old >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != old) cudaSetDevice(old);
+  }
+};
+
+// x_ref(theta_o): the array end that makes the shear a non-negative advance.
+double shear_reference(const std::vector<double> &u, double th) {
+  if (th > 0) return *std::max_element(u.begin(), u.end());
+  if (th < 0) return *std::min_element(u.begin(), u.end());
+  return 0.0;
+}
+
+long long to_fixed32(double v) { return std::llround(v * kTwo32); }
+
+// frac(v) as an unsigned 0.64 fixed-point fraction
+unsigned long long frac64(double v) {
+  double f = v - std::floor(v);
+  if (f >= 1.0) f = 0.0;
+  const double hi = std::floor(f * kTwo32);
+  double lo = std::floor((f * kTwo32 - hi) * kTwo32);
+  if (lo < 0) lo = 0;
+  if (lo >= kTwo32) lo = kTwo32 - 1;
+  return ((unsigned long long)hi << 32) | (unsigned long long)lo;
+}
+
+// Host staging of the plan's tables, uploaded in one allocation.
+struct Blob {
+  std::vector<unsigned char> bytes;
+  template <typename T>
+  size_t add(const std::vector<T> &v) {
+    const size_t off = align_up(bytes.size());
+    bytes.resize(off + std::max<size_t>(sizeof(T) * v.size(), 1));
+    if (!v.empty()) std::memcpy(bytes.data() + off, v.data(), sizeof(T) * v.size());
+    return off;
+  }
+};
+
+template <typename T>
+T *at(void *base, size_t off) {
+  return reinterpret_cast<T *>(static_cast<unsigned char *>(base) + off);
+}
+
+kk_status validate_common(const kk_plan_desc *d) {
+  if (!d) { set_error("null plan description"); return KK_ERR_INVALID_ARG; }
+  if (d->n_elem < 1 || !d->elem_x) { set_error("n_elem < 1 or elem_x null"); return KK_ERR_INVALID_ARG; }
+  if (d->n_tx < 1 || !d->tx_angles) { set_error("n_tx < 1 or tx_angles null"); return KK_ERR_INVALID_ARG; }
+  for (int i = 0; i < d->n_tx; ++i)
+    if (!(std::fabs(d->tx_angles[i]) < kMaxAngle)) { set_error("transmit angle out of range (|theta| < 80 deg)"); return KK_ERR_INVALID_ARG; }
+  for (int l = 0; l < d->n_elem; ++l)
+    if (!std::isfinite(d->elem_x[l])) { set_error("non-finite element position"); return KK_ERR_INVALID_ARG; }
+  if (!(d->c > 0) || !(d->fs > 0) || !std::isfinite(d->c) || !std::isfinite(d->fs)) { set_error("c and fs must be positive"); return KK_ERR_INVALID_ARG; }
+  const kk_grid &g = d->grid;
+  if (g.nx < 1 || g.nz < 1 || g.nx > 8192 || g.nz > 8192) { set_error("grid size out of range [1, 8192]"); return KK_ERR_INVALID_ARG; }
+  if (!(g.dx > 0) || !(g.dz > 0) || !(g.z0 >= 0) || !std::isfinite(g.x0)) { set_error("grid needs dx > 0, dz > 0, z0 >= 0"); return KK_ERR_INVALID_ARG; }
+  if (d->n_samples < 2 || d->n_samples % 2) { set_error("n_samples must be even"); return KK_ERR_INVALID_ARG; }
+  if (!fft_size_supported(d->n_samples / 2)) { set_error("n_samples / 2 must be one of 128, 256, 512, 768, 1024, 1536, 2048"); return KK_ERR_UNSUPPORTED; }
+  if (d->rf_dtype != KK_RF_I16 && d->rf_dtype != KK_RF_F32) { set_error("bad rf_dtype"); return KK_ERR_INVALID_ARG; }
+  // the largest delay must stay well inside the 32.32 fixed-point and FP32 index range
+  const double xmax = std::max(std::fabs(g.x0), std::fabs(g.x0 + g.dx * (g.nx + 64)));
+  const double zmax = g.z0 + g.dz * (g.nz + 64);
+  double umax = 0;
+  for (int l = 0; l < d->n_elem; ++l) umax = std::max(umax, std::fabs(d->elem_x[l]));
+  const double smax = d->fs / d->c * (2 * (xmax + umax) + 2 * zmax);
+  if (smax > 1e6) { set_error("geometry gives delays beyond 1e6 samples"); return KK_ERR_INVALID_ARG; }
+  int dev_count = 0;
+  if (cudaGetDeviceCount(&dev_count) != cudaSuccess || d->device < 0 || d->device >= dev_count) {
+    set_error("device ordinal not available");
+    return KK_ERR_INVALID_ARG;
+  }
+  return KK_OK;
+}
+
+void fill_fft(kk_plan &p, Blob &blob, size_t &off_tw, size_t &off_rw) {
+  p.fft = make_fft_plan(p.F);
+  std::vector<float2> tw(std::max(p.fft.tw_count, 1));
+  for (int s = 0; s < p.fft.npass; ++s) {
+    const int R = p.fft.radix[s], ns = p.fft.ns[s];
+    for (int k = 0; k < ns; ++k)
+      for (int r = 1; r < R; ++r) {
+        const long long m = ((long long)r * k) % ((long long)ns * R);
+        const double a = -kTwoPi * (double)m / (double)(ns * R);
+        tw[p.fft.tw_off[s] + k * (R - 1) + (r - 1)] = make_float2((float)std::cos(a), (float)std::sin(a));
+      }
+  }
+  std::vector<float2> rw(p.F);
+  for (int k = 0; k < p.F; ++k) {
+    const double a = -kTwoPi * (double)k / (double)p.T;
+    rw[k] = make_float2((float)std::cos(a), (float)std::sin(a));
+  }
+  off_tw = blob.add(tw);
+  off_rw = blob.add(rw);
+}
+
+kk_status upload(kk_plan &p, const Blob &blob) {
+  void *dev = nullptr;
+  cudaError_t e = cudaMalloc(&dev, blob.bytes.size());
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    set_error("plan table allocation failed");
+    return KK_ERR_OOM;
+  }
+  e = cudaMemcpy(dev, blob.bytes.data(), blob.bytes.size(), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    cudaFree(dev);
+    return cuda_fail(e, "plan table upload");
+  }
+  p.dev_block = dev;
+  return KK_OK;
+}
+
+int choose_stage(int win) {
+  // about 40 KB of staged windows per CTA, at most 32 pairs / transmits
+  int st = (int)(40 * 1024 / (16 * (size_t)win));
+  return std::max(1, std::min(32, st));
+}
+
+kk_status make_kk(kk_plan &p, const kk_plan_desc *d) {
+  if (d->n_rx < 1 || !d->rx_angles) { set_error("n_rx < 1 or rx_angles null"); return KK_ERR_INVALID_ARG; }
+  if (d->n_pairs < 1 || !d->pairs) { set_error("n_pairs < 1 or pairs null"); return KK_ERR_INVALID_ARG; }
+  if (d->n_groups < 1) { set_error("n_groups < 1"); return KK_ERR_INVALID_ARG; }
+  if (d->compound < KK_COMPOUND_NONE || d->compound > KK_COMPOUND_INCOHERENT) { set_error("bad compound mode"); return KK_ERR_INVALID_ARG; }
+  if (d->precision != KK_PREC_F32) { set_error("only the FP32 precision form is built in this library"); return KK_ERR_UNSUPPORTED; }
+  for (int o = 0; o < d->n_rx; ++o)
+    if (!(std::fabs(d->rx_angles[o]) < kMaxAngle)) { set_error("receive angle out of range (|theta| < 80 deg)"); return KK_ERR_INVALID_ARG; }
+  const int P = d->n_pairs, J = d->n_groups;
+  std::vector<int> gp(P, 0);
+  for (int q = 0; q < P; ++q) {
+    const int i = d->pairs[2 * q], o = d->pairs[2 * q + 1];
+    if (i < 0 || i >= d->n_tx || o < 0 || o >= d->n_rx) { set_error("pair index out of range"); return KK_ERR_INVALID_ARG; }
+    if (d->group_of_pair) {
+      gp[q] = d->group_of_pair[q];
+      if (gp[q] < 0 || gp[q] >= J) { set_error("group index out of range"); return KK_ERR_INVALID_ARG; }
+    }
+  }
+  p.P = P;
+  p.J = J;
+  p.compound = d->compound;
+  p.precision = d->precision;
+
+  std::vector<double> u(d->elem_x, d->elem_x + p.L);
+  // transmits and receive angles in use
+  std::vector<int> tx_used, rx_used;
+  for (int q = 0; q < P; ++q) {
+    tx_used.push_back(d->pairs[2 * q]);
+    rx_used.push_back(d->pairs[2 * q + 1]);
+  }
+  std::sort(tx_used.begin(), tx_used.end());
+  tx_used.erase(std::unique(tx_used.begin(), tx_used.end()), tx_used.end());
+  std::sort(rx_used.begin(), rx_used.end());
+  rx_used.erase(std::unique(rx_used.begin(), rx_used.end()), rx_used.end());
+  p.Nu = (int)tx_used.size();
+  p.Mu = (int)rx_used.size();
+  std::vector<int> tx_pos(d->n_tx, -1), rx_pos(d->n_rx, -1);
+  for (int a = 0; a < p.Nu; ++a) tx_pos[tx_used[a]] = a;
+  for (int a = 0; a < p.Mu; ++a) rx_pos[rx_used[a]] = a;
+  p.compression = (double)p.L / (double)p.Mu;
+
+  Blob blob;
+  size_t off_tw, off_rw;
+  fill_fft(p, blob, off_tw, off_rw);
+  std::vector<int32_t> txu(tx_used.begin(), tx_used.end());
+  const size_t off_txu = blob.add(txu);
+
+  // shear phases: frac(fs delta_l(theta_o) / T), delta = (x_ref - u_l) sin(theta_o) / c
+  std::vector<unsigned long long> phase((size_t)p.Mu * p.L);
+  for (int a = 0; a < p.Mu; ++a) {
+    const double th = d->rx_angles[rx_used[a]];
+    const double xr = shear_reference(u, th);
+    for (int l = 0; l < p.L; ++l) {
+      const double D = d->fs * (xr - u[l]) * std::sin(th) / d->c;  // samples
+      phase[(size_t)a * p.L + l] = frac64(D / (double)p.T);
+    }
+  }
+  const size_t off_phase = blob.add(phase);
+
+  std::vector<int32_t> pair_q(P);
+  for (int q = 0; q < P; ++q)
+    pair_q[q] = tx_pos[d->pairs[2 * q]] * p.Mu + rx_pos[d->pairs[2 * q + 1]];
+  const size_t off_pq = blob.add(pair_q);
+
+  // gather tables, pairs stably sorted by group
+  std::vector<int> order(P);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return gp[a] < gp[b]; });
+  p.h_group_start.assign(J + 1, 0);
+  for (int q = 0; q < P; ++q) p.h_group_start[gp[q] + 1]++;
+  for (int g = 0; g < J; ++g) p.h_group_start[g + 1] += p.h_group_start[g];
+  std::vector<int32_t> row(P);
+  std::vector<long long> A(P), Bv(P), C(P);
+  std::vector<float> Af(P), Bf(P);
+  const kk_grid &g = p.grid;
+  const double k_s = d->fs / d->c;
+  double span = 0;
+  for (int s = 0; s < P; ++s) {
+    const int q = order[s];
+    const double ti = d->tx_angles[d->pairs[2 * q]];
+    const double to = d->rx_angles[d->pairs[2 * q + 1]];
+    const double xr = shear_reference(u, to);
+    const double sx = std::sin(ti) + std::sin(to);
+    const double cz = std::cos(ti) + std::cos(to);
+    const double a = k_s * g.dx * sx;
+    const double b = k_s * g.dz * cz;
+    const double c0 = k_s * (g.x0 * sx + g.z0 * cz - xr * std::sin(to));
+    row[s] = q;
+    A[s] = to_fixed32(a);
+    Bv[s] = to_fixed32(b);
+    C[s] = to_fixed32(c0);
+    Af[s] = (float)a;
+    Bf[s] = (float)b;
+    span = std::max(span, (std::fabs(a) * (kTileX - 1) + b * (kTileZ - 1)));
+  }
+  const size_t off_row = blob.add(row), off_A = blob.add(A), off_B = blob.add(Bv), off_C = blob.add(C);
+  const size_t off_Af = blob.add(Af), off_Bf = blob.add(Bf);
+  std::vector<int32_t> gs(p.h_group_start.begin(), p.h_group_start.end());
+  const size_t off_gs = blob.add(gs);
+
+  p.bf_win = (int)std::ceil(span) + 4;
+  p.bf_stage = choose_stage(p.bf_win);
+  p.tiles_x = (g.nx + kTileX - 1) / kTileX;
+  p.tiles_z = (g.nz + kTileZ - 1) / kTileZ;
+  // split the pair list so the grid covers the GPU (~4 CTAs per SM), keeping
+  // >= 2 stages of work per slice
+  int sms = 148;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p.device);
+  const int tiles = p.tiles_x * p.tiles_z;
+  int split = (4 * sms + tiles - 1) / tiles;
+  int max_by_pairs = std::max(1, (P / J) / (2 * p.bf_stage));
+  p.bf_split = std::max(1, std::min(split, max_by_pairs));
+
+  // workspace: X [F][Nu][L], Y [F][Nu][Mu], partial images
+  size_t off = 0;
+  p.ws_X = off;
+  off = align_up(off + sizeof(float2) * (size_t)p.F * p.Nu * p.L);
+  p.ws_Y = off;
+  off = align_up(off + sizeof(float2) * (size_t)p.F * p.Nu * p.Mu);
+  p.ws_part = off;
+  if (p.bf_split > 1) off = align_up(off + sizeof(float2) * (size_t)p.bf_split * J * g.nx * g.nz);
+  p.ws_total = off;
+
+  kk_status st = upload(p, blob);
+  if (st != KK_OK) return st;
+  void *b = p.dev_block;
+  p.t.fft_tw = at<float2>(b, off_tw);
+  p.t.rfft_w = at<float2>(b, off_rw);
+  p.t.tx_used = at<int32_t>(b, off_txu);
+  p.t.phase = at<unsigned long long>(b, off_phase);
+  p.t.pair_q = at<int32_t>(b, off_pq);
+  p.t.bf_row = at<int32_t>(b, off_row);
+  p.t.bf_A = at<long long>(b, off_A);
+  p.t.bf_B = at<long long>(b, off_B);
+  p.t.bf_C = at<long long>(b, off_C);
+  p.t.bf_Af = at<float>(b, off_Af);
+  p.t.bf_Bf = at<float>(b, off_Bf);
+  p.t.group_start = at<int32_t>(b, off_gs);
+  return KK_OK;
+}
+
+kk_status make_das(kk_plan &p, const kk_plan_desc *d) {
+  p.is_das = true;
+  p.J = 1;
+  p.P = p.N * p.L;
+  p.Nu = p.N;
+  p.Mu = 0;
+  p.compound = KK_COMPOUND_NONE;
+  p.precision = KK_PREC_F32;
+  p.compression = 1.0;
+  Blob blob;
+  size_t off_tw, off_rw;
+  fill_fft(p, blob, off_tw, off_rw);
+  std::vector<int32_t> txu(p.N);
+  std::iota(txu.begin(), txu.end(), 0);
+  const size_t off_txu = blob.add(txu);
+  const kk_grid &g = p.grid;
+  const double k_s = d->fs / d->c;
+  std::vector<long long> A(p.N), Bv(p.N), C(p.N);
+  std::vector<float> Af(p.N), Bf(p.N);
+  double span_in = 0;
+  for (int i = 0; i < p.N; ++i) {
+    const double th = d->tx_angles[i];
+    const double a = k_s * g.dx * std::sin(th), b = k_s * g.dz * std::cos(th);
+    const double c0 = k_s * (g.x0 * std::sin(th) + g.z0 * std::cos(th));
+    A[i] = to_fixed32(a);
+    Bv[i] = to_fixed32(b);
+    C[i] = to_fixed32(c0);
+    Af[i] = (float)a;
+    Bf[i] = (float)b;
+    span_in = std::max(span_in, std::fabs(a) * (kTileX - 1) + b * (kTileZ - 1));
+  }
+  p.tiles_x = (g.nx + kTileX - 1) / kTileX;
+  p.tiles_z = (g.nz + kTileZ - 1) / kTileZ;
+  auto split_df = [](double v) {
+    const float hi = (float)v;
+    return make_float2(hi, (float)(v - (double)hi));
+  };
+  std::vector<float2> xs(p.tiles_x * kTileX), zs(p.tiles_z * kTileZ), us(p.L);
+  for (size_t k = 0; k < xs.size(); ++k) xs[k] = split_df(k_s * (g.x0 + g.dx * (double)k));
+  for (size_t k = 0; k < zs.size(); ++k) zs[k] = split_df(k_s * (g.z0 + g.dz * (double)k));
+  for (int l = 0; l < p.L; ++l) us[l] = split_df(k_s * d->elem_x[l]);
+  const size_t off_A = blob.add(A), off_B = blob.add(Bv), off_C = blob.add(C);
+  const size_t off_Af = blob.add(Af), off_Bf = blob.add(Bf);
+  const size_t off_xs = blob.add(xs), off_zs = blob.add(zs), off_us = blob.add(us);
+  const double span_out = k_s * (g.dx * (kTileX - 1) + g.dz * (kTileZ - 1));
+  p.bf_win = (int)std::ceil(span_in + span_out) + 6;
+  p.bf_stage = choose_stage(p.bf_win);
+  p.bf_split = 1;
+  // workspace: X [F][N*L], analytic channels y [N*L][T]
+  size_t off = 0;
+  p.ws_X = off;
+  off = align_up(off + sizeof(float2) * (size_t)p.F * p.N * p.L);
+  p.ws_Y = off;
+  off = align_up(off + sizeof(float2) * (size_t)p.N * p.L * p.T);
+  p.ws_part = off;
+  p.ws_total = off;
+  kk_status st = upload(p, blob);
+  if (st != KK_OK) return st;
+  void *b = p.dev_block;
+  p.t.fft_tw = at<float2>(b, off_tw);
+  p.t.rfft_w = at<float2>(b, off_rw);
+  p.t.tx_used = at<int32_t>(b, off_txu);
+  p.t.das_A = at<long long>(b, off_A);
+  p.t.das_B = at<long long>(b, off_B);
+  p.t.das_C = at<long long>(b, off_C);
+  p.t.das_Af = at<float>(b, off_Af);
+  p.t.das_Bf = at<float>(b, off_Bf);
+  p.t.xs = at<float2>(b, off_xs);
+  p.t.zs = at<float2>(b, off_zs);
+  p.t.us = at<float2>(b, off_us);
+  return KK_OK;
+}
+
+kk_status create(kk_plan **out, const kk_plan_desc *d, bool das) {
+  if (!out) { set_error("null output pointer"); return KK_ERR_INVALID_ARG; }
+  *out = nullptr;
+  kk_status st = validate_common(d);
+  if (st != KK_OK) return st;
+  DeviceGuard guard(d->device);
+  if (!guard.ok) { set_error("cudaSetDevice failed"); return KK_ERR_CUDA; }
+  kk_plan *p = new (std::nothrow) kk_plan();
+  if (!p) { set_error("host allocation failed"); return KK_ERR_OOM; }
+  p->device = d->device;
+  p->L = d->n_elem;
+  p->N = d->n_tx;
+  p->T = d->n_samples;
+  p->F = d->n_samples / 2;
+  p->grid = d->grid;
+  p->c = d->c;
+  p->fs = d->fs;
+  p->rf_dtype = d->rf_dtype;
+  try {
+    st = das ? make_das(*p, d) : make_kk(*p, d);
+  } catch (const std::bad_alloc &) {
+    set_error("host allocation failed");
+    st = KK_ERR_OOM;
+  } catch (...) {
+    set_error("unexpected host exception in plan creation");
+    st = KK_ERR_INVALID_ARG;
+  }
+  if (st != KK_OK) {
+    if (p->dev_block) cudaFree(p->dev_block);
+    delete p;
+    return st;
+  }
+  *out = p;
+  return KK_OK;
+}
+
+kk_status check_plan(const kk_plan *p, bool want_das) {
+  if (!p) { set_error("null plan"); return KK_ERR_INVALID_ARG; }
+  if (p->is_das != want_das) { set_error(want_das ? "expected a DAS plan" : "expected a KK plan"); return KK_ERR_INVALID_ARG; }
+  return KK_OK;
+}
+
+bool aligned(const void *ptr, size_t a) { return ((uintptr_t)ptr % a) == 0; }
+
+kk_status enqueue_decompose(const kk_plan *p, const void *rf, void *rf_theta, void *ws, cudaStream_t s) {
+  float2 *X = at<float2>(ws, p->ws_X);
+  float2 *Y = at<float2>(ws, p->ws_Y);
+  cudaError_t e = launch_spectrum(*p, rf, X, p->Nu, p->t.tx_used, s);
+  if (e != cudaSuccess) return cuda_fail(e, "spectrum launch");
+  e = launch_shear_f32(*p, X, Y, s);
+  if (e != cudaSuccess) return cuda_fail(e, "shear launch");
+  e = launch_inverse(*p, Y, p->Nu * p->Mu, p->t.pair_q, p->P, (float2 *)rf_theta, s);
+  if (e != cudaSuccess) return cuda_fail(e, "inverse launch");
+  return KK_OK;
+}
+
+kk_status enqueue_beamform(const kk_plan *p, const void *rf_theta, void *B, float *I, void *ws, cudaStream_t s) {
+  float2 *part = (p->bf_split > 1) ? at<float2>(ws, p->ws_part) : nullptr;
+  cudaError_t e = launch_kk_gather(*p, (const float2 *)rf_theta, (float2 *)B, I, part, s);
+  if (e != cudaSuccess) return cuda_fail(e, "kk gather launch");
+  return KK_OK;
+}
+
+kk_status enqueue_das(const kk_plan *p, const void *rf, void *B, float *I, void *ws, cudaStream_t s) {
+  float2 *X = at<float2>(ws, p->ws_X);
+  float2 *y = at<float2>(ws, p->ws_Y);
+  cudaError_t e = launch_spectrum(*p, rf, X, p->N, p->t.tx_used, s);
+  if (e != cudaSuccess) return cuda_fail(e, "spectrum launch");
+  e = launch_inverse(*p, X, p->N * p->L, nullptr, p->N * p->L, y, s);
+  if (e != cudaSuccess) return cuda_fail(e, "inverse launch");
+  e = launch_das_gather(*p, y, (float2 *)B, I, s);
+  if (e != cudaSuccess) return cuda_fail(e, "das gather launch");
+  return KK_OK;
+}
+
+}  // namespace
+}  // namespace kk
+
+using namespace kk;
+
+extern "C" {
+
+const char *kk_last_error(void) { return g_err.c_str(); }
+
+const char *kk_version(void) { return "kkbeam 0.1 (sm_103a)"; }
+
+kk_status kk_plan_create(kk_plan **out, const kk_plan_desc *d) { return create(out, d, false); }
+
+kk_status das_plan_create(kk_plan **out, const kk_plan_desc *d) { return create(out, d, true); }
+
+void kk_plan_destroy(kk_plan *p) {
+  if (!p) return;
+  if (p->dev_block) {
+    DeviceGuard guard(p->device);
+    cudaFree(p->dev_block);
+  }
+  delete p;
+}
+
+kk_status kk_plan_workspace_size(const kk_plan *p, size_t *bytes) {
+  if (!p || !bytes) { set_error("null argument"); return KK_ERR_INVALID_ARG; }
+  *bytes = p->ws_total;
+  return KK_OK;
+}
+
+kk_status kk_plan_get_info(const kk_plan *p, kk_plan_info *info) {
+  if (!p || !info) { set_error("null argument"); return KK_ERR_INVALID_ARG; }
+  std::memset(info, 0, sizeof(*info));
+  info->n_elem = p->L;
+  info->n_tx = p->N;
+  info->n_samples = p->T;
+  info->n_bins = p->F;
+  info->n_tx_used = p->Nu;
+  info->n_rx_used = p->Mu;
+  info->n_pairs = p->P;
+  info->n_groups = p->J;
+  info->nx = p->grid.nx;
+  info->nz = p->grid.nz;
+  info->is_das = p->is_das ? 1 : 0;
+  info->workspace_bytes = p->ws_total;
+  info->rf_bytes = (size_t)p->N * p->L * p->T * (p->rf_dtype == KK_RF_I16 ? 2 : 4);
+  info->rf_theta_bytes = p->is_das ? 0 : (size_t)p->P * p->T * 8;
+  info->image_bytes = (size_t)p->J * p->grid.nx * p->grid.nz * 8;
+  info->intensity_bytes = (size_t)p->grid.nx * p->grid.nz * 4;
+  info->compression_factor = p->compression;
+  info->launches_decompose = p->is_das ? 0 : 3;
+  info->launches_beamform = p->is_das ? 3 : (p->bf_split > 1 ? 2 : 1);
+  return KK_OK;
+}
+
+kk_status kk_decompose(const kk_plan *p, const void *d_rf, void *d_rf_theta, void *d_ws, void *stream) {
+  kk_status st = check_plan(p, false);
+  if (st != KK_OK) return st;
+  if (!d_rf || !d_rf_theta || !d_ws) { set_error("null buffer"); return KK_ERR_INVALID_ARG; }
+  if (!aligned(d_rf, 16) || !aligned(d_rf_theta, 16) || !aligned(d_ws, kAlign)) { set_error("buffers must be 16-byte aligned (workspace 256)"); return KK_ERR_INVALID_ARG; }
+  DeviceGuard guard(p->device);
+  return enqueue_decompose(p, d_rf, d_rf_theta, d_ws, (cudaStream_t)stream);
+}
+
+kk_status kk_spectrum(const kk_plan *p, const void *d_rf, void *d_X, void *stream) {
+  kk_status st = check_plan(p, false);
+  if (st != KK_OK) return st;
+  if (!d_rf || !d_X) { set_error("null buffer"); return KK_ERR_INVALID_ARG; }
+  DeviceGuard guard(p->device);
+  cudaError_t e = launch_spectrum(*p, d_rf, (float2 *)d_X, p->Nu, p->t.tx_used, (cudaStream_t)stream);
+  return e == cudaSuccess ? KK_OK : cuda_fail(e, "spectrum launch");
+}
+
+kk_status kk_shear(const kk_plan *p, const void *d_X, void *d_Y, void *stream) {
+  kk_status st = check_plan(p, false);
+  if (st != KK_OK) return st;
+  if (!d_X || !d_Y) { set_error("null buffer"); return KK_ERR_INVALID_ARG; }
+  DeviceGuard guard(p->device);
+  cudaError_t e = launch_shear_f32(*p, (const float2 *)d_X, (float2 *)d_Y, (cudaStream_t)stream);
+  return e == cudaSuccess ? KK_OK : cuda_fail(e, "shear launch");
+}
+
+kk_status kk_inverse(const kk_plan *p, const void *d_Y, void *d_rf_theta, void *stream) {
+  kk_status st = check_plan(p, false);
+  if (st != KK_OK) return st;
+  if (!d_Y || !d_rf_theta) { set_error("null buffer"); return KK_ERR_INVALID_ARG; }
+  if (!aligned(d_rf_theta, 16)) { set_error("rf_theta must be 16-byte aligned"); return KK_ERR_INVALID_ARG; }
+  DeviceGuard guard(p->device);
+  cudaError_t e = launch_inverse(*p, (const float2 *)d_Y, p->Nu * p->Mu, p->t.pair_q, p->P,
+                                 (float2 *)d_rf_theta, (cudaStream_t)stream);
+  return e == cudaSuccess ? KK_OK : cuda_fail(e, "inverse launch");
+}
+
+kk_status kk_beamform(const kk_plan *p, const void *d_rf_theta, void *d_B, float *d_I, void *d_ws, void *stream) {
+  kk_status st = check_plan(p, false);
+  if (st != KK_OK) return st;
+  if (!d_rf_theta || !d_B) { set_error("null buffer"); return KK_ERR_INVALID_ARG; }
+  if (p->compound != KK_COMPOUND_NONE && !d_I) { set_error("compound mode set but I is null"); return KK_ERR_INVALID_ARG; }
+  if (p->bf_split > 1 && !d_ws) { set_error("workspace required"); return KK_ERR_INVALID_ARG; }
+  DeviceGuard guard(p->device);
+  return enqueue_beamform(p, d_rf_theta, d_B, d_I, d_ws, (cudaStream_t)stream);
+}
+
+kk_status das_beamform(const kk_plan *p, const void *d_rf, void *d_B, float *d_I, void *d_ws, void *stream) {
+  kk_status st = check_plan(p, true);
+  if (st != KK_OK) return st;
+  if (!d_rf || !d_B || !d_ws) { set_error("null buffer"); return KK_ERR_INVALID_ARG; }
+  if (!aligned(d_rf, 16) || !aligned(d_ws, kAlign)) { set_error("buffers must be 16-byte aligned (workspace 256)"); return KK_ERR_INVALID_ARG; }
+  DeviceGuard guard(p->device);
+  return enqueue_das(p, d_rf, d_B, d_I, d_ws, (cudaStream_t)stream);
+}
+
+kk_status kk_run_host_scratch_size(const kk_plan *p, size_t *bytes) {
+  if (!p || !bytes) { set_error("null argument"); return KK_ERR_INVALID_ARG; }
+  kk_plan_info info;
+  kk_plan_get_info(p, &info);
+  size_t off = align_up(info.rf_bytes);
+  off += align_up(info.rf_theta_bytes);
+  off += align_up(info.image_bytes);
+  off += align_up(info.intensity_bytes);
+  off += align_up(p->ws_total);
+  *bytes = off;
+  return KK_OK;
+}
+
+kk_status kk_run_host(const kk_plan *p, const void *h_rf, void *h_B, float *h_I, void *d_scratch, void *stream) {
+  if (!p || !h_rf || !h_B || !d_scratch) { set_error("null argument"); return KK_ERR_INVALID_ARG; }
+  if (!aligned(d_scratch, kAlign)) { set_error("scratch must be 256-byte aligned"); return KK_ERR_INVALID_ARG; }
+  kk_plan_info info;
+  kk_plan_get_info(p, &info);
+  unsigned char *base = (unsigned char *)d_scratch;
+  size_t off = 0;
+  void *d_rf = base + off; off += align_up(info.rf_bytes);
+  void *d_rt = base + off; off += align_up(info.rf_theta_bytes);
+  void *d_B = base + off; off += align_up(info.image_bytes);
+  float *d_I = (float *)(base + off); off += align_up(info.intensity_bytes);
+  void *d_ws = base + off;
+  DeviceGuard guard(p->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = cudaMemcpyAsync(d_rf, h_rf, info.rf_bytes, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return cuda_fail(e, "rf upload");
+  const bool want_I = p->is_das || p->compound != KK_COMPOUND_NONE;
+  kk_status st;
+  if (p->is_das) {
+    st = enqueue_das(p, d_rf, d_B, want_I ? d_I : nullptr, d_ws, s);
+  } else {
+    st = enqueue_decompose(p, d_rf, d_rt, d_ws, s);
+    if (st == KK_OK) st = enqueue_beamform(p, d_rt, d_B, want_I ? d_I : nullptr, d_ws, s);
+  }
+  if (st != KK_OK) return st;
+  e = cudaMemcpyAsync(h_B, d_B, info.image_bytes, cudaMemcpyDeviceToHost, s);
+  if (e != cudaSuccess) return cuda_fail(e, "image download");
+  if (h_I && want_I) {
+    e = cudaMemcpyAsync(h_I, d_I, info.intensity_bytes, cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return cuda_fail(e, "intensity download");
+  }
+  return KK_OK;
+}
+
+kk_status kk_scheme_angles(int32_t kind, int32_t n_tx, const double *tx, double dtheta, int32_t M,
+                           double j, double *out_rx) {
+  if (!out_rx || M < 1) { set_error("M < 1 or null output"); return KK_ERR_INVALID_ARG; }
+  if (kind == KK_SCHEME_SAME) {
+    if (!tx || M != n_tx) { set_error("SAME scheme needs tx and M == n_tx"); return KK_ERR_INVALID_ARG; }
+    for (int m = 0; m < M; ++m) out_rx[m] = tx[m];
+    return KK_OK;
+  }
+  if (!(dtheta > 0) || !std::isfinite(dtheta)) { set_error("dtheta must be positive"); return KK_ERR_INVALID_ARG; }
+  const int half = n_tx / 2;
+  if (kind == KK_SCHEME_CONFOCAL && half < 1) { set_error("confocal scheme needs floor(n_tx/2) >= 1"); return KK_ERR_INVALID_ARG; }
+  if (kind != KK_SCHEME_VERNIER && kind != KK_SCHEME_SHIFTED && kind != KK_SCHEME_CONFOCAL) {
+    set_error("unknown scheme");
+    return KK_ERR_INVALID_ARG;
+  }
+  for (int m = 0; m < M; ++m) {
+    const double o = (double)m - 0.5 * (double)(M - 1);   // receive index, Section II-C
+    const double ao = std::fabs(o);
+    const double sg = (o > 0) ? 1.0 : (o < 0 ? -1.0 : 0.0);
+    double shift = 0.0;
+    if (kind == KK_SCHEME_SHIFTED) shift = j;                           // Eq. (uniform)
+    if (kind == KK_SCHEME_CONFOCAL) shift = std::fmod(std::floor(ao), (double)half);  // Eq. (confocal)
+    out_rx[m] = sg * dtheta * (2.0 * ao / (double)M + shift);
+  }
+  return KK_OK;
+}
+
+}  // extern "C"

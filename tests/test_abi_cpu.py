@@ -1,0 +1,90 @@
+"""CPU checks of the C-ABI library: it builds for sm_103a, loads, exports
+every symbol the header declares, and its host-only logic is right.  No
+compute call is made (there may be no GPU here)."""
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+import paper_2603_22496_gb300 as kb
+from paper_2603_22496_gb300 import build as kbuild
+from oracle import schemes
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(__file__)), "include", "kkbeam.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    kbuild.build()
+    return kb.load()
+
+
+def _declared():
+    txt = open(HEADER).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(kk_\w+|das_\w+)\s*\(", txt)))
+
+
+def test_library_exports_every_declared_symbol(lib):
+    declared = _declared()
+    assert len(declared) >= 15
+    out = subprocess.run(["nm", "-D", "--defined-only", kb.library_path()],
+                         capture_output=True, text=True, check=True).stdout
+    exported = set(re.findall(r"\s[TW]\s+(\S+)", out))
+    missing = [s for s in declared if s not in exported]
+    assert not missing, missing
+    assert sorted(kb.EXPORTS) == declared
+    for s in declared:
+        assert hasattr(lib, s)
+
+
+def test_build_targets_sm103a_only():
+    assert kbuild.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def test_version_string(lib):
+    assert "sm_103a" in kb.kk_version()
+
+
+@pytest.mark.parametrize("kind,M,j", [("vernier", 11, 0), ("vernier", 16, 0), ("shifted", 15, 3),
+                                      ("shifted", 7, 7), ("confocal", 15, 0), ("confocal", 21, 0),
+                                      ("confocal", 16, 0)])
+def test_scheme_angles_match_oracle(lib, kind, M, j):
+    N = 15
+    tx = np.deg2rad(np.linspace(-12, 12, N))
+    dth = schemes.transmit_spacing(tx)
+    ref = {"vernier": lambda: schemes.rx_vernier(dth, M),
+           "shifted": lambda: schemes.rx_shifted(dth, M, j),
+           "confocal": lambda: schemes.rx_confocal(dth, M, N)}[kind]()
+    got = kb.kk_scheme_angles({"vernier": kb.KK_SCHEME_VERNIER, "shifted": kb.KK_SCHEME_SHIFTED,
+                               "confocal": kb.KK_SCHEME_CONFOCAL}[kind], N, dth, M, j)
+    assert np.abs(got - ref).max() <= 1e-15
+
+
+def test_scheme_angles_rejects_bad_arguments(lib):
+    with pytest.raises(kb.KKError) as e:
+        kb.kk_scheme_angles(kb.KK_SCHEME_VERNIER, 5, 0.01, 0)
+    assert e.value.status == kb.KK_ERR_INVALID_ARG
+    with pytest.raises(kb.KKError):
+        kb.kk_scheme_angles(kb.KK_SCHEME_CONFOCAL, 1, 0.01, 5)    # floor(N/2) = 0
+    with pytest.raises(kb.KKError):
+        kb.kk_scheme_angles(kb.KK_SCHEME_SAME, 3, 0.0, 4, tx=np.zeros(3))
+    with pytest.raises(kb.KKError):
+        kb.kk_scheme_angles(99, 5, 0.01, 5)
+
+
+def test_plan_validation_is_host_side(lib):
+    """Argument errors are reported before any device work."""
+    d, keep = kb._desc(np.zeros(4), np.zeros(2), (8, 8, 0.0, 1e-4, 1e-3, 1e-4), 1540.0, 20e6,
+                       100, kb.KK_RF_F32, rx_angles=np.zeros(1), pairs=[[0, 0]])
+    with pytest.raises(kb.KKError) as e:          # T/2 = 50 is not a supported FFT length
+        kb.kk_plan_create(d)
+    assert e.value.status in (kb.KK_ERR_UNSUPPORTED, kb.KK_ERR_INVALID_ARG)
+    d, keep = kb._desc(np.zeros(4), np.array([1.5]), (8, 8, 0.0, 1e-4, 1e-3, 1e-4), 1540.0, 20e6,
+                       256, kb.KK_RF_F32, rx_angles=np.zeros(1), pairs=[[0, 0]])
+    with pytest.raises(kb.KKError) as e:          # 86 degree transmit
+        kb.kk_plan_create(d)
+    assert e.value.status == kb.KK_ERR_INVALID_ARG
+    assert kb.load().kk_last_error()
