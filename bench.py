@@ -40,6 +40,9 @@ def _args():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--quick", action="store_true", help="skip the side measurements")
+    ap.add_argument("--profile", default=None, choices=["kk_image", "decompose", "das", "vernier"],
+                    help="run three launches of one stage of the benchmark frame and exit "
+                         "(a small, bounded target for ncu)")
     return ap.parse_args()
 
 
@@ -379,16 +382,71 @@ def _oracle_frame_seconds(w, rx, pairs, rx_keep, rows):
     return t_dec_frame + t_bf * (nz / rows), t_dec, t_bf
 
 
+def run_profile(args):
+    """Three launches of one stage on the benchmark frame (~0.4 GB on the device)."""
+    import torch
+    from paper_2603_22496_gb300 import build as kbuild
+    kbuild.build()
+    import paper_2603_22496_gb300 as kb
+    kb.load()
+    w = _workload(0)
+    d_rf = torch.from_numpy(w.rf).cuda()
+    if args.profile == "das":
+        dplan = kb.Plan(w.elem_x, w.tx_angles, w.grid, w.c, w.fs, w.n_samples, kb.KK_RF_I16, das=True)
+        ws, B, I = dplan.empty_workspace(), dplan.empty_image(), dplan.empty_intensity()
+        for _ in range(3):
+            dplan.das(d_rf, B, I, ws)
+    else:
+        rx, pairs = _vernier_pairs(w, kb) if args.profile == "vernier" else _full_pairs(w)
+        plan = kb.Plan(w.elem_x, w.tx_angles, w.grid, w.c, w.fs, w.n_samples, kb.KK_RF_I16,
+                       rx_angles=rx, pairs=pairs, compound=kb.KK_COMPOUND_COHERENT)
+        ws, rt, B, I = plan.empty_workspace(), plan.empty_rf_theta(), plan.empty_image(), plan.empty_intensity()
+        plan.decompose(d_rf, rt, ws)
+        for _ in range(3):
+            if args.profile in ("decompose", "vernier"):
+                plan.decompose(d_rf, rt, ws)
+            if args.profile in ("kk_image", "vernier"):
+                plan.beamform(rt, B, I, ws)
+    torch.cuda.synchronize()
+    print(f"profile target {args.profile}: done")
+
+
+def _gpu_rows_vs_oracle(w, rx, pairs, rows):
+    """rel-L2 of the GPU image's first `rows` rows against the FP64 oracle."""
+    import numpy as np
+    import torch
+    import paper_2603_22496_gb300 as kb
+    from oracle import kk, schemes
+    plan = kb.Plan(w.elem_x, w.tx_angles, w.grid, w.c, w.fs, w.n_samples, kb.KK_RF_I16,
+                   rx_angles=rx, pairs=pairs)
+    ws, rt, B = plan.empty_workspace(), plan.empty_rf_theta(), plan.empty_image()
+    plan.decompose(torch.from_numpy(w.rf).cuda(), rt, ws)
+    plan.beamform(rt, B, None, ws)
+    torch.cuda.synchronize()
+    g = B[0, :rows].cpu().numpy().astype(np.float64)
+    g = g[..., 0] + 1j * g[..., 1]
+    ps = schemes.PairSet(w.tx_angles, rx, pairs[:, 0].astype(np.int64),
+                         pairs[:, 1].astype(np.int64), np.zeros(pairs.shape[0], np.int64), 1)
+    pix = np.array([(ix, iz) for iz in range(rows) for ix in range(w.grid[0])])
+    ref = kk.kk_image(w.rf, w.elem_x, ps, w.grid, w.fs, w.c, pixels=pix)[0]
+    return kk.rel_l2(g.ravel(), ref)
+
+
 def cpu_baseline(w, rx, pairs):
     import numpy as np
     cores = os.cpu_count()
     rx_keep = np.arange(128)                          # the whole decomposition
     rows = 32
     sec, t_dec, t_bf = _oracle_frame_seconds(w, rx, pairs, rx_keep, rows)
-    return {"value": round(1.0 / sec, 5), "unit": UNIT, "cores": cores, "kind": "oracle",
+    out = {"value": round(1.0 / sec, 5), "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"FP64 oracle: decomposition of all 9600 pairs "
                       f"({t_dec:.2f} s) and image formation of {rows}/512 rows over all 9600 pairs "
                       f"({t_bf:.2f} s), scaled to one frame"}
+    try:
+        out["gpu_rel_l2_first_32_rows"] = _gpu_rows_vs_oracle(w, rx, pairs, 32)
+    except Exception as e:  # pragma: no cover - report, do not hide
+        out["gpu_rel_l2_first_32_rows"] = f"error: {e}"
+    return out
 
 
 def run_reference(args):
@@ -425,7 +483,9 @@ def run_reference(args):
 
 if __name__ == "__main__":
     a = _args()
-    if a.impl == "reference":
+    if a.profile:
+        run_profile(a)
+    elif a.impl == "reference":
         run_reference(a)
     else:
         run_ours(a)

@@ -128,9 +128,21 @@ def _check(status: int):
 
 
 def _ptr(t) -> ctypes.c_void_p:
-    """Device pointer of a torch tensor (None -> NULL)."""
+    """Device pointer of a contiguous CUDA torch tensor (None -> NULL)."""
     if t is None:
         return ctypes.c_void_p(0)
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous (the C ABI takes dense row-major buffers)")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _host_ptr(t) -> ctypes.c_void_p:
+    if t is None:
+        return ctypes.c_void_p(0)
+    if t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous host tensor")
     return ctypes.c_void_p(t.data_ptr())
 
 
@@ -249,8 +261,7 @@ def kk_run_host_scratch_size(h) -> int:
 
 def kk_run_host(h, h_rf, h_B, h_I, scratch, stream=None):
     """h_rf/h_B/h_I: CPU tensors (pinned for asynchronous copies)."""
-    _check(load().kk_run_host(h, ctypes.c_void_p(h_rf.data_ptr()), ctypes.c_void_p(h_B.data_ptr()),
-                              ctypes.c_void_p(h_I.data_ptr()) if h_I is not None else None,
+    _check(load().kk_run_host(h, _host_ptr(h_rf), _host_ptr(h_B), _host_ptr(h_I),
                               _ptr(scratch), _stream(stream)))
 
 

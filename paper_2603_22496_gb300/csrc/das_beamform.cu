@@ -61,7 +61,7 @@ __global__ void __launch_bounds__(kGatherThreads)
                  const float *__restrict__ dAf, const float *__restrict__ dBf,
                  const float2 *__restrict__ xs, const float2 *__restrict__ zs,
                  const float2 *__restrict__ us, int nx, int nz, int tiles_x, int win, int stage,
-                 float2 *__restrict__ B, float *__restrict__ I) {
+                 int split, float2 *__restrict__ B, float *__restrict__ I) {
   extern __shared__ float4 sw[];
   __shared__ WarpChan s_wc[4][kMaxStage];
   __shared__ float2 s_ab[kMaxStage];
@@ -88,7 +88,9 @@ __global__ void __launch_bounds__(kGatherThreads)
 #pragma unroll
   for (int r = 0; r < kRowsPerThread; ++r) acc[r] = make_float2(0.f, 0.f);
 
-  for (int l = 0; l < L; ++l) {
+  const int sidx = blockIdx.y;
+  const int lb = (int)(((long long)L * sidx) / split), le = (int)(((long long)L * (sidx + 1)) / split);
+  for (int l = lb; l < le; ++l) {
     const float2 u = __ldg(us + l);
     // receive delay of this thread's pixels: integer part (x16 bytes) + fraction
     const float2 dx2 = df_sqr(df_sub(xq, u));
@@ -133,16 +135,19 @@ __global__ void __launch_bounds__(kGatherThreads)
         }
       }
       __syncthreads();
-      for (int e = tid; e < ns * win; e += kGatherThreads) {
-        const int j = e / win, m = e - j * win;
-        const int k = s_w0[j] + m;
-        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (k >= 0 && k <= T - 2) {
-          const float2 *yr = y + (size_t)s_row[j] * T;
-          const float2 a = __ldg(yr + k), b = __ldg(yr + k + 1);
-          v = make_float4(a.x, a.y, b.x - a.x, b.y - a.y);
+      for (int j = warp; j < ns; j += kGatherThreads / 32) {
+        const int w0 = s_w0[j];
+        const float2 *yr = y + (size_t)s_row[j] * T;
+        float4 *dst = sw + j * win;
+        for (int m = lane; m < win; m += 32) {
+          const int k = w0 + m;
+          float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+          if ((unsigned)k <= (unsigned)(T - 2)) {
+            const float2 a = __ldg(yr + k), b = __ldg(yr + k + 1);
+            v = make_float4(a.x, a.y, b.x - a.x, b.y - a.y);
+          }
+          dst[m] = v;
         }
-        sw[e] = v;
       }
       __syncthreads();
       float2 sacc[kRowsPerThread];
@@ -171,26 +176,48 @@ __global__ void __launch_bounds__(kGatherThreads)
       }
     }
   }
+  // split == 1: final image; otherwise this element slice's partial image
+  float2 *dst = B + (size_t)sidx * nx * nz;
 #pragma unroll
   for (int r = 0; r < kRowsPerThread; ++r) {
     const int iz = izb + r;
     if (ix < nx && iz < nz) {
-      B[(size_t)iz * nx + ix] = acc[r];
-      if (I != nullptr) I[(size_t)iz * nx + ix] = fmaf(acc[r].x, acc[r].x, acc[r].y * acc[r].y);
+      dst[(size_t)iz * nx + ix] = acc[r];
+      if (split == 1 && I != nullptr) I[(size_t)iz * nx + ix] = fmaf(acc[r].x, acc[r].x, acc[r].y * acc[r].y);
     }
   }
+}
+
+// Sum element-slice partials in slice order.
+__global__ void k_das_reduce(const float2 *__restrict__ part, int split, int npix,
+                             float2 *__restrict__ B, float *__restrict__ I) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= npix) return;
+  float2 a = make_float2(0.f, 0.f);
+  for (int s = 0; s < split; ++s) {
+    const float2 v = part[(size_t)s * npix + q];
+    a.x += v.x;
+    a.y += v.y;
+  }
+  B[q] = a;
+  if (I != nullptr) I[q] = fmaf(a.x, a.x, a.y * a.y);
 }
 
 }  // namespace
 
 cudaError_t launch_das_gather(const kk_plan &p, const float2 *y, float2 *B, float *I,
-                              cudaStream_t s) {
+                              float2 *partial, cudaStream_t s) {
   const size_t smem = sizeof(float4) * (size_t)p.bf_stage * p.bf_win;
   cudaFuncSetAttribute(k_das_gather, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  const dim3 grid(p.tiles_x * p.tiles_z);
+  const dim3 grid(p.tiles_x * p.tiles_z, p.bf_split);
   k_das_gather<<<grid, kGatherThreads, smem, s>>>(
       y, p.N, p.L, p.T, p.t.das_A, p.t.das_B, p.t.das_C, p.t.das_Af, p.t.das_Bf, p.t.xs, p.t.zs,
-      p.t.us, p.grid.nx, p.grid.nz, p.tiles_x, p.bf_win, p.bf_stage, B, I);
+      p.t.us, p.grid.nx, p.grid.nz, p.tiles_x, p.bf_win, p.bf_stage, p.bf_split,
+      p.bf_split > 1 ? partial : B, I);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || p.bf_split == 1) return e;
+  const int npix = p.grid.nx * p.grid.nz;
+  k_das_reduce<<<(npix + 255) / 256, 256, 0, s>>>(partial, p.bf_split, npix, B, I);
   return cudaGetLastError();
 }
 

@@ -102,17 +102,20 @@ __global__ void __launch_bounds__(kGatherThreads)
         }
       }
       __syncthreads();
-      // stage windows
-      for (int e = tid; e < ns * win; e += kGatherThreads) {
-        const int j = e / win, m = e - j * win;
-        const int k = s_w0[j] + m;
-        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (k >= 0 && k <= T - 2) {
-          const float2 *y = rf_theta + (size_t)s_row[j] * T;
-          const float2 a = __ldg(y + k), b = __ldg(y + k + 1);
-          v = make_float4(a.x, a.y, b.x - a.x, b.y - a.y);
+      // stage windows: warp w stages pairs w, w+4, ...; lanes walk the window
+      for (int j = warp; j < ns; j += kGatherThreads / 32) {
+        const int w0 = s_w0[j];
+        const float2 *y = rf_theta + (size_t)s_row[j] * T;
+        float4 *dst = sw + j * win;
+        for (int m = lane; m < win; m += 32) {
+          const int k = w0 + m;
+          float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+          if ((unsigned)k <= (unsigned)(T - 2)) {
+            const float2 a = __ldg(y + k), b = __ldg(y + k + 1);
+            v = make_float4(a.x, a.y, b.x - a.x, b.y - a.y);
+          }
+          dst[m] = v;
         }
-        sw[e] = v;
       }
       __syncthreads();
       float2 sacc[kRowsPerThread];

@@ -101,6 +101,6 @@ cudaError_t launch_shear_f32(const kk_plan &p, const float2 *X, float2 *Y, cudaS
 cudaError_t launch_kk_gather(const kk_plan &p, const float2 *rf_theta, float2 *B, float *I,
                              float2 *partial, cudaStream_t s);
 cudaError_t launch_das_gather(const kk_plan &p, const float2 *y, float2 *B, float *I,
-                              cudaStream_t s);
+                              float2 *partial, cudaStream_t s);
 
 }  // namespace kk

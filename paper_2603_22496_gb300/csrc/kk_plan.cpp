@@ -344,14 +344,19 @@ kk_status make_das(kk_plan &p, const kk_plan_desc *d) {
   const double span_out = k_s * (g.dx * (kTileX - 1) + g.dz * (kTileZ - 1));
   p.bf_win = (int)std::ceil(span_in + span_out) + 6;
   p.bf_stage = choose_stage(p.bf_win);
-  p.bf_split = 1;
-  // workspace: X [F][N*L], analytic channels y [N*L][T]
+  // split the element loop so the grid covers the GPU (~4 CTAs per SM)
+  int sms = 148;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p.device);
+  const int tiles = p.tiles_x * p.tiles_z;
+  p.bf_split = std::max(1, std::min((4 * sms + tiles - 1) / tiles, p.L / 4));
+  // workspace: X [F][N*L], analytic channels y [N*L][T], partial images
   size_t off = 0;
   p.ws_X = off;
   off = align_up(off + sizeof(float2) * (size_t)p.F * p.N * p.L);
   p.ws_Y = off;
   off = align_up(off + sizeof(float2) * (size_t)p.N * p.L * p.T);
   p.ws_part = off;
+  if (p.bf_split > 1) off = align_up(off + sizeof(float2) * (size_t)p.bf_split * g.nx * g.nz);
   p.ws_total = off;
   kk_status st = upload(p, blob);
   if (st != KK_OK) return st;
@@ -440,7 +445,8 @@ kk_status enqueue_das(const kk_plan *p, const void *rf, void *B, float *I, void 
   if (e != cudaSuccess) return cuda_fail(e, "spectrum launch");
   e = launch_inverse(*p, X, p->N * p->L, nullptr, p->N * p->L, y, s);
   if (e != cudaSuccess) return cuda_fail(e, "inverse launch");
-  e = launch_das_gather(*p, y, (float2 *)B, I, s);
+  float2 *part = (p->bf_split > 1) ? at<float2>(ws, p->ws_part) : nullptr;
+  e = launch_das_gather(*p, y, (float2 *)B, I, part, s);
   if (e != cudaSuccess) return cuda_fail(e, "das gather launch");
   return KK_OK;
 }
@@ -496,7 +502,7 @@ kk_status kk_plan_get_info(const kk_plan *p, kk_plan_info *info) {
   info->intensity_bytes = (size_t)p->grid.nx * p->grid.nz * 4;
   info->compression_factor = p->compression;
   info->launches_decompose = p->is_das ? 0 : 3;
-  info->launches_beamform = p->is_das ? 3 : (p->bf_split > 1 ? 2 : 1);
+  info->launches_beamform = (p->is_das ? 2 : 0) + (p->bf_split > 1 ? 2 : 1);
   return KK_OK;
 }
 

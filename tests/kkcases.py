@@ -54,7 +54,7 @@ def scheme_both(kind, tx_angles, M, j=0, tx_subset=None, js=None):
 
 def to_dev(a, device="cuda:0"):
     import torch
-    return torch.from_numpy(np.ascontiguousarray(a)).to(device)
+    return torch.from_numpy(np.ascontiguousarray(a)).to(device).contiguous()
 
 
 def cplx(t):

@@ -46,7 +46,7 @@ def test_stage_shear_matches_oracle():
     plan = kc.kk_plan_for(w, rx, pairs, grp, J)
     Xo = kk.analytic_spectrum(w.rf)                                   # [N][L][F]
     Xf = np.transpose(Xo, (2, 0, 1)).astype(np.complex64)             # [F][N][L]
-    X = torch.from_numpy(np.stack([Xf.real, Xf.imag], -1)).cuda()
+    X = torch.from_numpy(np.ascontiguousarray(np.stack([Xf.real, Xf.imag], -1))).cuda()
     F = w.n_samples // 2
     Y = torch.empty((F, plan.info.n_tx_used, plan.info.n_rx_used, 2), device="cuda:0")
     plan.shear(X, Y)
@@ -67,7 +67,7 @@ def test_stage_inverse_matches_oracle():
     rng = np.random.default_rng(4)
     Yh = (rng.standard_normal((F, plan.info.n_tx_used, plan.info.n_rx_used))
           + 1j * rng.standard_normal((F, plan.info.n_tx_used, plan.info.n_rx_used))).astype(np.complex64)
-    Y = torch.from_numpy(np.stack([Yh.real, Yh.imag], -1)).cuda()
+    Y = torch.from_numpy(np.ascontiguousarray(np.stack([Yh.real, Yh.imag], -1))).cuda()
     rt = plan.empty_rf_theta()
     plan.inverse(Y, rt)
     torch.cuda.synchronize()
