@@ -149,6 +149,17 @@ void kk_plan_destroy(kk_plan *p);
 
 kk_status kk_plan_get_info(const kk_plan *p, kk_plan_info *info);
 
+/*
+ * Tuning of the KK image-formation kernel (no counterpart in the paper: a
+ * launch-shape choice).  rows in {2, 4, 8}: pixels per thread along z, tile =
+ * 32 x (4 rows) pixels; stage in {4, 8, 16}: pairs staged per batch.  Results
+ * do not depend on it beyond FP32 rounding order.  Returns
+ * KK_ERR_UNSUPPORTED when the grid's staged window is too long for the shape
+ * (the plan keeps its previous shape).  Changes workspace_bytes: call before
+ * allocating the workspace, never while work is in flight.
+ */
+kk_status kk_plan_set_gather(kk_plan *p, int32_t rows, int32_t stage);
+
 /* Workspace bytes needed by kk_decompose / kk_beamform / das_beamform. */
 kk_status kk_plan_workspace_size(const kk_plan *p, size_t *bytes);
 

@@ -6,13 +6,18 @@
 //   Section II-F's LUT decomposition taken to its limit).
 //
 // Design (gather-bound; tensor cores do not apply):
-//  * one CTA per 32x32 pixel tile (and per slice of the pair list when the
-//    grid has too few tiles to fill the GPU); 4 warps, lane = x offset,
-//    8 z rows per thread;
-//  * pairs are processed in stages: for each pair of a stage the CTA stages
-//    the window of y_p that its tile can touch into shared memory as
-//    (y[k], y[k+1] - y[k]) so one 16-byte load gives a linear interpolation;
-//    entries outside [0, T-2] are zero, which implements the record-end rule;
+//  * one CTA per 32 x (4 ROWS) pixel tile (and per slice of the pair list
+//    when the grid has too few tiles to fill the GPU); 4 warps, lane = x
+//    offset, ROWS z rows per thread;
+//  * pairs are processed in stages of STAGE pairs: for each pair the CTA
+//    stages the window of y_p its tile can touch into shared memory as
+//    16-byte entries E[k] = (y[k], y[k+1]), so one load gives a linear
+//    interpolation; E[k] = 0 outside k in [0, T-2], which implements the
+//    record-end rule exactly;
+//  * staging goes through registers: lane m of a warp reads y[k] and y[k+1]
+//    and writes E[k], so a warp's 16-byte stores are contiguous (no bank
+//    conflicts); the loads of stage s+1 are issued before the gathers of
+//    stage s, so their latency hides behind the gathers;
 //  * delays: the 32.32 fixed-point coefficients give, per (warp, pair), the
 //    integer sample of a reference pixel and its fraction; each pixel then
 //    adds A dx + B dz (|.| <= ~20 samples) in FP32, so no FP32 rounding ever
@@ -20,144 +25,280 @@
 //  * floor() is a round-down add of 1.5 * 2^23 (no conversion instruction);
 //    the integer lands in the mantissa and indexes the staged window;
 //  * sums are two-level: per stage, then across stages (FP32).
-// Index bound: with W0 = floor(min_tile s) - 1 and the staged window length
-// >= span + 4 (span = (|A| + B) * 31), every read index lies in [0, win).
+// Index bound: with W0 = floor(min_tile s) - 1 and a staged window of
+// win >= span + 4 entries (span = |A| 31 + B (TZ - 1)), every read index lies
+// in [0, win).
 #include "kk_internal.h"
 
 namespace kk {
 
 namespace {
 
-constexpr int kMaxStage = 32;
-
-struct __align__(8) WarpPair {
+// Everything a warp needs for one pair, read with one broadcast 16-byte load.
+struct __align__(16) WarpPair {
+  float a, b;    // delay slopes along x and z (samples per pixel)
+  float phi;     // fraction of the warp's reference pixel delay
   unsigned off;  // byte offset of entry (k_ref - W0) minus the floor magic
-  float phi;     // fraction of the reference pixel's delay
 };
+
+struct __align__(8) PairSrc {
+  int w0;   // first staged sample
+  int row;  // row of rf_theta
+};
+
+// Per-pair inputs of the delay tables, copied asynchronously one stage ahead.
+struct __align__(8) PairIn {
+  long long A, B, C;  // 32.32 fixed-point delay coefficients
+  float af, bf;       // FP32 slopes
+  int row;
+  int pad;
+};
+
+__device__ __forceinline__ void cp_async4(void *smem_dst, const void *gsrc) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void *smem_dst, const void *gsrc) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
 __device__ __forceinline__ float2 f2add(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 
-__global__ void __launch_bounds__(kGatherThreads)
+template <int ROWS, int STAGE, int NPT, int MINB, bool MULTI>
+__global__ void __launch_bounds__(kGatherThreads, MINB)
     k_kk_gather(const float2 *__restrict__ rf_theta, int T, const int32_t *__restrict__ bf_row,
                 const long long *__restrict__ bfA, const long long *__restrict__ bfB,
                 const long long *__restrict__ bfC, const float *__restrict__ bfAf,
                 const float *__restrict__ bfBf, const int32_t *__restrict__ group_start, int J,
-                int nx, int nz, int tiles_x, int win, int stage, int split,
-                float2 *__restrict__ out, float *__restrict__ I, int compound) {
-  extern __shared__ float4 sw[];  // [stage][win] staged (y, dy) entries
-  __shared__ WarpPair s_wp[4][kMaxStage];
-  __shared__ float2 s_ab[kMaxStage];
-  __shared__ int s_w0[kMaxStage];
-  __shared__ int s_row[kMaxStage];
+                int nx, int nz, int tiles_x, int win, int split, float2 *__restrict__ out,
+                float *__restrict__ I, int compound) {
+  static_assert(STAGE <= 32 && STAGE % 4 == 0, "one table thread per (pair, warp)");
+  static_assert(NPT <= kMaxStagedEntries, "staged entries held in registers");
+  constexpr int TZ = 4 * ROWS;
+  constexpr int PPW = STAGE / 4;          // pairs staged by each warp
+  constexpr int QPP = NPT / PPW;          // entries per lane per staged pair
+  static_assert(QPP * PPW == NPT, "NPT must be a multiple of STAGE / 4");
+  extern __shared__ float4 sw[];          // [STAGE][win] staged entries
+  __shared__ WarpPair s_wp[2][4][STAGE];
+  __shared__ PairSrc s_src[2][STAGE];
+  __shared__ PairIn s_in[2][STAGE];
 
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
-  const int tile = blockIdx.x;
+  const int tj = tid & 31, tw = tid >> 5;  // table thread: pair tj, warp reference tw
   const int sidx = blockIdx.y;
-  const int ix0 = (tile % tiles_x) * kTileX;
-  const int iz0 = (tile / tiles_x) * kTileZ;
+  const int ix0 = (blockIdx.x % tiles_x) * kTileX;
+  const int iz0 = (blockIdx.x / tiles_x) * TZ;
   const int ix = ix0 + lane;
-  const int izb = iz0 + warp * kRowsPerThread;
+  const int izb = iz0 + warp * ROWS;
   const float dl = (float)(lane - 16);
 
-  float2 sumB[kRowsPerThread];
-  float Isum[kRowsPerThread];
+  // ---- stage schedule: groups in order, this CTA's slice of each group ----
+  int g = 0, pe = 0, ps = 0;
+  auto enter_group = [&](int gg) {
+    for (g = gg; g < J; ++g) {
+      const int gb = group_start[g];
+      const unsigned n = (unsigned)(group_start[g + 1] - gb);
+      ps = gb + (int)((n * (unsigned)sidx) / (unsigned)split);
+      pe = gb + (int)((n * (unsigned)(sidx + 1)) / (unsigned)split);
+      if (pe > ps) return;
+    }
+  };
+
+  // image accumulators; with several groups also the running compound state
+  constexpr int CR = MULTI ? ROWS : 1;
+  float2 acc[ROWS], sumB[CR];
+  float Isum[CR];
 #pragma unroll
-  for (int r = 0; r < kRowsPerThread; ++r) {
+  for (int r = 0; r < ROWS; ++r) acc[r] = make_float2(0.f, 0.f);
+#pragma unroll
+  for (int r = 0; r < CR; ++r) {
     sumB[r] = make_float2(0.f, 0.f);
     Isum[r] = 0.f;
   }
+  int gw = 0;  // next group whose image is written
 
-  for (int g = 0; g < J; ++g) {
-    const int gb = group_start[g], ge = group_start[g + 1];
-    const int n = ge - gb;
-    const int pb = gb + (int)(((long long)n * sidx) / split);
-    const int pe = gb + (int)(((long long)n * (sidx + 1)) / split);
-    float2 acc[kRowsPerThread];
-#pragma unroll
-    for (int r = 0; r < kRowsPerThread; ++r) acc[r] = make_float2(0.f, 0.f);
+  float2 raw0[NPT], raw1[NPT];  // y[k], y[k+1] of this lane's staged entries
 
-    for (int ps = pb; ps < pe; ps += stage) {
-      const int ns = min(stage, pe - ps);
-      __syncthreads();  // previous stage fully consumed
-      {
-        const int j = tid & 31, w = tid >> 5;
-        if (j < ns) {
-          const int p = ps + j;
-          const long long A = __ldg(bfA + p), Bq = __ldg(bfB + p), Cq = __ldg(bfC + p);
-          const long long smin = Cq + Bq * (long long)iz0 + A * (long long)(A >= 0 ? ix0 : ix0 + kTileX - 1);
-          const int w0 = (int)(smin >> 32) - 1;
-          const long long sref = Cq + Bq * (long long)(iz0 + w * kRowsPerThread + kRowsPerThread / 2) +
-                                 A * (long long)(ix0 + 16);
-          const int kref = (int)(sref >> 32);
-          WarpPair wp;
-          wp.phi = (float)(unsigned)(sref & 0xffffffffLL) * 0x1p-32f;
-          wp.off = (unsigned)(j * win + (kref - w0)) * 16u - (unsigned)kFloorMagicBits * 16u;
-          s_wp[w][j] = wp;
-          if (w == 0) {
-            s_ab[j] = make_float2(__ldg(bfAf + p), __ldg(bfBf + p));
-            s_w0[j] = w0;
-            s_row[j] = __ldg(bf_row + p);
-          }
+  enter_group(0);
+  int cur_g = g, cur_p = ps, cur_n = (g < J) ? min(STAGE, pe - ps) : 0;
+  int nxt_g = J, nxt_p = 0, nxt_n = 0;
+  int buf = 0;
+
+  // per-pair inputs of a stage (NS pairs from P0) into s_in[B_], asynchronously
+#define KK_FETCH(P0, NS, B_)                           \
+  if (tw == 0 && tj < (NS)) {                          \
+    const int p_ = (P0) + tj;                          \
+    PairIn *d_ = &s_in[B_][tj];                        \
+    cp_async8(&d_->A, bfA + p_);                       \
+    cp_async8(&d_->B, bfB + p_);                       \
+    cp_async8(&d_->C, bfC + p_);                       \
+    cp_async4(&d_->af, bfAf + p_);                     \
+    cp_async4(&d_->bf, bfBf + p_);                     \
+    cp_async4(&d_->row, bf_row + p_);                  \
+  }                                                    \
+  cp_async_commit();
+  // tables of a stage (NS pairs, inputs in s_in[B_]) into buffer B_
+#define KK_TABLES(NS, B_)                                                                        \
+  if (tj < (NS)) {                                                                               \
+    const PairIn in = s_in[B_][tj];                                                              \
+    const long long smin = in.C + in.B * (long long)iz0 +                                        \
+                           in.A * (long long)(in.A >= 0 ? ix0 : ix0 + kTileX - 1);               \
+    const int w0 = (int)(smin >> 32) - 1;                                                        \
+    const long long sref = in.C + in.B * (long long)(iz0 + tw * ROWS + ROWS / 2) +               \
+                           in.A * (long long)(ix0 + 16);                                         \
+    const int kref = (int)(sref >> 32);                                                          \
+    WarpPair wp;                                                                                 \
+    wp.a = in.af;                                                                                \
+    wp.b = in.bf;                                                                                \
+    wp.phi = (float)(unsigned)(sref & 0xffffffffLL) * 0x1p-32f;                                  \
+    wp.off = (unsigned)(tj * win + (kref - w0)) * 16u - (unsigned)kFloorMagicBits * 16u;         \
+    s_wp[B_][tw][tj] = wp;                                                                       \
+    if (tw == 0) s_src[B_][tj] = PairSrc{w0, in.row};                                            \
+  }
+  // raw samples of a stage (NS pairs, tables in buffer B_) into registers:
+  // warp w stages pairs w, w+4, ...; lane handles entries m = lane + 32 i
+#define KK_LOAD_RAW(NS, B_)                                                        \
+  _Pragma("unroll") for (int u = 0; u < PPW; ++u) {                                \
+    const int j = warp + 4 * u;                                                    \
+    const PairSrc src = s_src[B_][j < (NS) ? j : 0];                               \
+    const float2 *y = rf_theta + (size_t)src.row * T;                              \
+    _Pragma("unroll") for (int i = 0; i < QPP; ++i) {                              \
+      const int m = lane + 32 * i;                                                 \
+      const int k = src.w0 + m;                                                    \
+      float2 a = make_float2(0.f, 0.f), b = make_float2(0.f, 0.f);                 \
+      if (j < (NS) && m < win && (unsigned)k <= (unsigned)(T - 2)) {               \
+        a = __ldg(y + k);                                                          \
+        b = __ldg(y + k + 1);                                                      \
+      }                                                                            \
+      raw0[u * QPP + i] = a;                                                       \
+      raw1[u * QPP + i] = b;                                                       \
+    }                                                                              \
+  }
+
+  if (cur_g < J) {
+    KK_FETCH(cur_p, cur_n, 0);
+    ps = cur_p + cur_n;
+    if (ps >= pe) enter_group(cur_g + 1);
+    nxt_g = g;
+    nxt_p = ps;
+    nxt_n = (g < J) ? min(STAGE, pe - ps) : 0;
+    if (nxt_g < J) { KK_FETCH(nxt_p, nxt_n, 1); }
+    cp_async_wait_all();
+    __syncthreads();
+    KK_TABLES(cur_n, 0);
+    __syncthreads();
+    KK_LOAD_RAW(cur_n, 0);
+  }
+  const char *swb = reinterpret_cast<const char *>(sw);
+  while (cur_g < J) {
+    cp_async_wait_all();  // inputs of the next stage have landed
+    __syncthreads();      // everyone is done gathering from sw
+    // entries E[k] = (y[k], y[k+1]) of this stage (zero outside [0, T-2])
+#pragma unroll
+    for (int u = 0; u < PPW; ++u) {
+      const int j = warp + 4 * u;
+#pragma unroll
+      for (int i = 0; i < QPP; ++i) {
+        const int m = lane + 32 * i;
+        if (j < cur_n && m < win) {
+          const float2 a = raw0[u * QPP + i], b = raw1[u * QPP + i];
+          sw[(size_t)j * win + m] = make_float4(a.x, a.y, b.x, b.y);
         }
       }
-      __syncthreads();
-      // stage windows: warp w stages pairs w, w+4, ...; lanes walk the window
-      for (int j = warp; j < ns; j += kGatherThreads / 32) {
-        const int w0 = s_w0[j];
-        const float2 *y = rf_theta + (size_t)s_row[j] * T;
-        float4 *dst = sw + j * win;
-        for (int m = lane; m < win; m += 32) {
-          const int k = w0 + m;
-          float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-          if ((unsigned)k <= (unsigned)(T - 2)) {
-            const float2 a = __ldg(y + k), b = __ldg(y + k + 1);
-            v = make_float4(a.x, a.y, b.x - a.x, b.y - a.y);
-          }
-          dst[m] = v;
-        }
-      }
-      __syncthreads();
-      float2 sacc[kRowsPerThread];
-#pragma unroll
-      for (int r = 0; r < kRowsPerThread; ++r) sacc[r] = make_float2(0.f, 0.f);
-      const char *swb = reinterpret_cast<const char *>(sw);
-      for (int j = 0; j < ns; ++j) {
-        const float2 ab = s_ab[j];
-        const WarpPair wp = s_wp[warp][j];
-        const float base = fmaf(ab.x, dl, wp.phi);
-#pragma unroll
-        for (int r = 0; r < kRowsPerThread; ++r) {
-          const float s = fmaf(ab.y, (float)(r - kRowsPerThread / 2), base);
-          const float t = __fadd_rd(s, kFloorMagic);
-          const float f = s - (t - kFloorMagic);
-          const unsigned addr = wp.off + ((unsigned)__float_as_int(t) << 4);
-          const float4 e = *reinterpret_cast<const float4 *>(swb + addr);
-          sacc[r].x += fmaf(f, e.z, e.x);
-          sacc[r].y += fmaf(f, e.w, e.y);
-        }
-      }
-#pragma unroll
-      for (int r = 0; r < kRowsPerThread; ++r) acc[r] = f2add(acc[r], sacc[r]);
     }
-    // group finished: write B_j (or this slice's partial of it)
-    float2 *dst = out + ((size_t)sidx * J + g) * (size_t)nx * nz;
+    if (nxt_g < J) { KK_TABLES(nxt_n, buf ^ 1); }
+    // schedule and per-pair inputs of the stage after next (in flight below)
+    int n2_g = J, n2_p = 0, n2_n = 0;
+    if (nxt_g < J) {
+      ps = nxt_p + nxt_n;
+      if (ps >= pe) enter_group(nxt_g + 1);
+      n2_g = g;
+      n2_p = ps;
+      n2_n = (g < J) ? min(STAGE, pe - ps) : 0;
+      if (n2_g < J) { KK_FETCH(n2_p, n2_n, buf); }
+    }
+    __syncthreads();  // entries of this stage and tables of the next visible
+    if (nxt_g < J) { KK_LOAD_RAW(nxt_n, buf ^ 1); }  // in flight during the gathers
+
+    while (gw < cur_g) {
+      float2 *dst = out + ((size_t)sidx * J + gw) * (size_t)nx * nz;
 #pragma unroll
-    for (int r = 0; r < kRowsPerThread; ++r) {
+      for (int r = 0; r < ROWS; ++r) {
+        const int iz = izb + r;
+        if (ix < nx && iz < nz) dst[(size_t)iz * nx + ix] = acc[r];
+        if constexpr (MULTI) {
+          sumB[r] = f2add(sumB[r], acc[r]);
+          Isum[r] = fmaf(acc[r].x, acc[r].x, fmaf(acc[r].y, acc[r].y, Isum[r]));
+          acc[r] = make_float2(0.f, 0.f);
+        }
+      }
+      ++gw;
+    }
+    float2 sacc[ROWS];
+#pragma unroll
+    for (int r = 0; r < ROWS; ++r) sacc[r] = make_float2(0.f, 0.f);
+    const WarpPair *tab = s_wp[buf][warp];
+#pragma unroll 2
+    for (int j = 0; j < cur_n; ++j) {
+      const WarpPair wp = tab[j];
+      const float base = fmaf(wp.a, dl, wp.phi);
+#pragma unroll
+      for (int r = 0; r < ROWS; ++r) {
+        const float s = fmaf(wp.b, (float)(r - ROWS / 2), base);
+        const float t = __fadd_rd(s, kFloorMagic);
+        const float f = s - (t - kFloorMagic);
+        const float gg = 1.0f - f;
+        const unsigned addr = wp.off + ((unsigned)__float_as_int(t) << 4);
+        const float4 e = *reinterpret_cast<const float4 *>(swb + addr);
+        sacc[r].x = fmaf(gg, e.x, sacc[r].x);
+        sacc[r].x = fmaf(f, e.z, sacc[r].x);
+        sacc[r].y = fmaf(gg, e.y, sacc[r].y);
+        sacc[r].y = fmaf(f, e.w, sacc[r].y);
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < ROWS; ++r) acc[r] = f2add(acc[r], sacc[r]);
+    cur_g = nxt_g;
+    cur_p = nxt_p;
+    cur_n = nxt_n;
+    nxt_g = n2_g;
+    nxt_p = n2_p;
+    nxt_n = n2_n;
+    buf ^= 1;
+  }
+#undef KK_FETCH
+#undef KK_TABLES
+#undef KK_LOAD_RAW
+  while (gw < J) {
+    float2 *dst = out + ((size_t)sidx * J + gw) * (size_t)nx * nz;
+#pragma unroll
+    for (int r = 0; r < ROWS; ++r) {
       const int iz = izb + r;
       if (ix < nx && iz < nz) dst[(size_t)iz * nx + ix] = acc[r];
-      sumB[r] = f2add(sumB[r], acc[r]);
-      Isum[r] = fmaf(acc[r].x, acc[r].x, fmaf(acc[r].y, acc[r].y, Isum[r]));
+      if constexpr (MULTI) {
+        sumB[r] = f2add(sumB[r], acc[r]);
+        Isum[r] = fmaf(acc[r].x, acc[r].x, fmaf(acc[r].y, acc[r].y, Isum[r]));
+        acc[r] = make_float2(0.f, 0.f);
+      }
     }
+    ++gw;
   }
   if (split == 1 && I != nullptr && compound != KK_COMPOUND_NONE) {
 #pragma unroll
-    for (int r = 0; r < kRowsPerThread; ++r) {
+    for (int r = 0; r < ROWS; ++r) {
       const int iz = izb + r;
       if (ix < nx && iz < nz) {
-        const float v = (compound == KK_COMPOUND_COHERENT)
-                            ? fmaf(sumB[r].x, sumB[r].x, sumB[r].y * sumB[r].y)
-                            : Isum[r];
+        float v;
+        if constexpr (MULTI) {
+          v = (compound == KK_COMPOUND_COHERENT) ? fmaf(sumB[r].x, sumB[r].x, sumB[r].y * sumB[r].y)
+                                                 : Isum[r];
+        } else {
+          v = fmaf(acc[r].x, acc[r].x, acc[r].y * acc[r].y);   // one group: |B|^2
+        }
         I[(size_t)iz * nx + ix] = v;
       }
     }
@@ -182,19 +323,76 @@ __global__ void k_kk_reduce(const float2 *__restrict__ part, int split, int J, i
     I[q] = (compound == KK_COMPOUND_COHERENT) ? fmaf(sb.x, sb.x, sb.y * sb.y) : si;
 }
 
+template <int ROWS, int STAGE, int NPT>
+cudaError_t launch_cfg(const kk_plan &p, const float2 *rf_theta, float2 *dst, float *I,
+                       cudaStream_t s) {
+  // registers held to 64 for ROWS <= 4 (8 CTAs of 128 threads per SM) and
+  // to 102 for ROWS = 8 (5 CTAs)
+  auto k = (p.J > 1) ? k_kk_gather<ROWS, STAGE, NPT, (ROWS <= 4 ? 8 : 5), true>
+                     : k_kk_gather<ROWS, STAGE, NPT, (ROWS <= 4 ? 8 : 5), false>;
+  const size_t smem = sizeof(float4) * (size_t)STAGE * p.bf_win;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const dim3 grid(p.tiles_x * p.tiles_z, p.bf_split);
+  k<<<grid, kGatherThreads, smem, s>>>(rf_theta, p.T, p.t.bf_row, p.t.bf_A, p.t.bf_B, p.t.bf_C,
+                                       p.t.bf_Af, p.t.bf_Bf, p.t.group_start, p.J, p.grid.nx,
+                                       p.grid.nz, p.tiles_x, p.bf_win, p.bf_split, dst, I,
+                                       p.compound);
+  return cudaGetLastError();
+}
+
+// entries per lane needed to stage win entries of STAGE pairs; a lane holds
+// at most kMaxStagedEntries of them in registers
+template <int ROWS, int STAGE>
+cudaError_t launch_rs(const kk_plan &p, const float2 *rf_theta, float2 *dst, float *I,
+                      cudaStream_t s) {
+  constexpr int PPW = STAGE / 4;
+  const int q = gather_entries_per_lane(p.bf_win);
+  if constexpr (PPW * 1 <= kMaxStagedEntries) {
+    if (q == 1) return launch_cfg<ROWS, STAGE, PPW * 1>(p, rf_theta, dst, I, s);
+  }
+  if constexpr (PPW * 2 <= kMaxStagedEntries) {
+    if (q == 2) return launch_cfg<ROWS, STAGE, PPW * 2>(p, rf_theta, dst, I, s);
+  }
+  if constexpr (PPW * 4 <= kMaxStagedEntries) {
+    if (q <= 4) return launch_cfg<ROWS, STAGE, PPW * 4>(p, rf_theta, dst, I, s);
+  }
+  if constexpr (PPW * 8 <= kMaxStagedEntries) {
+    if (q <= 8) return launch_cfg<ROWS, STAGE, PPW * 8>(p, rf_theta, dst, I, s);
+  }
+  return cudaErrorInvalidConfiguration;
+}
+
 }  // namespace
+
+int gather_entries_per_lane(int win) {
+  const int q = (win + 31) / 32;
+  return q <= 1 ? 1 : (q <= 2 ? 2 : (q <= 4 ? 4 : (q <= 8 ? 8 : 0)));
+}
+
+bool gather_config_supported(int rows, int stage, int win) {
+  if (!((rows == 2 || rows == 4 || rows == 8) && (stage == 4 || stage == 8 || stage == 16))) return false;
+  const int q = gather_entries_per_lane(win);
+  return q > 0 && (stage / 4) * q <= kMaxStagedEntries;
+}
 
 cudaError_t launch_kk_gather(const kk_plan &p, const float2 *rf_theta, float2 *B, float *I,
                              float2 *partial, cudaStream_t s) {
-  const size_t smem = sizeof(float4) * (size_t)p.bf_stage * p.bf_win;
-  cudaFuncSetAttribute(k_kk_gather, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  const dim3 grid(p.tiles_x * p.tiles_z, p.bf_split);
   float2 *dst = (p.bf_split > 1) ? partial : B;
-  k_kk_gather<<<grid, kGatherThreads, smem, s>>>(
-      rf_theta, p.T, p.t.bf_row, p.t.bf_A, p.t.bf_B, p.t.bf_C, p.t.bf_Af, p.t.bf_Bf,
-      p.t.group_start, p.J, p.grid.nx, p.grid.nz, p.tiles_x, p.bf_win, p.bf_stage, p.bf_split, dst,
-      I, p.compound);
-  cudaError_t e = cudaGetLastError();
+  cudaError_t e;
+  const int key = p.bf_rows * 100 + p.bf_stage;
+  switch (key) {
+    case 204: e = launch_rs<2, 4>(p, rf_theta, dst, I, s); break;
+    case 208: e = launch_rs<2, 8>(p, rf_theta, dst, I, s); break;
+    case 216: e = launch_rs<2, 16>(p, rf_theta, dst, I, s); break;
+    case 404: e = launch_rs<4, 4>(p, rf_theta, dst, I, s); break;
+    case 408: e = launch_rs<4, 8>(p, rf_theta, dst, I, s); break;
+    case 416: e = launch_rs<4, 16>(p, rf_theta, dst, I, s); break;
+    case 804: e = launch_rs<8, 4>(p, rf_theta, dst, I, s); break;
+    case 808: e = launch_rs<8, 8>(p, rf_theta, dst, I, s); break;
+    case 816: e = launch_rs<8, 16>(p, rf_theta, dst, I, s); break;
+    default: return cudaErrorInvalidConfiguration;
+  }
   if (e != cudaSuccess || p.bf_split == 1) return e;
   const int npix = p.grid.nx * p.grid.nz;
   k_kk_reduce<<<(npix + 255) / 256, 256, 0, s>>>(partial, p.bf_split, p.J, npix, B, I, p.compound);

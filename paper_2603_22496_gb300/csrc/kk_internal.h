@@ -77,16 +77,23 @@ struct kk_plan {
   void *dev_block = nullptr;     // the one allocation holding DevTables
   std::vector<int32_t> h_group_start;
   // gather kernel configuration
+  int bf_rows = 8;     // z rows per thread: tile = 32 x (4 * bf_rows) pixels
   int bf_win = 0;      // window entries staged per pair / channel
   int bf_stage = 0;    // pairs (KK) or transmits (DAS) per stage
   int bf_split = 1;    // pair-range splits (KK), partial images reduced after
   int tiles_x = 0, tiles_z = 0;
+  std::vector<double> h_bfA, h_bfB;  // per-pair delay slopes (samples per pixel)
   // workspace layout (bytes from the workspace base)
   size_t ws_X = 0, ws_Y = 0, ws_part = 0, ws_total = 0;
   double compression = 0;
 };
 
 namespace kk {
+
+// staged entries a lane of the gather kernels holds in registers
+constexpr int kMaxStagedEntries = 8;
+int gather_entries_per_lane(int win);
+bool gather_config_supported(int rows, int stage, int win);
 
 // thread-local error message
 void set_error(const std::string &msg);

@@ -150,6 +150,40 @@ kk_status upload(kk_plan &p, const Blob &blob) {
   return KK_OK;
 }
 
+// Window length, tile grid, pair-range split and workspace of the KK gather
+// for a (rows, stage) configuration.
+kk_status configure_kk_gather(kk_plan &p, int rows, int stage) {
+  const kk_grid &g = p.grid;
+  const int tz = 4 * rows;
+  double span = 0;
+  for (size_t q = 0; q < p.h_bfA.size(); ++q)
+    span = std::max(span, std::fabs(p.h_bfA[q]) * (kTileX - 1) + p.h_bfB[q] * (tz - 1));
+  // window: W0 = floor(min s) - 1, so a length >= span + 4 covers every read
+  const int win = (int)std::ceil(span) + 4;
+  if (!gather_config_supported(rows, stage, win)) {
+    set_error("gather shape not available for this grid (staged window of " + std::to_string(win) +
+              " samples); use fewer rows or a smaller stage");
+    return KK_ERR_UNSUPPORTED;
+  }
+  p.bf_rows = rows;
+  p.bf_stage = stage;
+  p.bf_win = win;
+  p.tiles_x = (g.nx + kTileX - 1) / kTileX;
+  p.tiles_z = (g.nz + tz - 1) / tz;
+  // split the pair list so the grid covers the GPU (~4 CTAs per SM), keeping
+  // >= 2 stages of work per slice
+  int sms = 148;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p.device);
+  const int tiles = p.tiles_x * p.tiles_z;
+  const int split = (4 * sms + tiles - 1) / tiles;
+  const int max_by_pairs = std::max(1, (p.P / p.J) / (2 * stage));
+  p.bf_split = std::max(1, std::min(split, max_by_pairs));
+  size_t off = p.ws_part;
+  if (p.bf_split > 1) off = align_up(off + sizeof(float2) * (size_t)p.bf_split * p.J * g.nx * g.nz);
+  p.ws_total = off;
+  return KK_OK;
+}
+
 int choose_stage(int win) {
   // about 40 KB of staged windows per CTA, at most 32 pairs / transmits
   int st = (int)(40 * 1024 / (16 * (size_t)win));
@@ -244,40 +278,34 @@ kk_status make_kk(kk_plan &p, const kk_plan_desc *d) {
     const double b = k_s * g.dz * cz;
     const double c0 = k_s * (g.x0 * sx + g.z0 * cz - xr * std::sin(to));
     row[s] = q;
+    p.h_bfA.push_back(a);
+    p.h_bfB.push_back(b);
     A[s] = to_fixed32(a);
     Bv[s] = to_fixed32(b);
     C[s] = to_fixed32(c0);
     Af[s] = (float)a;
     Bf[s] = (float)b;
-    span = std::max(span, (std::fabs(a) * (kTileX - 1) + b * (kTileZ - 1)));
   }
   const size_t off_row = blob.add(row), off_A = blob.add(A), off_B = blob.add(Bv), off_C = blob.add(C);
   const size_t off_Af = blob.add(Af), off_Bf = blob.add(Bf);
   std::vector<int32_t> gs(p.h_group_start.begin(), p.h_group_start.end());
   const size_t off_gs = blob.add(gs);
 
-  p.bf_win = (int)std::ceil(span) + 4;
-  p.bf_stage = choose_stage(p.bf_win);
-  p.tiles_x = (g.nx + kTileX - 1) / kTileX;
-  p.tiles_z = (g.nz + kTileZ - 1) / kTileZ;
-  // split the pair list so the grid covers the GPU (~4 CTAs per SM), keeping
-  // >= 2 stages of work per slice
-  int sms = 148;
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p.device);
-  const int tiles = p.tiles_x * p.tiles_z;
-  int split = (4 * sms + tiles - 1) / tiles;
-  int max_by_pairs = std::max(1, (P / J) / (2 * p.bf_stage));
-  p.bf_split = std::max(1, std::min(split, max_by_pairs));
-
-  // workspace: X [F][Nu][L], Y [F][Nu][Mu], partial images
+  // workspace: X [F][Nu][L], Y [F][Nu][Mu], then the gather's partial images
   size_t off = 0;
   p.ws_X = off;
   off = align_up(off + sizeof(float2) * (size_t)p.F * p.Nu * p.L);
   p.ws_Y = off;
   off = align_up(off + sizeof(float2) * (size_t)p.F * p.Nu * p.Mu);
   p.ws_part = off;
-  if (p.bf_split > 1) off = align_up(off + sizeof(float2) * (size_t)p.bf_split * J * g.nx * g.nz);
-  p.ws_total = off;
+  (void)span;
+  // default launch shape: 32 x 16 tiles, 16 pairs per stage (8 when the
+  // window is long); coarse grids fall back to smaller stages
+  kk_status cst = KK_ERR_UNSUPPORTED;
+  for (const int *rs : {(const int[2]){4, 16}, (const int[2]){4, 8}, (const int[2]){4, 4},
+                        (const int[2]){2, 8}, (const int[2]){2, 4}})
+    if ((cst = configure_kk_gather(p, rs[0], rs[1])) == KK_OK) break;
+  if (cst != KK_OK) return cst;
 
   kk_status st = upload(p, blob);
   if (st != KK_OK) return st;
@@ -475,6 +503,19 @@ void kk_plan_destroy(kk_plan *p) {
   delete p;
 }
 
+kk_status kk_plan_set_gather(kk_plan *p, int32_t rows, int32_t stage) {
+  kk_status st = check_plan(p, false);
+  if (st != KK_OK) return st;
+  if (!((rows == 2 || rows == 4 || rows == 8) && (stage == 4 || stage == 8 || stage == 16))) {
+    set_error("gather configuration must be rows in {2, 4, 8}, stage in {4, 8, 16}");
+    return KK_ERR_INVALID_ARG;
+  }
+  const int r0 = p->bf_rows, s0 = p->bf_stage;
+  st = configure_kk_gather(*p, rows, stage);
+  if (st != KK_OK) configure_kk_gather(*p, r0, s0);
+  return st;
+}
+
 kk_status kk_plan_workspace_size(const kk_plan *p, size_t *bytes) {
   if (!p || !bytes) { set_error("null argument"); return KK_ERR_INVALID_ARG; }
   *bytes = p->ws_total;
@@ -550,6 +591,7 @@ kk_status kk_beamform(const kk_plan *p, const void *d_rf_theta, void *d_B, float
   if (!d_rf_theta || !d_B) { set_error("null buffer"); return KK_ERR_INVALID_ARG; }
   if (p->compound != KK_COMPOUND_NONE && !d_I) { set_error("compound mode set but I is null"); return KK_ERR_INVALID_ARG; }
   if (p->bf_split > 1 && !d_ws) { set_error("workspace required"); return KK_ERR_INVALID_ARG; }
+  if (!aligned(d_rf_theta, 16) || (d_ws && !aligned(d_ws, kAlign))) { set_error("rf_theta must be 16-byte aligned (workspace 256)"); return KK_ERR_INVALID_ARG; }
   DeviceGuard guard(p->device);
   return enqueue_beamform(p, d_rf_theta, d_B, d_I, d_ws, (cudaStream_t)stream);
 }

@@ -255,3 +255,35 @@ def test_large_das_sampled_pixels(large):
     pix = _sample_pixels(w.grid, 2000, 2)
     ref = kk.das_image(w.rf, w.tx_angles, w.elem_x, w.grid, FS, C, pixels=pix)
     assert kc.rel_l2(B[pix[:, 1], pix[:, 0]], ref) <= TOL
+
+
+@pytest.mark.parametrize("rows,stage", [(2, 4), (2, 8), (4, 4), (4, 8), (8, 4)])
+def test_every_gather_configuration(rows, stage):
+    """Every launch shape of the KK gather gives the oracle's image (hybrid
+    groups, coherent compounding, ragged grid)."""
+    import torch
+    w = kksynth.workload_small()
+    grid = (70, 58, -5e-3, 0.11e-3, 6e-3, 0.09e-3)
+    ops, (rx, pairs, grp, J) = kc.scheme_both("hybrid", w.tx_angles, 7, js=[0, 3, 5])
+    plan = kc.kk_plan_for(w, rx, pairs, grp, J, kb.KK_COMPOUND_COHERENT, grid)
+    plan.set_gather(rows, stage)
+    ws, rt, B, I = plan.empty_workspace(), plan.empty_rf_theta(), plan.empty_image(), plan.empty_intensity()
+    plan.decompose(kc.to_dev(w.rf), rt, ws)
+    plan.beamform(rt, B, I, ws)
+    torch.cuda.synchronize()
+    ref = kk.kk_image(w.rf, w.elem_x, ops, grid, FS, C)
+    assert kc.rel_l2(kc.cplx(B), ref) <= TOL
+    assert kc.rel_l2(I.cpu().numpy(), kk.compound(ref, "coherent")) <= 2 * TOL
+
+
+def test_gather_configuration_rejects_bad_shapes():
+    w = kksynth.workload_small()
+    ops, (rx, pairs, grp, J) = kc.scheme_both("vernier", w.tx_angles, 5)
+    plan = kc.kk_plan_for(w, rx, pairs, grp, J)
+    with pytest.raises(kb.KKError):
+        plan.set_gather(6, 16)
+    with pytest.raises(kb.KKError):
+        plan.set_gather(8, 64)
+    with pytest.raises(kb.KKError):      # small grid's window too long for 32 x 32 tiles x 16 pairs
+        plan.set_gather(8, 16)
+    plan.set_gather(4, 8)
