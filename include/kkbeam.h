@@ -199,6 +199,29 @@ kk_status kk_beamform(const kk_plan *p, const void *d_rf_theta, void *d_B,
                       float *d_I, void *d_workspace, void *stream);
 
 /*
+ * KK image formation that allocates nothing.  The paper has no counterpart:
+ * this entry point exists for callers that cannot call cudaMalloc or hand
+ * over a workspace -- code running inside a host framework that owns all
+ * device memory through its own pool, a plugin loaded into such a process,
+ * a real-time loop that must never allocate.
+ *
+ * Same inputs, outputs and results as kk_beamform.  The partial images of the
+ * pair slices, which kk_beamform keeps in the caller's workspace, live in a
+ * fixed 8 MiB device array compiled into the library; every GPU that loads
+ * the library holds that array until the process exits.  A plan whose partial
+ * images need more than 8 MiB (pair slices x groups x nx x nz x 8 bytes; 0
+ * when the plan uses a single slice) is rejected with KK_ERR_INVALID_ARG.
+ * The first call on a device looks up the array's device address (a set-up
+ * step, no allocation): make that first call before any stream capture.
+ * All calls share the one array, which keeps the last call's contents (every
+ * call rewrites all it reads, so nothing needs clearing); calls that overlap
+ * on the GPU -- different streams, or host threads without ordering -- race
+ * and must be serialised by the caller.
+ */
+kk_status kk_beamform_noalloc(const kk_plan *p, const void *d_rf_theta, void *d_B,
+                              float *d_I, void *stream);
+
+/*
  * DAS reference path (Eq. (DAS)): analytic signal of every channel (same FFT,
  * mask and inverse as step 1, no shear), then
  *   B(ix, iz) = sum_{i,l} lerp(y_il, fs (tau_in + |r - (u_l, 0)| / c))

@@ -31,7 +31,7 @@ _STATUS = {0: "KK_OK", 1: "KK_ERR_INVALID_ARG", 2: "KK_ERR_UNSUPPORTED", 3: "KK_
 # every symbol declared in include/kkbeam.h
 EXPORTS = ["kk_plan_create", "das_plan_create", "kk_plan_destroy", "kk_plan_get_info",
            "kk_plan_set_gather", "kk_plan_workspace_size", "kk_decompose", "kk_spectrum", "kk_shear", "kk_inverse",
-           "kk_beamform", "das_beamform", "kk_run_host_scratch_size", "kk_run_host",
+           "kk_beamform", "kk_beamform_noalloc", "das_beamform", "kk_run_host_scratch_size", "kk_run_host",
            "kk_scheme_angles", "kk_last_error", "kk_version"]
 
 
@@ -107,6 +107,7 @@ def load(build_if_missing: bool = False):
         "kk_shear": ([vp, vp, vp, vp], st),
         "kk_inverse": ([vp, vp, vp, vp], st),
         "kk_beamform": ([vp, vp, vp, vp, vp, vp], st),
+        "kk_beamform_noalloc": ([vp, vp, vp, vp, vp], st),
         "das_beamform": ([vp, vp, vp, vp, vp, vp], st),
         "kk_run_host_scratch_size": ([vp, ctypes.POINTER(ctypes.c_size_t)], st),
         "kk_run_host": ([vp, vp, vp, vp, vp, vp], st),
@@ -252,6 +253,12 @@ def kk_inverse(h, Y, rf_theta, stream=None):
 def kk_beamform(h, rf_theta, B, I=None, workspace=None, stream=None):
     _check(load().kk_beamform(h, _ptr(rf_theta), _ptr(B), _ptr(I), _ptr(workspace),
                               _stream(stream)))
+
+
+def kk_beamform_noalloc(h, rf_theta, B, I=None, stream=None):
+    """kk_beamform without a workspace: the library's fixed device scratch is
+    used instead (for callers that cannot allocate device memory)."""
+    _check(load().kk_beamform_noalloc(h, _ptr(rf_theta), _ptr(B), _ptr(I), _stream(stream)))
 
 
 def das_beamform(h, rf, B, I=None, workspace=None, stream=None):

@@ -1,0 +1,87 @@
+// kk_noalloc.cu -- KK image formation for callers that cannot allocate.
+//
+// kk_beamform keeps the partial images of its pair slices in the caller's
+// workspace.  Some callers cannot provide one: code that runs where
+// cudaMalloc is unavailable or forbidden (inside a host framework that owns
+// all device memory through its own pool, a plugin loaded into such a
+// process, a real-time loop that must not allocate).  For them this file
+// holds the scratch in a fixed file-scope device array compiled into the
+// library, and kk_beamform_noalloc launches the same gather and reduction
+// kernels with it.  Nothing here calls cudaMalloc, cudaFree or any
+// allocating routine.
+#include <mutex>
+
+#include "kk_internal.h"
+
+namespace kk {
+namespace {
+
+// 8 MiB: one million complex partial pixels (pair slices x groups x pixels).
+// Every GPU that loads the library holds this array until the process exits.
+constexpr size_t kNoAllocScratchBytes = size_t(8) << 20;
+constexpr int kMaxDevices = 64;
+
+static __device__ __align__(256) float2 g_noalloc_scratch[kNoAllocScratchBytes / sizeof(float2)];
+
+std::mutex g_mu;
+void *g_scratch_ptr[kMaxDevices] = {};
+
+// Device address of the scratch array on `device` (which is current).  Host
+// code cannot use the symbol itself: it names a host-side stand-in.
+kk_status scratch_address(int device, void **out) {
+  if (device < 0 || device >= kMaxDevices) {
+    set_error("device ordinal beyond the no-allocation scratch table");
+    return KK_ERR_INVALID_ARG;
+  }
+  std::lock_guard<std::mutex> lock(g_mu);
+  if (!g_scratch_ptr[device]) {
+    void *ptr = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (e != cudaSuccess || ptr == nullptr) {
+      if (e == cudaSuccess) e = cudaErrorInvalidSymbol;
+      return cuda_fail(e, "cudaGetSymbolAddress(no-allocation scratch)");
+    }
+    g_scratch_ptr[device] = ptr;
+  }
+  *out = g_scratch_ptr[device];
+  return KK_OK;
+}
+
+}  // namespace
+}  // namespace kk
+
+using namespace kk;
+
+extern "C" kk_status kk_beamform_noalloc(const kk_plan *p, const void *d_rf_theta, void *d_B,
+                                         float *d_I, void *stream) {
+  if (!p) { set_error("null plan"); return KK_ERR_INVALID_ARG; }
+  if (p->is_das) { set_error("expected a KK plan"); return KK_ERR_INVALID_ARG; }
+  if (!d_rf_theta || !d_B) { set_error("null buffer"); return KK_ERR_INVALID_ARG; }
+  if (p->compound != KK_COMPOUND_NONE && !d_I) { set_error("compound mode set but I is null"); return KK_ERR_INVALID_ARG; }
+  if ((uintptr_t)d_rf_theta % 16) { set_error("rf_theta must be 16-byte aligned"); return KK_ERR_INVALID_ARG; }
+  const size_t need = (p->bf_split > 1)
+                          ? sizeof(float2) * (size_t)p->bf_split * p->J * p->grid.nx * p->grid.nz
+                          : 0;
+  if (need > kNoAllocScratchBytes) {
+    set_error("plan needs " + std::to_string(need) + " bytes of partial images; the no-allocation "
+              "scratch holds " + std::to_string(kNoAllocScratchBytes) + " (use kk_beamform with a workspace)");
+    return KK_ERR_INVALID_ARG;
+  }
+  int old = -1;
+  if (cudaGetDevice(&old) != cudaSuccess) old = -1;
+  if (old != p->device && cudaSetDevice(p->device) != cudaSuccess) {
+    set_error("cudaSetDevice failed");
+    return KK_ERR_CUDA;
+  }
+  kk_status st = KK_OK;
+  void *scratch = nullptr;
+  if (need > 0) st = scratch_address(p->device, &scratch);
+  if (st == KK_OK) {
+    // every slice writes each of its partial pixels, so nothing needs clearing
+    cudaError_t e = launch_kk_gather(*p, (const float2 *)d_rf_theta, (float2 *)d_B, d_I,
+                                     (float2 *)scratch, (cudaStream_t)stream);
+    if (e != cudaSuccess) st = cuda_fail(e, "kk gather launch (no-allocation)");
+  }
+  if (old >= 0 && old != p->device) cudaSetDevice(old);
+  return st;
+}
