@@ -101,7 +101,10 @@ typedef struct kk_plan_desc {
   double fs;                  /* sampling rate > 0 */
   int32_t n_samples;          /* T: even, T/2 in {128,256,512,768,1024,1536,2048} */
   int32_t rf_dtype;           /* kk_rf_dtype */
-  int32_t precision;          /* kk_precision (KK only; DAS is FP32) */
+  int32_t precision;          /* kk_precision (KK only; DAS is FP32).  The
+                                 BF16/F16/F8E4M3 forms run the decomposition
+                                 contraction on tensor cores and need
+                                 n_elem <= 128 and <= 256 transmits in use */
   int32_t device;             /* CUDA device ordinal the plan lives on */
 } kk_plan_desc;
 
@@ -160,6 +163,14 @@ kk_status kk_plan_get_info(const kk_plan *p, kk_plan_info *info);
  */
 kk_status kk_plan_set_gather(kk_plan *p, int32_t rows, int32_t stage);
 
+/*
+ * Device status word of the plan's kernels: KK_OK, or KK_ERR_TIMEOUT when a
+ * bounded device-side wait gave up (the kernel then abandoned its work and
+ * released its resources).  Synchronises with the device, returns the word
+ * in *status and resets it to KK_OK.  No counterpart in the paper.
+ */
+kk_status kk_plan_status(const kk_plan *p, int32_t *status);
+
 /* Workspace bytes needed by kk_decompose / kk_beamform / das_beamform. */
 kk_status kk_plan_workspace_size(const kk_plan *p, size_t *bytes);
 
@@ -177,8 +188,13 @@ kk_status kk_plan_workspace_size(const kk_plan *p, size_t *bytes);
 kk_status kk_decompose(const kk_plan *p, const void *d_rf, void *d_rf_theta,
                        void *d_workspace, void *stream);
 
-/* Stage calls of kk_decompose, for inspection and testing (FP32 plans only).
- * d_X: [F][Nu][L] cfloat (h_k applied).  d_Y: [F][Nu][Mu] cfloat. */
+/* Stage calls of kk_decompose, for inspection and testing.
+ * d_X: [F][Nu][L] complex spectra with h_k applied: cfloat for FP32 plans,
+ *      interleaved (re, im) bfloat16 for BF16 plans, float16 for F16 and
+ *      F8E4M3 plans (the FP8 form rounds to e4m3 inside the contraction).
+ *      The float16 spectra are stored times 2^-ceil(log2(2T)) so that RF
+ *      samples of magnitude <= 32768 cannot overflow; kk_shear undoes it.
+ * d_Y: [F][Nu][Mu] cfloat for every precision. */
 kk_status kk_spectrum(const kk_plan *p, const void *d_rf, void *d_X, void *stream);
 kk_status kk_shear(const kk_plan *p, const void *d_X, void *d_Y, void *stream);
 kk_status kk_inverse(const kk_plan *p, const void *d_Y, void *d_rf_theta,

@@ -30,7 +30,7 @@ _STATUS = {0: "KK_OK", 1: "KK_ERR_INVALID_ARG", 2: "KK_ERR_UNSUPPORTED", 3: "KK_
 
 # every symbol declared in include/kkbeam.h
 EXPORTS = ["kk_plan_create", "das_plan_create", "kk_plan_destroy", "kk_plan_get_info",
-           "kk_plan_set_gather", "kk_plan_workspace_size", "kk_decompose", "kk_spectrum", "kk_shear", "kk_inverse",
+           "kk_plan_set_gather", "kk_plan_status", "kk_plan_workspace_size", "kk_decompose", "kk_spectrum", "kk_shear", "kk_inverse",
            "kk_beamform", "kk_beamform_noalloc", "das_beamform", "kk_run_host_scratch_size", "kk_run_host",
            "kk_scheme_angles", "kk_last_error", "kk_version"]
 
@@ -102,6 +102,7 @@ def load(build_if_missing: bool = False):
         "kk_plan_get_info": ([vp, ctypes.POINTER(kk_plan_info)], st),
         "kk_plan_workspace_size": ([vp, ctypes.POINTER(ctypes.c_size_t)], st),
         "kk_plan_set_gather": ([vp, ctypes.c_int32, ctypes.c_int32], st),
+        "kk_plan_status": ([vp, ctypes.POINTER(ctypes.c_int32)], st),
         "kk_decompose": ([vp, vp, vp, vp, vp], st),
         "kk_spectrum": ([vp, vp, vp, vp], st),
         "kk_shear": ([vp, vp, vp, vp], st),
@@ -234,6 +235,13 @@ def kk_plan_set_gather(h, rows: int, stage: int):
     _check(load().kk_plan_set_gather(h, int(rows), int(stage)))
 
 
+def kk_plan_status(h) -> int:
+    """Device status word (KK_OK or KK_ERR_TIMEOUT); synchronises and resets it."""
+    v = ctypes.c_int32()
+    _check(load().kk_plan_status(h, ctypes.byref(v)))
+    return int(v.value)
+
+
 def kk_decompose(h, rf, rf_theta, workspace, stream=None):
     _check(load().kk_decompose(h, _ptr(rf), _ptr(rf_theta), _ptr(workspace), _stream(stream)))
 
@@ -325,6 +333,9 @@ class Plan:
     def set_gather(self, rows: int, stage: int):
         kk_plan_set_gather(self.handle, rows, stage)
         self.info = kk_plan_get_info(self.handle)
+
+    def status(self) -> int:
+        return kk_plan_status(self.handle)
 
     def decompose(self, rf, rf_theta, workspace, stream=None):
         kk_decompose(self.handle, rf, rf_theta, workspace, stream)

@@ -18,6 +18,9 @@
 // bin-major global access touches C consecutive complex values.  The
 // transform runs in place in shared memory: every pass reads its butterfly
 // inputs into registers, synchronises, then writes the outputs.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 #include "kk_internal.h"
 
 namespace kk {
@@ -157,12 +160,20 @@ __device__ __forceinline__ float2 load_pair(const float *p) {
 
 // ---- forward: analytic spectrum -------------------------------------------
 // X[k][c] for channel c = iu * L + l (row tx_rows[iu] * L + l of rf).
-template <int F, int C, int NT, typename TIn>
+__device__ __forceinline__ void store_x(float2 *X, size_t idx, float2 v) { X[idx] = v; }
+__device__ __forceinline__ void store_x(__nv_bfloat162 *X, size_t idx, float2 v) {
+  X[idx] = __floats2bfloat162_rn(v.x, v.y);
+}
+__device__ __forceinline__ void store_x(__half2 *X, size_t idx, float2 v) {
+  X[idx] = __floats2half2_rn(v.x, v.y);
+}
+
+template <int F, int C, int NT, typename TIn, typename TOut>
 __global__ void __launch_bounds__(NT) k_spectrum(const TIn *__restrict__ rf,
                                                  const int32_t *__restrict__ tx_rows, int L,
                                                  int n_ch, const float2 *__restrict__ tw,
                                                  const float2 *__restrict__ rw,
-                                                 float2 *__restrict__ X) {
+                                                 TOut *__restrict__ X, float xscale) {
   constexpr int FS = F + 1;
   constexpr int T = 2 * F;
   extern __shared__ float2 sm[];
@@ -191,10 +202,10 @@ __global__ void __launch_bounds__(NT) k_spectrum(const TIn *__restrict__ rf,
     const float2 e = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
     const float2 o = make_float2(0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
     float2 x = cadd(e, cmul(__ldg(rw + k), o));
-    const float h = (k == 0) ? 1.f : 2.f;
+    const float h = (k == 0) ? xscale : 2.f * xscale;
     x.x *= h;
     x.y *= h;
-    X[(size_t)k * n_ch + c] = x;
+    store_x(X, (size_t)k * n_ch + c, x);
   }
 }
 
@@ -246,23 +257,36 @@ struct FftCfg {
   static constexpr int NT = (F <= 256) ? 256 : 512;
 };
 
-template <int F>
-static cudaError_t spectrum_f(const kk_plan &p, const void *rf, float2 *X, int n_rows,
-                              const int32_t *rows, cudaStream_t s) {
+template <int F, typename TIn, typename TOut>
+static cudaError_t spectrum_ft(const kk_plan &p, const void *rf, void *X, int n_ch,
+                               const int32_t *rows, cudaStream_t s) {
   using Cfg = FftCfg<F>;
-  const int n_ch = n_rows * p.L;
   const size_t smem = sizeof(float2) * Cfg::CS * (F + 1);
   const dim3 grid((n_ch + Cfg::CS - 1) / Cfg::CS);
-  if (p.rf_dtype == KK_RF_I16) {
-    auto k = k_spectrum<F, Cfg::CS, Cfg::NT, int16_t>;
-    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k<<<grid, Cfg::NT, smem, s>>>((const int16_t *)rf, rows, p.L, n_ch, p.t.fft_tw, p.t.rfft_w, X);
-  } else {
-    auto k = k_spectrum<F, Cfg::CS, Cfg::NT, float>;
-    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k<<<grid, Cfg::NT, smem, s>>>((const float *)rf, rows, p.L, n_ch, p.t.fft_tw, p.t.rfft_w, X);
-  }
+  auto k = k_spectrum<F, Cfg::CS, Cfg::NT, TIn, TOut>;
+  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k<<<grid, Cfg::NT, smem, s>>>((const TIn *)rf, rows, p.L, n_ch, p.t.fft_tw, p.t.rfft_w, (TOut *)X,
+                                p.x_scale);
   return cudaGetLastError();
+}
+
+template <int F, typename TIn>
+static cudaError_t spectrum_fi(const kk_plan &p, const void *rf, void *X, int n_ch,
+                               const int32_t *rows, cudaStream_t s) {
+  switch (p.precision) {
+    case KK_PREC_BF16: return spectrum_ft<F, TIn, __nv_bfloat162>(p, rf, X, n_ch, rows, s);
+    case KK_PREC_F16:
+    case KK_PREC_F8E4M3: return spectrum_ft<F, TIn, __half2>(p, rf, X, n_ch, rows, s);
+    default: return spectrum_ft<F, TIn, float2>(p, rf, X, n_ch, rows, s);
+  }
+}
+
+template <int F>
+static cudaError_t spectrum_f(const kk_plan &p, const void *rf, void *X, int n_rows,
+                              const int32_t *rows, cudaStream_t s) {
+  const int n_ch = n_rows * p.L;
+  if (p.rf_dtype == KK_RF_I16) return spectrum_fi<F, int16_t>(p, rf, X, n_ch, rows, s);
+  return spectrum_fi<F, float>(p, rf, X, n_ch, rows, s);
 }
 
 template <int F>
@@ -278,7 +302,7 @@ static cudaError_t inverse_f(const kk_plan &p, const float2 *Y, int ncol, const 
   return cudaGetLastError();
 }
 
-cudaError_t launch_spectrum(const kk_plan &p, const void *rf, float2 *X, int n_rows,
+cudaError_t launch_spectrum(const kk_plan &p, const void *rf, void *X, int n_rows,
                             const int32_t *rows, cudaStream_t s) {
   switch (p.F) {
     case 128: return spectrum_f<128>(p, rf, X, n_rows, rows, s);

@@ -59,6 +59,7 @@ struct DevTables {
   float2 *xs = nullptr;                // [nx] x fs / c as (hi, lo)
   float2 *zs = nullptr;                // [nz] z fs / c as (hi, lo)
   float2 *us = nullptr;                // [L]  u fs / c as (hi, lo)
+  int *status = nullptr;               // device status word (KK_OK or KK_ERR_TIMEOUT)
 };
 
 }  // namespace kk
@@ -75,6 +76,7 @@ struct kk_plan {
   kk::FftPlan fft;
   kk::DevTables t;
   void *dev_block = nullptr;     // the one allocation holding DevTables
+  size_t status_off = 0;
   std::vector<int32_t> h_group_start;
   // gather kernel configuration
   int bf_rows = 8;     // z rows per thread: tile = 32 x (4 * bf_rows) pixels
@@ -86,6 +88,10 @@ struct kk_plan {
   // workspace layout (bytes from the workspace base)
   size_t ws_X = 0, ws_Y = 0, ws_part = 0, ws_total = 0;
   double compression = 0;
+  // FP16-stored spectra (F16 and F8E4M3 forms) are scaled by an exact power
+  // of two, 2^-ceil(log2(2T)), so |X| <= 2 T 32768 stays below the FP16
+  // maximum; the contraction's epilogue multiplies by 1 / x_scale
+  float x_scale = 1.f;
 };
 
 namespace kk {
@@ -100,11 +106,17 @@ void set_error(const std::string &msg);
 kk_status cuda_fail(cudaError_t e, const char *what);
 
 // ---- launches (each returns cudaGetLastError() after the launch) ----------
-cudaError_t launch_spectrum(const kk_plan &p, const void *rf, float2 *X, int n_tx_rows,
+// X is complex FP32, BF16 or FP16 per the plan's precision (spectrum_bytes)
+cudaError_t launch_spectrum(const kk_plan &p, const void *rf, void *X, int n_tx_rows,
                             const int32_t *tx_rows, cudaStream_t s);
 cudaError_t launch_inverse(const kk_plan &p, const float2 *Y, int ncol, const int32_t *col_of_row,
                            int nrow, float2 *out, cudaStream_t s);
 cudaError_t launch_shear_f32(const kk_plan &p, const float2 *X, float2 *Y, cudaStream_t s);
+cudaError_t launch_shear_tc(const kk_plan &p, const void *X, float2 *Y, cudaStream_t s);
+size_t tc_shear_smem_bytes(int precision, int NP);
+// bytes of one complex spectrum value for the plan's precision: FP32 8,
+// BF16 / FP16 4 (FP8 plans keep FP16 spectra and round to e4m3 per column)
+inline int spectrum_bytes(int precision) { return precision == KK_PREC_F32 ? 8 : 4; }
 cudaError_t launch_kk_gather(const kk_plan &p, const float2 *rf_theta, float2 *B, float *I,
                              float2 *partial, cudaStream_t s);
 cudaError_t launch_das_gather(const kk_plan &p, const float2 *y, float2 *B, float *I,

@@ -131,6 +131,8 @@ void fill_fft(kk_plan &p, Blob &blob, size_t &off_tw, size_t &off_rw) {
   }
   off_tw = blob.add(tw);
   off_rw = blob.add(rw);
+  std::vector<int32_t> status(1, 0);
+  p.status_off = blob.add(status);
 }
 
 kk_status upload(kk_plan &p, const Blob &blob) {
@@ -195,7 +197,7 @@ kk_status make_kk(kk_plan &p, const kk_plan_desc *d) {
   if (d->n_pairs < 1 || !d->pairs) { set_error("n_pairs < 1 or pairs null"); return KK_ERR_INVALID_ARG; }
   if (d->n_groups < 1) { set_error("n_groups < 1"); return KK_ERR_INVALID_ARG; }
   if (d->compound < KK_COMPOUND_NONE || d->compound > KK_COMPOUND_INCOHERENT) { set_error("bad compound mode"); return KK_ERR_INVALID_ARG; }
-  if (d->precision != KK_PREC_F32) { set_error("only the FP32 precision form is built in this library"); return KK_ERR_UNSUPPORTED; }
+  if (d->precision < KK_PREC_F32 || d->precision > KK_PREC_F8E4M3) { set_error("bad precision"); return KK_ERR_INVALID_ARG; }
   for (int o = 0; o < d->n_rx; ++o)
     if (!(std::fabs(d->rx_angles[o]) < kMaxAngle)) { set_error("receive angle out of range (|theta| < 80 deg)"); return KK_ERR_INVALID_ARG; }
   const int P = d->n_pairs, J = d->n_groups;
@@ -226,6 +228,15 @@ kk_status make_kk(kk_plan &p, const kk_plan_desc *d) {
   rx_used.erase(std::unique(rx_used.begin(), rx_used.end()), rx_used.end());
   p.Nu = (int)tx_used.size();
   p.Mu = (int)rx_used.size();
+  if (p.precision == KK_PREC_F16 || p.precision == KK_PREC_F8E4M3) {
+    int e = 0;
+    while ((1 << e) < 2 * p.T) ++e;
+    p.x_scale = std::ldexp(1.0f, -e);
+  }
+  if (p.precision != KK_PREC_F32 && (p.L > 128 || p.Nu > 256)) {
+    set_error("tensor-core precision forms need <= 128 elements and <= 256 transmits in use");
+    return KK_ERR_UNSUPPORTED;
+  }
   std::vector<int> tx_pos(d->n_tx, -1), rx_pos(d->n_rx, -1);
   for (int a = 0; a < p.Nu; ++a) tx_pos[tx_used[a]] = a;
   for (int a = 0; a < p.Mu; ++a) rx_pos[rx_used[a]] = a;
@@ -291,10 +302,11 @@ kk_status make_kk(kk_plan &p, const kk_plan_desc *d) {
   std::vector<int32_t> gs(p.h_group_start.begin(), p.h_group_start.end());
   const size_t off_gs = blob.add(gs);
 
-  // workspace: X [F][Nu][L], Y [F][Nu][Mu], then the gather's partial images
+  // workspace: X [F][Nu][L] (complex, precision-dependent width), Y [F][Nu][Mu]
+  // complex FP32, then the gather's partial images
   size_t off = 0;
   p.ws_X = off;
-  off = align_up(off + sizeof(float2) * (size_t)p.F * p.Nu * p.L);
+  off = align_up(off + (size_t)spectrum_bytes(p.precision) * p.F * p.Nu * p.L);
   p.ws_Y = off;
   off = align_up(off + sizeof(float2) * (size_t)p.F * p.Nu * p.Mu);
   p.ws_part = off;
@@ -322,6 +334,7 @@ kk_status make_kk(kk_plan &p, const kk_plan_desc *d) {
   p.t.bf_Af = at<float>(b, off_Af);
   p.t.bf_Bf = at<float>(b, off_Bf);
   p.t.group_start = at<int32_t>(b, off_gs);
+  p.t.status = at<int>(b, p.status_off);
   return KK_OK;
 }
 
@@ -400,6 +413,7 @@ kk_status make_das(kk_plan &p, const kk_plan_desc *d) {
   p.t.xs = at<float2>(b, off_xs);
   p.t.zs = at<float2>(b, off_zs);
   p.t.us = at<float2>(b, off_us);
+  p.t.status = at<int>(b, p.status_off);
   return KK_OK;
 }
 
@@ -448,11 +462,12 @@ kk_status check_plan(const kk_plan *p, bool want_das) {
 bool aligned(const void *ptr, size_t a) { return ((uintptr_t)ptr % a) == 0; }
 
 kk_status enqueue_decompose(const kk_plan *p, const void *rf, void *rf_theta, void *ws, cudaStream_t s) {
-  float2 *X = at<float2>(ws, p->ws_X);
+  void *X = at<unsigned char>(ws, p->ws_X);
   float2 *Y = at<float2>(ws, p->ws_Y);
   cudaError_t e = launch_spectrum(*p, rf, X, p->Nu, p->t.tx_used, s);
   if (e != cudaSuccess) return cuda_fail(e, "spectrum launch");
-  e = launch_shear_f32(*p, X, Y, s);
+  e = (p->precision == KK_PREC_F32) ? launch_shear_f32(*p, (const float2 *)X, Y, s)
+                                     : launch_shear_tc(*p, X, Y, s);
   if (e != cudaSuccess) return cuda_fail(e, "shear launch");
   e = launch_inverse(*p, Y, p->Nu * p->Mu, p->t.pair_q, p->P, (float2 *)rf_theta, s);
   if (e != cudaSuccess) return cuda_fail(e, "inverse launch");
@@ -516,6 +531,18 @@ kk_status kk_plan_set_gather(kk_plan *p, int32_t rows, int32_t stage) {
   return st;
 }
 
+kk_status kk_plan_status(const kk_plan *p, int32_t *status) {
+  if (!p || !status) { set_error("null argument"); return KK_ERR_INVALID_ARG; }
+  DeviceGuard guard(p->device);
+  int32_t v = 0, zero = 0;
+  cudaError_t e = cudaMemcpy(&v, p->t.status, sizeof(v), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "status read");
+  e = cudaMemcpy(p->t.status, &zero, sizeof(zero), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(e, "status reset");
+  *status = v;
+  return KK_OK;
+}
+
 kk_status kk_plan_workspace_size(const kk_plan *p, size_t *bytes) {
   if (!p || !bytes) { set_error("null argument"); return KK_ERR_INVALID_ARG; }
   *bytes = p->ws_total;
@@ -561,7 +588,7 @@ kk_status kk_spectrum(const kk_plan *p, const void *d_rf, void *d_X, void *strea
   if (st != KK_OK) return st;
   if (!d_rf || !d_X) { set_error("null buffer"); return KK_ERR_INVALID_ARG; }
   DeviceGuard guard(p->device);
-  cudaError_t e = launch_spectrum(*p, d_rf, (float2 *)d_X, p->Nu, p->t.tx_used, (cudaStream_t)stream);
+  cudaError_t e = launch_spectrum(*p, d_rf, d_X, p->Nu, p->t.tx_used, (cudaStream_t)stream);
   return e == cudaSuccess ? KK_OK : cuda_fail(e, "spectrum launch");
 }
 
@@ -570,7 +597,9 @@ kk_status kk_shear(const kk_plan *p, const void *d_X, void *d_Y, void *stream) {
   if (st != KK_OK) return st;
   if (!d_X || !d_Y) { set_error("null buffer"); return KK_ERR_INVALID_ARG; }
   DeviceGuard guard(p->device);
-  cudaError_t e = launch_shear_f32(*p, (const float2 *)d_X, (float2 *)d_Y, (cudaStream_t)stream);
+  cudaError_t e = (p->precision == KK_PREC_F32)
+                      ? launch_shear_f32(*p, (const float2 *)d_X, (float2 *)d_Y, (cudaStream_t)stream)
+                      : launch_shear_tc(*p, d_X, (float2 *)d_Y, (cudaStream_t)stream);
   return e == cudaSuccess ? KK_OK : cuda_fail(e, "shear launch");
 }
 

@@ -1,0 +1,424 @@
+// kk_shear_tc.cu -- the far-field decomposition contraction on the 5th-
+// generation tensor cores (tcgen05, TMEM accumulators): BF16, FP16 and
+// FP8-e4m3 operand forms with FP32 accumulation.
+//
+// Per frequency bin k the decomposition is the complex product (Eq.
+// (compression) applied through the Fourier shift theorem, Section II-F)
+//     Y[k][i][o] = sum_l X[k][i][l] W[k][o][l],  W = exp(+2 pi i k phi[o][l]).
+// It is run as a real GEMM D = A B^T with
+//     A row (o, re) = [ Wr[o][l], -Wi[o][l] ]_l     A row (o, im) = [ Wi, Wr ]_l
+//     B row i       = [ Xr[i][l],  Xi[i][l] ]_l     (K index = 2 l + component)
+// so D[(o, re)][i] = Re Y, D[(o, im)][i] = Im Y.  B is the spectrum in its own
+// interleaved layout; A is generated on chip from the 0.64 fixed-point phases
+// (never stored in HBM).
+//
+// One CTA (one warpgroup) per bin at a time: it copies B into shared memory,
+// then for each tile of 64 receive angles (128 rows of A) generates A, one
+// thread issues K/16 (K/32 for FP8) tcgen05.mma into a TMEM accumulator of
+// 128 lanes x N columns, commits to an mbarrier, and the four warps read the
+// accumulator back (tcgen05.ld) and store Y.
+//
+// Shared-memory operands use the no-swizzle K-major canonical layout: 8-row x
+// 16-byte core matrices, K-adjacent core matrices 128 bytes apart (LBO), 8-row
+// groups KC*ES/16*... apart (SBO = 16 bytes x K-cores x 8).
+//
+// FP8: the scale is per column (k, i) of X -- it factors out of the sum over
+// elements; X is rounded to e4m3 as X / s with s = max_l |X| / 448, W is
+// stored as 64 W (|W| <= 1, clear of e4m3 subnormals), and the FP32 result is
+// multiplied by s / 64 in the epilogue.
+//
+// Every wait is bounded (%globaltimer): on timeout the CTA records
+// KK_ERR_TIMEOUT in the plan's status word, frees its TMEM and returns.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "kk_internal.h"
+
+namespace kk {
+
+namespace {
+
+constexpr int kTcThreads = 128;
+constexpr int kKC = 256;                 // K elements per pass (128 array elements)
+constexpr int kRowsM = 128;              // rows of A per tile (64 receive angles)
+constexpr unsigned long long kWaitNs = 200000000ull;  // 200 ms
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ unsigned long long globaltimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// ---- mbarrier ---------------------------------------------------------------
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// bounded wait; false on timeout
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+  const unsigned long long t0 = globaltimer();
+  while (!mbar_try_wait(bar, parity)) {
+    if (globaltimer() - t0 > kWaitNs) return false;
+  }
+  return true;
+}
+
+// ---- tcgen05 ----------------------------------------------------------------
+__device__ __forceinline__ void tmem_alloc(uint32_t *slot, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)),
+               "r"(ncols)
+               : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish() {
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void fence_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+template <int KIND>
+__device__ __forceinline__ void mma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                    uint32_t accumulate) {
+  if constexpr (KIND == 2) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+  } else {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+  }
+}
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   smem_u32(bar))
+               : "memory");
+}
+// 32 lanes x 16 consecutive 32-bit columns of this warp's lane quarter
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr)
+      : "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Shared-memory matrix descriptor: K-major, no swizzle.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)((lbo & 0x3FFFFu) >> 4) << 16;
+  d |= (uint64_t)((sbo & 0x3FFFFu) >> 4) << 32;
+  d |= (uint64_t)1 << 46;  // descriptor version for this architecture
+  return d;                // base offset 0, relative LBO, no swizzle
+}
+
+// Instruction descriptor: FP32 accumulate, A and B K-major, M x N tile.
+__host__ __device__ constexpr uint32_t instr_desc(uint32_t fmt, uint32_t M, uint32_t N) {
+  return (1u << 4) | (fmt << 7) | (fmt << 10) | ((N >> 3) << 17) | ((M >> 4) << 24);
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+  return *reinterpret_cast<const uint32_t *>(&h);
+}
+__device__ __forceinline__ uint32_t pack_f16(float a, float b) {
+  const __half2 h = __floats2half2_rn(a, b);
+  return *reinterpret_cast<const uint32_t *>(&h);
+}
+// two floats -> two e4m3 bytes (round to nearest, saturate), low byte = a
+__device__ __forceinline__ uint32_t pack_e4m3x2(float a, float b) {
+  uint16_t r;
+  asm("cvt.rn.satfinite.e4m3x2.f32 %0, %1, %2;" : "=h"(r) : "f"(b), "f"(a));
+  return r;
+}
+
+template <int KIND>
+struct Fmt {
+  static constexpr int ES = (KIND == 2) ? 1 : 2;        // bytes per operand element
+  static constexpr int KSTEP = (KIND == 2) ? 32 : 16;   // K per MMA instruction
+  static constexpr uint32_t code = (KIND == 0) ? 1u : 0u;  // BF16 = 1, F16 = 0, E4M3 = 0
+  static constexpr int EPC = 16 / ES;                   // elements per 16-byte core row
+};
+
+// byte offset of element (row, k) in a K-major no-swizzle tile of kKC columns
+template <int ES>
+__device__ __forceinline__ uint32_t core_off(int row, int kbyte) {
+  constexpr uint32_t SBO = (uint32_t)(kKC * ES / 16) * 128u;
+  return (uint32_t)(row >> 3) * SBO + (uint32_t)(kbyte >> 4) * 128u + (uint32_t)(row & 7) * 16u +
+         (uint32_t)(kbyte & 15);
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(kTcThreads, 1)
+    k_shear_tc(const void *__restrict__ Xv, const unsigned long long *__restrict__ phase, int F,
+               int L, int Nu, int Mu, int NP, float yscale, float2 *__restrict__ Y,
+               int *__restrict__ status) {
+  using FM = Fmt<KIND>;
+  constexpr int ES = FM::ES;
+  constexpr uint32_t LBO = 128u;
+  constexpr uint32_t SBO = (uint32_t)(kKC * ES / 16) * 128u;
+  extern __shared__ __align__(1024) unsigned char smem[];
+  unsigned char *sA = smem;                                   // kRowsM x kKC elements
+  unsigned char *sB = smem + (size_t)kRowsM * kKC * ES;       // NP x kKC elements
+  float *sScale = reinterpret_cast<float *>(sB + (size_t)NP * kKC * ES);  // [NP] (FP8)
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tmem_slot;
+  __shared__ int s_abort;
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  uint32_t ncols = 32;
+  while ((int)ncols < NP) ncols <<= 1;
+
+  if (warp == 0) {
+    tmem_alloc(&tmem_slot, ncols);
+    tmem_relinquish();
+  }
+  if (tid == 0) {
+    mbar_init(&mbar, 1);
+    s_abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+  const uint32_t idesc = instr_desc(FM::code, kRowsM, (uint32_t)NP);
+  uint32_t phase_bit = 0;
+  bool ok = true;
+
+  for (int k = blockIdx.x; k < F && ok; k += gridDim.x) {
+    // ---- B: X[k][i][l] for i < NP (zero rows beyond Nu), l < L ----
+    if constexpr (KIND == 2) {
+      // FP16 spectra -> per-column scale -> e4m3
+      const __half2 *Xk = reinterpret_cast<const __half2 *>(Xv) + (size_t)k * Nu * L;
+      for (int i = warp; i < NP; i += kTcThreads / 32) {
+        float m = 0.f;
+        if (i < Nu)
+          for (int l = lane; l < L; l += 32) {
+            const float2 v = __half22float2(Xk[(size_t)i * L + l]);
+            m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)));
+          }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        const float s = (m > 0.f) ? m / 448.f : 1.f;
+        const float inv = 1.f / s;
+        if (lane == 0) sScale[i] = s;
+        // 16-byte core rows: 8 complex elements each
+        for (int c = lane; c < kKC / 16; c += 32) {
+          uint32_t w[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int l0 = c * 8 + 2 * q;
+            float2 a = make_float2(0.f, 0.f), b = make_float2(0.f, 0.f);
+            if (i < Nu && l0 < L) a = __half22float2(Xk[(size_t)i * L + l0]);
+            if (i < Nu && l0 + 1 < L) b = __half22float2(Xk[(size_t)i * L + l0 + 1]);
+            w[q] = pack_e4m3x2(a.x * inv, a.y * inv) | (pack_e4m3x2(b.x * inv, b.y * inv) << 16);
+          }
+          *reinterpret_cast<uint4 *>(sB + core_off<1>(i, c * 16)) = make_uint4(w[0], w[1], w[2], w[3]);
+        }
+      }
+    } else {
+      // BF16 / FP16 spectra: one complex value is 4 bytes, so a 16-byte core
+      // row holds 4 consecutive complex X
+      const uint32_t *Xk = reinterpret_cast<const uint32_t *>(Xv) + (size_t)k * Nu * L;
+      const bool vec = (L & 3) == 0;
+      for (int e = tid; e < NP * (kKC / 8); e += kTcThreads) {
+        const int i = e / (kKC / 8), c = e - i * (kKC / 8);
+        const int l0 = c * 4;
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        if (i < Nu && l0 < L) {
+          if (vec) {
+            v = *reinterpret_cast<const uint4 *>(Xk + (size_t)i * L + l0);
+          } else {
+            uint32_t t[4] = {0u, 0u, 0u, 0u};
+            for (int q = 0; q < 4; ++q)
+              if (l0 + q < L) t[q] = Xk[(size_t)i * L + l0 + q];
+            v = make_uint4(t[0], t[1], t[2], t[3]);
+          }
+        }
+        *reinterpret_cast<uint4 *>(sB + core_off<2>(i, c * 16)) = v;
+      }
+    }
+
+    const unsigned long long kk64 = (unsigned long long)k;
+    for (int m0 = 0; m0 < Mu && ok; m0 += kRowsM / 2) {
+      // ---- A: rows (o, re) / (o, im) of W for o in [m0, m0 + 64) ----
+      constexpr int EPC = FM::EPC;                       // elements per core row
+      constexpr int LPR = EPC / 2;                       // array elements per core row
+      const float wscale = (KIND == 2) ? 64.f : 1.f;
+      for (int e = tid; e < (kRowsM / 2) * (kKC / EPC); e += kTcThreads) {
+        const int ol = e / (kKC / EPC), c = e - ol * (kKC / EPC);
+        const int o = m0 + ol;
+        float wr[LPR], wi[LPR];
+#pragma unroll
+        for (int q = 0; q < LPR; ++q) {
+          const int l = c * LPR + q;
+          wr[q] = wi[q] = 0.f;
+          if (o < Mu && l < L) {
+            const unsigned long long ph = __ldg(phase + (size_t)o * L + l) * kk64;
+            const float ang = (float)(int)(ph >> 32) * 1.4629180792671596e-09f;  // 2 pi / 2^32
+            float sn, cs;
+            __sincosf(ang, &sn, &cs);
+            wr[q] = cs * wscale;
+            wi[q] = sn * wscale;
+          }
+        }
+        uint4 re, im;
+        if constexpr (KIND == 2) {
+          uint32_t r4[4], i4[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            r4[q] = pack_e4m3x2(wr[2 * q], -wi[2 * q]) | (pack_e4m3x2(wr[2 * q + 1], -wi[2 * q + 1]) << 16);
+            i4[q] = pack_e4m3x2(wi[2 * q], wr[2 * q]) | (pack_e4m3x2(wi[2 * q + 1], wr[2 * q + 1]) << 16);
+          }
+          re = make_uint4(r4[0], r4[1], r4[2], r4[3]);
+          im = make_uint4(i4[0], i4[1], i4[2], i4[3]);
+        } else if constexpr (KIND == 0) {
+          re = make_uint4(pack_bf16(wr[0], -wi[0]), pack_bf16(wr[1], -wi[1]), pack_bf16(wr[2], -wi[2]),
+                          pack_bf16(wr[3], -wi[3]));
+          im = make_uint4(pack_bf16(wi[0], wr[0]), pack_bf16(wi[1], wr[1]), pack_bf16(wi[2], wr[2]),
+                          pack_bf16(wi[3], wr[3]));
+        } else {
+          re = make_uint4(pack_f16(wr[0], -wi[0]), pack_f16(wr[1], -wi[1]), pack_f16(wr[2], -wi[2]),
+                          pack_f16(wr[3], -wi[3]));
+          im = make_uint4(pack_f16(wi[0], wr[0]), pack_f16(wi[1], wr[1]), pack_f16(wi[2], wr[2]),
+                          pack_f16(wi[3], wr[3]));
+        }
+        *reinterpret_cast<uint4 *>(sA + core_off<ES>(2 * ol, c * 16)) = re;
+        *reinterpret_cast<uint4 *>(sA + core_off<ES>(2 * ol + 1, c * 16)) = im;
+      }
+      fence_async_smem();
+      __syncthreads();
+      if (tid == 0) {
+        tc_fence_after();
+        const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
+        const int ksteps = (2 * L + FM::KSTEP - 1) / FM::KSTEP;
+#pragma unroll 1
+        for (int s = 0; s < ksteps; ++s) {
+          const uint32_t koff = (uint32_t)s * (FM::KSTEP * ES / 16) * LBO;
+          mma<KIND>(tmem, smem_desc(a0 + koff, LBO, SBO), smem_desc(b0 + koff, LBO, SBO), idesc,
+                    s > 0 ? 1u : 0u);
+        }
+        mma_commit(&mbar);
+      }
+      // all threads wait for the accumulator
+      const bool done = mbar_wait(&mbar, phase_bit);
+      phase_bit ^= 1u;
+      if (!done) {
+        s_abort = 1;
+        ok = false;
+      }
+      __syncthreads();
+      if (s_abort) {
+        ok = false;
+        if (tid == 0) atomicExch(status, (int)KK_ERR_TIMEOUT);
+        // wait (bounded) for the MMAs still in flight before TMEM is freed
+        mbar_wait(&mbar, phase_bit ^ 1u);
+        break;
+      }
+      tc_fence_after();
+      // ---- epilogue: row r = 32 warp + lane -> (o, re|im) ----
+      const int r = warp * 32 + lane;
+      const int o = m0 + (r >> 1), part = r & 1;
+      const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+      float *Yf = reinterpret_cast<float *>(Y + (size_t)k * Nu * Mu);
+      for (int c0 = 0; c0 < NP; c0 += 16) {
+        float v[16];
+        tmem_ld16(trow + (uint32_t)c0, v);
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+          const int i = c0 + q;
+          if (i < Nu && o < Mu) {
+            float val = v[q] * yscale;
+            if constexpr (KIND == 2) val *= sScale[i] * (1.f / 64.f);
+            Yf[((size_t)i * Mu + o) * 2 + part] = val;
+          }
+        }
+      }
+      tc_fence_before();
+      __syncthreads();  // accumulator read and A free before the next tile
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0) tmem_dealloc(tmem, ncols);
+}
+
+}  // namespace
+
+size_t tc_shear_smem_bytes(int precision, int NP) {
+  const int ES = (precision == KK_PREC_F8E4M3) ? 1 : 2;
+  return (size_t)kRowsM * kKC * ES + (size_t)NP * kKC * ES + sizeof(float) * NP;
+}
+
+cudaError_t launch_shear_tc(const kk_plan &p, const void *X, float2 *Y, cudaStream_t s) {
+  const int NP = ((p.Nu + 15) / 16) * 16;
+  const size_t smem = tc_shear_smem_bytes(p.precision, NP);
+  int sms = 148;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p.device);
+  const int grid = std::min(p.F, sms);
+  cudaError_t e;
+  switch (p.precision) {
+    case KK_PREC_BF16: {
+      auto k = k_shear_tc<0>;
+      e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      k<<<grid, kTcThreads, smem, s>>>(X, p.t.phase, p.F, p.L, p.Nu, p.Mu, NP, 1.f / p.x_scale, Y,
+                                       p.t.status);
+      break;
+    }
+    case KK_PREC_F16: {
+      auto k = k_shear_tc<1>;
+      e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      k<<<grid, kTcThreads, smem, s>>>(X, p.t.phase, p.F, p.L, p.Nu, p.Mu, NP, 1.f / p.x_scale, Y,
+                                       p.t.status);
+      break;
+    }
+    case KK_PREC_F8E4M3: {
+      auto k = k_shear_tc<2>;
+      e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      k<<<grid, kTcThreads, smem, s>>>(X, p.t.phase, p.F, p.L, p.Nu, p.Mu, NP, 1.f / p.x_scale, Y,
+                                       p.t.status);
+      break;
+    }
+    default:
+      return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace kk
