@@ -40,7 +40,8 @@ def _args():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--quick", action="store_true", help="skip the side measurements")
-    ap.add_argument("--profile", default=None, choices=["kk_image", "decompose", "das", "vernier"],
+    ap.add_argument("--profile", default=None,
+                    choices=["kk_image", "decompose", "decompose_bf16", "decompose_f8e4m3", "das", "vernier"],
                     help="run three launches of one stage of the benchmark frame and exit "
                          "(a small, bounded target for ncu)")
     return ap.parse_args()
@@ -194,6 +195,17 @@ def _time_loop(fn, reps, flush=None):
     return sum(a.elapsed_time(b) for a, b in evs) / reps
 
 
+FORMS = (("bf16", "KK_PREC_BF16"), ("f32", "KK_PREC_F32"), ("f16", "KK_PREC_F16"),
+         ("f8e4m3", "KK_PREC_F8E4M3"))
+CHOSEN = "bf16"
+
+
+def _form_plan(kb, w, rx, pairs, prec_name, local):
+    return kb.Plan(w.elem_x, w.tx_angles, w.grid, w.c, w.fs, w.n_samples, kb.KK_RF_I16,
+                   rx_angles=rx, pairs=pairs, compound=kb.KK_COMPOUND_COHERENT,
+                   precision=getattr(kb, prec_name), device=local)
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -212,20 +224,24 @@ def run_ours(args):
 
     w = _workload(rank)
     rx, pairs = _full_pairs(w)
-    plan = kb.Plan(w.elem_x, w.tx_angles, w.grid, w.c, w.fs, w.n_samples, kb.KK_RF_I16,
-                   rx_angles=rx, pairs=pairs, compound=kb.KK_COMPOUND_COHERENT, device=local)
+    plans = {name: _form_plan(kb, w, rx, pairs, pn, local) for name, pn in FORMS}
+    plan = plans[CHOSEN]
     info = plan.info
     d_rf = torch.from_numpy(w.rf).to(dev)
-    ws, rt, B, I = plan.empty_workspace(), plan.empty_rf_theta(), plan.empty_image(), plan.empty_intensity()
+    ws = {n: p.empty_workspace() for n, p in plans.items()}
+    rt, B, I = plan.empty_rf_theta(), plan.empty_image(), plan.empty_intensity()
     flush_buf = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
 
     def flush():
         flush_buf.fill_(1)
 
-    def step():
-        plan.decompose(d_rf, rt, ws)
-        plan.beamform(rt, B, I, ws)
+    def make_step(p, wsp):
+        def step():
+            p.decompose(d_rf, rt, wsp)
+            p.beamform(rt, B, I, wsp)
+        return step
 
+    step = make_step(plan, ws[CHOSEN])
     for _ in range(max(args.warmup, 3)):
         step()
     torch.cuda.synchronize()
@@ -251,36 +267,60 @@ def run_ours(args):
     frames = args.steps * world
     value = frames / (ms_total / 1e3)
     launches = args.steps * (info.launches_decompose + info.launches_beamform)
+    status = plan.status()
 
     P, T, npix = info.n_pairs, info.n_samples, info.nx * info.nz
     out = {"metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world,
            "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": round(ms_step, 4),
-           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "bf16 decomposition operands (tcgen05, f32 accumulate); f32 FFTs, interpolation, sums",
            "data": "synthetic (seeded phantom: 20 wires, 3 cysts, 50k speckle; int16 at 30 dB SNR)",
            "config": {"workload": WORKLOAD, "elements": info.n_elem, "transmits": info.n_tx,
                       "samples": T, "rf": "int16", "grid": [info.nx, info.nz], "pairs": P,
                       "receive_angles": info.n_rx_used, "compound": "coherent",
-                      "form": "plain FP32 (decomposition on CUDA cores)",
+                      "form": "chosen: BF16 decomposition on tensor cores (plain FP32 in breakdown)",
                       "l2": "flushed between steps (256 MB write outside the timed events)",
                       "parallelism": f"frames per rank (x{world})"},
-           "gpu_launches": launches, "clocks": clk}
+           "gpu_launches": launches, "clocks": clk, "device_status": status}
 
     if rank == 0 and not args.quick:
         side = {}
         reps = 10
         F = info.n_bins
-        X = torch.empty((F, info.n_tx_used, info.n_elem, 2), device=dev)
-        Y = torch.empty((F, info.n_tx_used, info.n_rx_used, 2), device=dev)
-        ms_spec = _time_loop(lambda: plan.spectrum(d_rf, X), reps, flush)
-        ms_shear = _time_loop(lambda: plan.shear(X, Y), reps, flush)
-        ms_inv = _time_loop(lambda: plan.inverse(Y, rt), reps, flush)
-        ms_bf = _time_loop(lambda: plan.beamform(rt, B, I, ws), reps, flush)
+        # per-form frames/s and stage times on the same frame
+        forms = {}
+        for name, p in plans.items():
+            stp = make_step(p, ws[name])
+            for _ in range(3):
+                stp()
+            ms = _time_loop(stp, reps, flush)
+            X = torch.empty(F * info.n_tx_used * info.n_elem * (8 if name == "f32" else 4),
+                            dtype=torch.uint8, device=dev)
+            Y = torch.empty((F, info.n_tx_used, info.n_rx_used, 2), device=dev)
+            ms_spec = _time_loop(lambda: p.spectrum(d_rf, X), reps, flush)
+            ms_shear = _time_loop(lambda: p.shear(X, Y), reps, flush)
+            forms[name] = {"frames_per_s": round(1e3 / ms, 2), "ms_per_frame": round(ms, 4),
+                           "spectrum_ms": round(ms_spec, 4), "contraction_ms": round(ms_shear, 4)}
+            flops = 8.0 * F * info.n_rx_used * info.n_elem * info.n_tx_used
+            xbytes = F * info.n_tx_used * info.n_elem * (8 if name == "f32" else 4)
+            ybytes = F * info.n_tx_used * info.n_rx_used * 8
+            forms[name]["contraction_tflops"] = round(flops / (ms_shear / 1e3) / 1e12, 2)
+            forms[name]["contraction_hbm_gbs"] = round((xbytes + ybytes) / (ms_shear / 1e3) / 1e9, 1)
+            if name != "f32":
+                forms[name]["contraction_hbm_frac_of_" + peak_src] = round(
+                    (xbytes + ybytes) / (ms_shear / 1e3) / 1e9 / float(peaks["hbm_gbs"]), 3)
+        side["forms"] = forms
+        side["plain_fp32_frames_per_s"] = forms["f32"]["frames_per_s"]
+        Yc = torch.empty((F, info.n_tx_used, info.n_rx_used, 2), device=dev)
+        ms_inv = _time_loop(lambda: plan.inverse(Yc, rt), reps, flush)
+        ms_bf = _time_loop(lambda: plan.beamform(rt, B, I, ws[CHOSEN]), reps, flush)
         pp = float(P) * npix
-        side["stages_ms"] = {"spectrum": round(ms_spec, 4), "shear_contraction_f32": round(ms_shear, 4),
+        side["stages_ms"] = {"spectrum": forms[CHOSEN]["spectrum_ms"],
+                             "contraction": forms[CHOSEN]["contraction_ms"],
                              "inverse": round(ms_inv, 4), "kk_image": round(ms_bf, 4)}
         side["gpixel_pairs_per_s"] = round(pp / (ms_bf / 1e3) / 1e9, 2)
         # roofline of the dominant kernel: the KK gather, bound by the SM's
-        # shared-memory pipe: one 16-byte (y, dy) load per pixel-pair at
+        # shared-memory pipe: one 16-byte (y[k], y[k+1]) load per pixel-pair at
         # 128 B/clk/SM -> 8 pixel-pairs per clock per SM
         sm_max = float(peaks.get("sm_max_mhz", 2070.0))
         peak_pp = 8.0 * n_sm * sm_max * 1e6 / 1e9
@@ -295,16 +335,13 @@ def run_ours(args):
             "algorithmic_hbm_bytes": hbm_bytes,
             "hbm_gbs": round(hbm_bytes / (ms_bf / 1e3) / 1e9, 1),
             "hbm_frac_of_" + peak_src: round(hbm_bytes / (ms_bf / 1e3) / 1e9 / float(peaks["hbm_gbs"]), 4)}
-        # decomposition contraction (FP32 on CUDA cores): ALU roofline
-        flops = 8.0 * F * info.n_rx_used * info.n_elem * info.n_tx_used
-        fp32_peak = 2.0 * 128 * n_sm * sm_max * 1e6 / 1e12
-        side["shear_contraction"] = {"tflops": round(flops / (ms_shear / 1e3) / 1e12, 2),
-                                     "fp32_peak_tflops": round(fp32_peak, 1),
-                                     "frac": round(flops / (ms_shear / 1e3) / 1e12 / fp32_peak, 3)}
-        spec_bytes = info.rf_bytes + F * info.n_tx_used * info.n_elem * 8
+        spec_bytes = info.rf_bytes + F * info.n_tx_used * info.n_elem * 4
         inv_bytes = F * info.n_tx_used * info.n_rx_used * 8 + P * T * 8
-        side["spectrum_hbm_gbs"] = round(spec_bytes / (ms_spec / 1e3) / 1e9, 1)
+        side["spectrum_hbm_gbs"] = round(spec_bytes / (forms[CHOSEN]["spectrum_ms"] / 1e3) / 1e9, 1)
         side["inverse_hbm_gbs"] = round(inv_bytes / (ms_inv / 1e3) / 1e9, 1)
+        fp32_peak = 2.0 * 128 * n_sm * sm_max * 1e6 / 1e12
+        side["fp32_contraction_frac_of_fp32_alu_peak"] = round(
+            forms["f32"]["contraction_tflops"] / fp32_peak, 3)
         # vernier 8 x 16 pair subset (128 pairs) and DAS on the same frame
         vrx, vpairs = _vernier_pairs(w, kb)
         vplan = kb.Plan(w.elem_x, w.tx_angles, w.grid, w.c, w.fs, w.n_samples, kb.KK_RF_I16,
@@ -344,7 +381,7 @@ def run_ours(args):
                       "d2h_bytes_per_step": int(info.image_bytes + info.intensity_bytes),
                       "wall_ms_per_step": round((time.perf_counter() - t0) * 1e3 / k_e2e, 3)}
         if world == 1 and not args.no_cpu_baseline:
-            out["cpu_baseline"] = cpu_baseline(w, rx, pairs)
+            out["cpu_baseline"] = cpu_baseline(w, rx, pairs, plans)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:
@@ -352,7 +389,7 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def _oracle_frame_seconds(w, rx, pairs, rx_keep, rows):
+def _oracle_frame_seconds(w, rx, pairs, rx_keep, rows, keep_image=False):
     """Oracle time for the decomposition of the pairs whose receive angle is in
     rx_keep (every decomposition cost but the small analytic FFT scales with
     the number of receive angles) and image formation of `rows` grid rows over
@@ -375,10 +412,12 @@ def _oracle_frame_seconds(w, rx, pairs, rx_keep, rows):
     yy = np.zeros((ps.n_pairs, w.n_samples), np.complex128)
     yy[keep] = y
     t0 = time.perf_counter()
-    kk.kk_beamform(yy, w.elem_x, ps, w.grid, w.fs, w.c, pixels=pix)
+    img = kk.kk_beamform(yy, w.elem_x, ps, w.grid, w.fs, w.c, pixels=pix)
     t_bf = time.perf_counter() - t0
     frac_dec = keep.sum() / ps.n_pairs
     t_dec_frame = t_fft + max(t_dec - t_fft, 0.0) / frac_dec
+    if keep_image:
+        return t_dec_frame + t_bf * (nz / rows), t_dec, t_bf, img[0]
     return t_dec_frame + t_bf * (nz / rows), t_dec, t_bf
 
 
@@ -398,12 +437,14 @@ def run_profile(args):
             dplan.das(d_rf, B, I, ws)
     else:
         rx, pairs = _vernier_pairs(w, kb) if args.profile == "vernier" else _full_pairs(w)
+        prec = {"decompose_bf16": kb.KK_PREC_BF16, "decompose_f8e4m3": kb.KK_PREC_F8E4M3}.get(
+            args.profile, kb.KK_PREC_F32)
         plan = kb.Plan(w.elem_x, w.tx_angles, w.grid, w.c, w.fs, w.n_samples, kb.KK_RF_I16,
-                       rx_angles=rx, pairs=pairs, compound=kb.KK_COMPOUND_COHERENT)
+                       rx_angles=rx, pairs=pairs, compound=kb.KK_COMPOUND_COHERENT, precision=prec)
         ws, rt, B, I = plan.empty_workspace(), plan.empty_rf_theta(), plan.empty_image(), plan.empty_intensity()
         plan.decompose(d_rf, rt, ws)
         for _ in range(3):
-            if args.profile in ("decompose", "vernier"):
+            if args.profile.startswith("decompose") or args.profile == "vernier":
                 plan.decompose(d_rf, rt, ws)
             if args.profile in ("kk_image", "vernier"):
                 plan.beamform(rt, B, I, ws)
@@ -411,41 +452,37 @@ def run_profile(args):
     print(f"profile target {args.profile}: done")
 
 
-def _gpu_rows_vs_oracle(w, rx, pairs, rows):
-    """rel-L2 of the GPU image's first `rows` rows against the FP64 oracle."""
+def _gpu_rows(plan, w, rows):
+    """First `rows` rows of the plan's image of the frame (complex128)."""
     import numpy as np
     import torch
-    import paper_2603_22496_gb300 as kb
-    from oracle import kk, schemes
-    plan = kb.Plan(w.elem_x, w.tx_angles, w.grid, w.c, w.fs, w.n_samples, kb.KK_RF_I16,
-                   rx_angles=rx, pairs=pairs)
-    ws, rt, B = plan.empty_workspace(), plan.empty_rf_theta(), plan.empty_image()
+    ws, rt, B, I = plan.empty_workspace(), plan.empty_rf_theta(), plan.empty_image(), plan.empty_intensity()
     plan.decompose(torch.from_numpy(w.rf).cuda(), rt, ws)
-    plan.beamform(rt, B, None, ws)
+    plan.beamform(rt, B, I, ws)
     torch.cuda.synchronize()
     g = B[0, :rows].cpu().numpy().astype(np.float64)
-    g = g[..., 0] + 1j * g[..., 1]
-    ps = schemes.PairSet(w.tx_angles, rx, pairs[:, 0].astype(np.int64),
-                         pairs[:, 1].astype(np.int64), np.zeros(pairs.shape[0], np.int64), 1)
-    pix = np.array([(ix, iz) for iz in range(rows) for ix in range(w.grid[0])])
-    ref = kk.kk_image(w.rf, w.elem_x, ps, w.grid, w.fs, w.c, pixels=pix)[0]
-    return kk.rel_l2(g.ravel(), ref)
+    return (g[..., 0] + 1j * g[..., 1]).ravel()
 
 
-def cpu_baseline(w, rx, pairs):
+def cpu_baseline(w, rx, pairs, plans=None):
     import numpy as np
     cores = os.cpu_count()
     rx_keep = np.arange(128)                          # the whole decomposition
     rows = 32
-    sec, t_dec, t_bf = _oracle_frame_seconds(w, rx, pairs, rx_keep, rows)
+    sec, t_dec, t_bf, ref = _oracle_frame_seconds(w, rx, pairs, rx_keep, rows, keep_image=True)
     out = {"value": round(1.0 / sec, 5), "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"FP64 oracle: decomposition of all 9600 pairs "
                       f"({t_dec:.2f} s) and image formation of {rows}/512 rows over all 9600 pairs "
                       f"({t_bf:.2f} s), scaled to one frame"}
-    try:
-        out["gpu_rel_l2_first_32_rows"] = _gpu_rows_vs_oracle(w, rx, pairs, 32)
-    except Exception as e:  # pragma: no cover - report, do not hide
-        out["gpu_rel_l2_first_32_rows"] = f"error: {e}"
+    if plans:
+        from oracle import kk
+        rel = {}
+        for name, p in plans.items():
+            try:
+                rel[name] = kk.rel_l2(_gpu_rows(p, w, rows), ref)
+            except Exception as e:  # pragma: no cover - report, do not hide
+                rel[name] = f"error: {e}"
+        out["gpu_rel_l2_vs_oracle_first_32_rows"] = rel
     return out
 
 

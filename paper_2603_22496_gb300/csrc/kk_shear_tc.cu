@@ -12,11 +12,12 @@
 // interleaved layout; A is generated on chip from the 0.64 fixed-point phases
 // (never stored in HBM).
 //
-// One CTA (one warpgroup) per bin at a time: it copies B into shared memory,
-// then for each tile of 64 receive angles (128 rows of A) generates A, one
-// thread issues K/16 (K/32 for FP8) tcgen05.mma into a TMEM accumulator of
-// 128 lanes x N columns, commits to an mbarrier, and the four warps read the
-// accumulator back (tcgen05.ld) and store Y.
+// Each CTA (two warpgroups, two CTAs per SM) takes one bin at a time: it
+// copies B into shared memory, then for each tile of 64 receive angles (128
+// rows of A) generates A, one thread issues K/16 (K/32 for FP8) tcgen05.mma
+// into a TMEM accumulator of 128 lanes x N columns, commits to an mbarrier,
+// and the eight warps read the accumulator back (tcgen05.ld; warp w reads
+// lane quarter w % 4) and store Y.
 //
 // Shared-memory operands use the no-swizzle K-major canonical layout: 8-row x
 // 16-byte core matrices, K-adjacent core matrices 128 bytes apart (LBO), 8-row
@@ -38,7 +39,7 @@ namespace kk {
 
 namespace {
 
-constexpr int kTcThreads = 128;
+constexpr int kTcThreads = 256;        // two warpgroups
 constexpr int kKC = 256;                 // K elements per pass (128 array elements)
 constexpr int kRowsM = 128;              // rows of A per tile (64 receive angles)
 constexpr unsigned long long kWaitNs = 200000000ull;  // 200 ms
@@ -180,7 +181,7 @@ __device__ __forceinline__ uint32_t core_off(int row, int kbyte) {
 }
 
 template <int KIND>
-__global__ void __launch_bounds__(kTcThreads, 1)
+__global__ void __launch_bounds__(kTcThreads, 2)
     k_shear_tc(const void *__restrict__ Xv, const unsigned long long *__restrict__ phase, int F,
                int L, int Nu, int Mu, int NP, float yscale, float2 *__restrict__ Y,
                int *__restrict__ status) {
@@ -348,12 +349,14 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         break;
       }
       tc_fence_after();
-      // ---- epilogue: row r = 32 warp + lane -> (o, re|im) ----
-      const int r = warp * 32 + lane;
+      // ---- epilogue: warp w reads TMEM lane quarter w % 4 (rows r = 32 (w % 4)
+      // + lane -> (o, re|im)) and every other 16-column chunk from w / 4 ----
+      const int quarter = warp & 3, half = warp >> 2;
+      const int r = quarter * 32 + lane;
       const int o = m0 + (r >> 1), part = r & 1;
-      const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+      const uint32_t trow = tmem + ((uint32_t)(quarter * 32) << 16);
       float *Yf = reinterpret_cast<float *>(Y + (size_t)k * Nu * Mu);
-      for (int c0 = 0; c0 < NP; c0 += 16) {
+      for (int c0 = 16 * half; c0 < NP; c0 += 32) {
         float v[16];
         tmem_ld16(trow + (uint32_t)c0, v);
 #pragma unroll
@@ -388,7 +391,7 @@ cudaError_t launch_shear_tc(const kk_plan &p, const void *X, float2 *Y, cudaStre
   const size_t smem = tc_shear_smem_bytes(p.precision, NP);
   int sms = 148;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p.device);
-  const int grid = std::min(p.F, sms);
+  const int grid = std::min(p.F, 2 * sms);
   cudaError_t e;
   switch (p.precision) {
     case KK_PREC_BF16: {
