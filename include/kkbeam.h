@@ -247,6 +247,50 @@ kk_status das_beamform(const kk_plan *p, const void *d_rf, void *d_B,
                        float *d_I, void *d_workspace, void *stream);
 
 /*
+ * Batched form (no counterpart in the paper: a throughput form of steps 1
+ * and 2 for many frames).  Frames may differ in array, record length,
+ * transmit set, pair set and grid; each has its own KK plan and buffers.
+ *
+ * kk_batch_create builds a CUDA graph that runs every frame's decomposition
+ * (frames run concurrently) and then KK image formation for all frames as
+ * one persistent launch over their (frame, tile) work items, largest frames
+ * first.  shape = 0 picks the image-formation launch shape by timing the
+ * feasible shapes on this batch (the kernels run on the frames' buffers;
+ * creation first synchronises `stream`, then works on a private stream and
+ * returns when done); shape = rows * 100 + stage (rows in
+ * {2, 4, 8}, stage in {4, 8, 16}) sets it.  Results match the per-frame calls
+ * up to FP32 summation order.  The buffers given here are baked into the
+ * graph: refill them in place between runs.  Each frame needs its own
+ * workspace (frames run concurrently).
+ *
+ * kk_batch_run enqueues the graph on `stream`.  A batch must not run twice
+ * concurrently (it owns one work counter).
+ */
+typedef struct kk_batch kk_batch;
+
+typedef struct kk_batch_frame {
+  const kk_plan *plan;   /* KK plan of the frame */
+  const void *d_rf;      /* [N][L][T] int16 / float32 */
+  void *d_rf_theta;      /* [P][T] cfloat */
+  void *d_B;             /* [J][nz][nx] cfloat */
+  float *d_I;            /* [nz][nx], required when the plan compounds */
+  void *d_workspace;     /* >= the plan's workspace_bytes, 256-byte aligned */
+} kk_batch_frame;
+
+typedef struct kk_batch_info {
+  int32_t n_frames, n_items, rows, stage, max_window, grid, graph_nodes, n_tuned;
+  double pixel_pairs;      /* sum over frames of pairs x pixels */
+  int32_t tuned_shape[16]; /* shapes timed by the autotuner (rows * 100 + stage) */
+  float tuned_ms[16];      /* their image-formation times */
+} kk_batch_info;
+
+kk_status kk_batch_create(kk_batch **out, const kk_batch_frame *frames, int32_t n_frames,
+                          int32_t shape, void *stream);
+kk_status kk_batch_run(kk_batch *b, void *stream);
+kk_status kk_batch_get_info(const kk_batch *b, kk_batch_info *info);
+void kk_batch_destroy(kk_batch *b);
+
+/*
  * End to end from host memory: copies h_rf to the device, runs
  * kk_decompose + kk_beamform (or das_beamform for a DAS plan), copies B and
  * I back.  All on `stream`; returns after enqueueing (the caller
@@ -259,6 +303,23 @@ kk_status das_beamform(const kk_plan *p, const void *d_rf, void *d_B,
 kk_status kk_run_host_scratch_size(const kk_plan *p, size_t *bytes);
 kk_status kk_run_host(const kk_plan *p, const void *h_rf, void *h_B, float *h_I,
                       void *d_scratch, void *stream);
+
+/*
+ * Synthetic channel data on the GPU (input generation, not the method; the
+ * paper has no counterpart).  rf[i][l][t] = sum_s a_s p(t/fs - tau_in - tau_out)
+ * + optional white Gaussian noise, with tau_in = (x sin_i + z cos_i)/c,
+ * tau_out = |(x, z) - (u_l, 0)|/c and p(t) = exp(-alpha t^2) cos(2 pi f0 t)
+ * (spectrum -6 dB at f0 (1 +- bw/2), truncated at +-4 sigma), in FP32.
+ * d_tx_sincos [N][2] (sin, cos) of the transmit angles; d_elem_x [L] element
+ * positions (m); d_scat [n_scat][4] (x, z, amplitude, unused); noise from a
+ * counter-based generator seeded by `seed`.  d_rf [N][L][T] float32.
+ * Accumulation order is not fixed (shared-memory atomics): repeated calls
+ * may differ in the last bits.
+ */
+kk_status kk_simulate_rf(int32_t n_tx, const float *d_tx_sincos, int32_t n_elem,
+                         const float *d_elem_x, int32_t T, double fs, double c, double f0,
+                         double bw, int32_t n_scat, const float *d_scat, double noise_sigma,
+                         uint64_t seed, float *d_rf, void *stream);
 
 /*
  * Receive angles of one scheme (pure host, FP64):

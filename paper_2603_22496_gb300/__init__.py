@@ -32,7 +32,9 @@ _STATUS = {0: "KK_OK", 1: "KK_ERR_INVALID_ARG", 2: "KK_ERR_UNSUPPORTED", 3: "KK_
 EXPORTS = ["kk_plan_create", "das_plan_create", "kk_plan_destroy", "kk_plan_get_info",
            "kk_plan_set_gather", "kk_plan_status", "kk_plan_workspace_size", "kk_decompose", "kk_spectrum", "kk_shear", "kk_inverse",
            "kk_beamform", "kk_beamform_noalloc", "das_beamform", "kk_run_host_scratch_size", "kk_run_host",
-           "kk_scheme_angles", "kk_last_error", "kk_version"]
+           "kk_scheme_angles", "kk_last_error", "kk_version",
+           "kk_batch_create", "kk_batch_run", "kk_batch_get_info", "kk_batch_destroy",
+           "kk_simulate_rf"]
 
 
 class KKError(RuntimeError):
@@ -72,6 +74,19 @@ class kk_plan_info(ctypes.Structure):
                 ("rf_theta_bytes", ctypes.c_size_t), ("image_bytes", ctypes.c_size_t),
                 ("intensity_bytes", ctypes.c_size_t), ("compression_factor", ctypes.c_double),
                 ("launches_decompose", ctypes.c_int32), ("launches_beamform", ctypes.c_int32)]
+
+
+class kk_batch_frame(ctypes.Structure):
+    _fields_ = [("plan", ctypes.c_void_p), ("d_rf", ctypes.c_void_p), ("d_rf_theta", ctypes.c_void_p),
+                ("d_B", ctypes.c_void_p), ("d_I", ctypes.c_void_p), ("d_workspace", ctypes.c_void_p)]
+
+
+class kk_batch_info(ctypes.Structure):
+    _fields_ = [("n_frames", ctypes.c_int32), ("n_items", ctypes.c_int32), ("rows", ctypes.c_int32),
+                ("stage", ctypes.c_int32), ("max_window", ctypes.c_int32), ("grid", ctypes.c_int32),
+                ("graph_nodes", ctypes.c_int32), ("n_tuned", ctypes.c_int32),
+                ("pixel_pairs", ctypes.c_double), ("tuned_shape", ctypes.c_int32 * 16),
+                ("tuned_ms", ctypes.c_float * 16)]
 
 
 _lib = None
@@ -114,6 +129,13 @@ def load(build_if_missing: bool = False):
         "kk_run_host": ([vp, vp, vp, vp, vp, vp], st),
         "kk_scheme_angles": ([ctypes.c_int32, ctypes.c_int32, _dp, ctypes.c_double,
                               ctypes.c_int32, ctypes.c_double, _dp], st),
+        "kk_batch_create": ([pp, ctypes.POINTER(kk_batch_frame), ctypes.c_int32, ctypes.c_int32, vp], st),
+        "kk_batch_run": ([vp, vp], st),
+        "kk_batch_get_info": ([vp, ctypes.POINTER(kk_batch_info)], st),
+        "kk_batch_destroy": ([vp], None),
+        "kk_simulate_rf": ([ctypes.c_int32, vp, ctypes.c_int32, vp, ctypes.c_int32, ctypes.c_double,
+                            ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int32, vp,
+                            ctypes.c_double, ctypes.c_uint64, vp, vp], st),
         "kk_last_error": ([], ctypes.c_char_p),
         "kk_version": ([], ctypes.c_char_p),
     }
@@ -360,3 +382,58 @@ class Plan:
 
     def scratch_bytes(self) -> int:
         return kk_run_host_scratch_size(self.handle)
+
+
+class Batch:
+    """Owner of a kk_batch: many frames (each a Plan with its own buffers) in
+    one CUDA graph with a persistent image-formation launch."""
+
+    def __init__(self, frames, shape: int = 0, stream=None):
+        """frames: list of dicts with keys plan, rf, rf_theta, B, I (or None),
+        workspace (torch CUDA tensors).  shape 0 = autotune."""
+        self._frames = frames          # keep the tensors alive
+        arr = (kk_batch_frame * len(frames))()
+        for k, f in enumerate(frames):
+            arr[k] = kk_batch_frame(f["plan"].handle, _ptr(f["rf"]).value, _ptr(f["rf_theta"]).value,
+                                    _ptr(f["B"]).value, _ptr(f.get("I")).value or None,
+                                    _ptr(f["workspace"]).value)
+        h = ctypes.c_void_p()
+        _check(load().kk_batch_create(ctypes.byref(h), arr, len(frames), int(shape), _stream(stream)))
+        self.handle = h
+        self.info = kk_batch_info()
+        _check(load().kk_batch_get_info(h, ctypes.byref(self.info)))
+
+    def run(self, stream=None):
+        _check(load().kk_batch_run(self.handle, _stream(stream)))
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h:
+            try:
+                load().kk_batch_destroy(h)
+            except Exception:
+                pass
+            self.handle = None
+
+
+def kk_simulate_rf(tx_angles, elem_x, n_samples, scatterers, fs, c, f0=5e6, bw=0.6,
+                   noise_sigma=0.0, seed=0, out=None, stream=None):
+    """GPU synthetic RF (input generation).  scatterers: CUDA float32 [n][4]
+    (x, z, amplitude, unused) or [n][3]; returns / fills float32 [N][L][T]."""
+    import torch
+    dev = scatterers.device if hasattr(scatterers, "device") else torch.device("cuda")
+    tx = torch.as_tensor(np.asarray(tx_angles, dtype=np.float64))
+    sc = torch.stack([torch.sin(tx), torch.cos(tx)], -1).float().contiguous().to(dev)
+    ex = torch.as_tensor(np.asarray(elem_x, dtype=np.float32)).contiguous().to(dev)
+    sct = scatterers.float()
+    if sct.shape[1] == 3:
+        sct = torch.cat([sct, torch.zeros_like(sct[:, :1])], 1)
+    sct = sct.contiguous()
+    N, L = sc.shape[0], ex.shape[0]
+    if out is None:
+        out = torch.empty((N, L, int(n_samples)), dtype=torch.float32, device=dev)
+    _check(load().kk_simulate_rf(N, _ptr(sc), L, _ptr(ex), int(n_samples), float(fs), float(c),
+                                 float(f0), float(bw), int(sct.shape[0]), _ptr(sct),
+                                 float(noise_sigma), int(seed) & (2**64 - 1), _ptr(out),
+                                 _stream(stream)))
+    return out

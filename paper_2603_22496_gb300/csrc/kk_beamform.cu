@@ -67,31 +67,46 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 
 __device__ __forceinline__ float2 f2add(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 
-template <int ROWS, int STAGE, int NPT, int MINB, bool MULTI>
-__global__ void __launch_bounds__(kGatherThreads, MINB)
-    k_kk_gather(const float2 *__restrict__ rf_theta, int T, const int32_t *__restrict__ bf_row,
-                const long long *__restrict__ bfA, const long long *__restrict__ bfB,
-                const long long *__restrict__ bfC, const float *__restrict__ bfAf,
-                const float *__restrict__ bfBf, const int32_t *__restrict__ group_start, int J,
-                int nx, int nz, int tiles_x, int win, int split, float2 *__restrict__ out,
-                float *__restrict__ I, int compound) {
+// Per-pair state of the delay tables, double-buffered by stage.
+template <int STAGE>
+struct GatherSmem {
+  WarpPair wp[2][4][STAGE];
+  PairSrc src[2][STAGE];
+  PairIn in[2][STAGE];
+};
+
+// One tile (and pair slice) of KK image formation; shared by the per-plan
+// kernel and the batched persistent kernel.
+template <int ROWS, int STAGE, int NPT, bool MULTI>
+__device__ __forceinline__ void gather_tile(const GatherArgs &a, int tile, int sidx, float4 *sw,
+                                            GatherSmem<STAGE> &sm) {
+  const float2 *__restrict__ rf_theta = a.rf_theta;
+  const int T = a.T;
+  const int32_t *__restrict__ bf_row = a.bf_row;
+  const long long *__restrict__ bfA = a.bfA;
+  const long long *__restrict__ bfB = a.bfB;
+  const long long *__restrict__ bfC = a.bfC;
+  const float *__restrict__ bfAf = a.bfAf;
+  const float *__restrict__ bfBf = a.bfBf;
+  const int32_t *__restrict__ group_start = a.group_start;
+  const int J = a.J, nx = a.nx, nz = a.nz, tiles_x = a.tiles_x, win = a.win, split = a.split;
+  float2 *__restrict__ out = a.out;
+  float *__restrict__ I = a.I;
+  const int compound = a.compound;
+  auto &s_wp = sm.wp;
+  auto &s_src = sm.src;
+  auto &s_in = sm.in;
   static_assert(STAGE <= 32 && STAGE % 4 == 0, "one table thread per (pair, warp)");
   static_assert(NPT <= kMaxStagedEntries, "staged entries held in registers");
   constexpr int TZ = 4 * ROWS;
   constexpr int PPW = STAGE / 4;          // pairs staged by each warp
   constexpr int QPP = NPT / PPW;          // entries per lane per staged pair
   static_assert(QPP * PPW == NPT, "NPT must be a multiple of STAGE / 4");
-  extern __shared__ float4 sw[];          // [STAGE][win] staged entries
-  __shared__ WarpPair s_wp[2][4][STAGE];
-  __shared__ PairSrc s_src[2][STAGE];
-  __shared__ PairIn s_in[2][STAGE];
-
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
   const int tj = tid & 31, tw = tid >> 5;  // table thread: pair tj, warp reference tw
-  const int sidx = blockIdx.y;
-  const int ix0 = (blockIdx.x % tiles_x) * kTileX;
-  const int iz0 = (blockIdx.x / tiles_x) * TZ;
+  const int ix0 = (tile % tiles_x) * kTileX;
+  const int iz0 = (tile / tiles_x) * TZ;
   const int ix = ix0 + lane;
   const int izb = iz0 + warp * ROWS;
   const float dl = (float)(lane - 16);
@@ -305,6 +320,34 @@ __global__ void __launch_bounds__(kGatherThreads, MINB)
   }
 }
 
+template <int ROWS, int STAGE, int NPT, int MINB, bool MULTI>
+__global__ void __launch_bounds__(kGatherThreads, MINB) k_kk_gather(const GatherArgs a) {
+  extern __shared__ float4 sw[];  // [STAGE][win] staged entries
+  __shared__ GatherSmem<STAGE> sm;
+  gather_tile<ROWS, STAGE, NPT, MULTI>(a, blockIdx.x, blockIdx.y, sw, sm);
+}
+
+// Batched form: a persistent grid pulls (frame, tile) work items, largest
+// frames first, from an atomic counter until the list is exhausted.
+template <int ROWS, int STAGE, int NPT, int MINB>
+__global__ void __launch_bounds__(kGatherThreads, MINB)
+    k_kk_gather_batch(const GatherArgs *__restrict__ frames, const int2 *__restrict__ items,
+                      int n_items, int *__restrict__ counter) {
+  extern __shared__ float4 sw[];
+  __shared__ GatherSmem<STAGE> sm;
+  __shared__ int s_item;
+  for (;;) {
+    __syncthreads();  // previous item fully done with shared memory
+    if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
+    __syncthreads();
+    const int it = s_item;
+    if (it >= n_items) break;
+    const int2 w = items[it];
+    const GatherArgs a = frames[w.x];
+    gather_tile<ROWS, STAGE, NPT, true>(a, w.y, 0, sw, sm);
+  }
+}
+
 // Sum the pair-slice partials in slice order and compound.
 __global__ void k_kk_reduce(const float2 *__restrict__ part, int split, int J, int npix,
                             float2 *__restrict__ B, float *__restrict__ I, int compound) {
@@ -334,10 +377,7 @@ cudaError_t launch_cfg(const kk_plan &p, const float2 *rf_theta, float2 *dst, fl
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const dim3 grid(p.tiles_x * p.tiles_z, p.bf_split);
-  k<<<grid, kGatherThreads, smem, s>>>(rf_theta, p.T, p.t.bf_row, p.t.bf_A, p.t.bf_B, p.t.bf_C,
-                                       p.t.bf_Af, p.t.bf_Bf, p.t.group_start, p.J, p.grid.nx,
-                                       p.grid.nz, p.tiles_x, p.bf_win, p.bf_split, dst, I,
-                                       p.compound);
+  k<<<grid, kGatherThreads, smem, s>>>(gather_args(p, rf_theta, dst, I));
   return cudaGetLastError();
 }
 
@@ -364,6 +404,77 @@ cudaError_t launch_rs(const kk_plan &p, const float2 *rf_theta, float2 *dst, flo
 }
 
 }  // namespace
+
+GatherArgs gather_args(const kk_plan &p, const float2 *rf_theta, float2 *dst, float *I) {
+  GatherArgs a;
+  a.rf_theta = rf_theta;
+  a.T = p.T;
+  a.bf_row = p.t.bf_row;
+  a.bfA = p.t.bf_A;
+  a.bfB = p.t.bf_B;
+  a.bfC = p.t.bf_C;
+  a.bfAf = p.t.bf_Af;
+  a.bfBf = p.t.bf_Bf;
+  a.group_start = p.t.group_start;
+  a.J = p.J;
+  a.nx = p.grid.nx;
+  a.nz = p.grid.nz;
+  a.tiles_x = p.tiles_x;
+  a.win = p.bf_win;
+  a.split = p.bf_split;
+  a.out = dst;
+  a.I = I;
+  a.compound = p.compound;
+  return a;
+}
+
+template <int ROWS, int STAGE, int NPT>
+static cudaError_t batch_cfg(const GatherArgs *frames, const int2 *items, int n_items, int *counter,
+                             int max_win, int grid, cudaStream_t s) {
+  auto k = k_kk_gather_batch<ROWS, STAGE, NPT, (ROWS <= 4 ? 8 : 5)>;
+  const size_t smem = sizeof(float4) * (size_t)STAGE * max_win;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k<<<grid, kGatherThreads, smem, s>>>(frames, items, n_items, counter);
+  return cudaGetLastError();
+}
+
+template <int ROWS, int STAGE>
+static cudaError_t batch_rs(const GatherArgs *frames, const int2 *items, int n_items, int *counter,
+                            int max_win, int grid, cudaStream_t s) {
+  constexpr int PPW = STAGE / 4;
+  const int q = gather_entries_per_lane(max_win);
+  if constexpr (PPW * 1 <= kMaxStagedEntries) {
+    if (q == 1) return batch_cfg<ROWS, STAGE, PPW>(frames, items, n_items, counter, max_win, grid, s);
+  }
+  if constexpr (PPW * 2 <= kMaxStagedEntries) {
+    if (q == 2) return batch_cfg<ROWS, STAGE, PPW * 2>(frames, items, n_items, counter, max_win, grid, s);
+  }
+  if constexpr (PPW * 4 <= kMaxStagedEntries) {
+    if (q <= 4) return batch_cfg<ROWS, STAGE, PPW * 4>(frames, items, n_items, counter, max_win, grid, s);
+  }
+  if constexpr (PPW * 8 <= kMaxStagedEntries) {
+    if (q <= 8) return batch_cfg<ROWS, STAGE, PPW * 8>(frames, items, n_items, counter, max_win, grid, s);
+  }
+  return cudaErrorInvalidConfiguration;
+}
+
+cudaError_t launch_kk_gather_batch(int rows, int stage, const GatherArgs *frames, const int2 *items,
+                                   int n_items, int *counter, int max_win, int grid,
+                                   cudaStream_t s) {
+  switch (rows * 100 + stage) {
+    case 204: return batch_rs<2, 4>(frames, items, n_items, counter, max_win, grid, s);
+    case 208: return batch_rs<2, 8>(frames, items, n_items, counter, max_win, grid, s);
+    case 216: return batch_rs<2, 16>(frames, items, n_items, counter, max_win, grid, s);
+    case 404: return batch_rs<4, 4>(frames, items, n_items, counter, max_win, grid, s);
+    case 408: return batch_rs<4, 8>(frames, items, n_items, counter, max_win, grid, s);
+    case 416: return batch_rs<4, 16>(frames, items, n_items, counter, max_win, grid, s);
+    case 804: return batch_rs<8, 4>(frames, items, n_items, counter, max_win, grid, s);
+    case 808: return batch_rs<8, 8>(frames, items, n_items, counter, max_win, grid, s);
+    case 816: return batch_rs<8, 16>(frames, items, n_items, counter, max_win, grid, s);
+    default: return cudaErrorInvalidConfiguration;
+  }
+}
 
 int gather_entries_per_lane(int win) {
   const int q = (win + 31) / 32;

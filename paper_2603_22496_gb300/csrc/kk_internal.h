@@ -101,6 +101,32 @@ constexpr int kMaxStagedEntries = 8;
 int gather_entries_per_lane(int win);
 bool gather_config_supported(int rows, int stage, int win);
 
+// Arguments of one frame's KK gather (also the batched form's per-frame
+// descriptor, copied to the device).
+struct GatherArgs {
+  const float2 *rf_theta;
+  int T;
+  const int32_t *bf_row;
+  const long long *bfA, *bfB, *bfC;
+  const float *bfAf, *bfBf;
+  const int32_t *group_start;
+  int J, nx, nz, tiles_x, win, split;
+  float2 *out;
+  float *I;
+  int compound;
+};
+
+// Keeps the caller's current device and restores it on exit.
+struct DeviceGuard {
+  int old = -1;
+  bool ok = true;
+  explicit DeviceGuard(int dev);
+  ~DeviceGuard();
+};
+
+// spectrum -> contraction -> inverse of one frame on stream s (no checks)
+kk_status enqueue_decompose(const kk_plan *p, const void *rf, void *rf_theta, void *ws, cudaStream_t s);
+
 // thread-local error message
 void set_error(const std::string &msg);
 kk_status cuda_fail(cudaError_t e, const char *what);
@@ -119,6 +145,11 @@ size_t tc_shear_smem_bytes(int precision, int NP);
 inline int spectrum_bytes(int precision) { return precision == KK_PREC_F32 ? 8 : 4; }
 cudaError_t launch_kk_gather(const kk_plan &p, const float2 *rf_theta, float2 *B, float *I,
                              float2 *partial, cudaStream_t s);
+GatherArgs gather_args(const kk_plan &p, const float2 *rf_theta, float2 *dst, float *I);
+// persistent gather over n_items (frame, tile) items; *counter must be 0
+cudaError_t launch_kk_gather_batch(int rows, int stage, const GatherArgs *frames, const int2 *items,
+                                   int n_items, int *counter, int max_win, int grid,
+                                   cudaStream_t s);
 cudaError_t launch_das_gather(const kk_plan &p, const float2 *y, float2 *B, float *I,
                               float2 *partial, cudaStream_t s);
 

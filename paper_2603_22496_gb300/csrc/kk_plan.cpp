@@ -13,6 +13,15 @@
 
 namespace kk {
 
+DeviceGuard::DeviceGuard(int dev) {
+  if (cudaGetDevice(&old) != cudaSuccess) old = -1;
+  if (old != dev) ok = cudaSetDevice(dev) == cudaSuccess;
+}
+DeviceGuard::~DeviceGuard() {
+  int cur = -1;
+  if (old >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != old) cudaSetDevice(old);
+}
+
 static thread_local std::string g_err;
 
 void set_error(const std::string &msg) { g_err = msg; }
@@ -31,19 +40,6 @@ constexpr size_t kAlign = 256;
 
 size_t align_up(size_t v, size_t a = kAlign) { return (v + a - 1) / a * a; }
 
-// Keeps the caller's current device and restores it on exit.
-struct DeviceGuard {
-  int old = -1;
-  bool ok = true;
-  explicit DeviceGuard(int dev) {
-    if (cudaGetDevice(&old) != cudaSuccess) old = -1;
-    if (old != dev) ok = cudaSetDevice(dev) == cudaSuccess;
-  }
-  ~DeviceGuard() {
-    int cur = -1;
-    if (old >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != old) cudaSetDevice(old);
-  }
-};
 
 // x_ref(theta_o): the array end that makes the shear a non-negative advance.
 double shear_reference(const std::vector<double> &u, double th) {
@@ -461,6 +457,8 @@ kk_status check_plan(const kk_plan *p, bool want_das) {
 
 bool aligned(const void *ptr, size_t a) { return ((uintptr_t)ptr % a) == 0; }
 
+}  // namespace
+
 kk_status enqueue_decompose(const kk_plan *p, const void *rf, void *rf_theta, void *ws, cudaStream_t s) {
   void *X = at<unsigned char>(ws, p->ws_X);
   float2 *Y = at<float2>(ws, p->ws_Y);
@@ -473,6 +471,8 @@ kk_status enqueue_decompose(const kk_plan *p, const void *rf, void *rf_theta, vo
   if (e != cudaSuccess) return cuda_fail(e, "inverse launch");
   return KK_OK;
 }
+
+namespace {
 
 kk_status enqueue_beamform(const kk_plan *p, const void *rf_theta, void *B, float *I, void *ws, cudaStream_t s) {
   float2 *part = (p->bf_split > 1) ? at<float2>(ws, p->ws_part) : nullptr;
