@@ -40,6 +40,8 @@ def _args():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--quick", action="store_true", help="skip the side measurements")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-form measurement")
+    ap.add_argument("--batch-frames", type=int, default=256)
     ap.add_argument("--profile", default=None,
                     choices=["kk_image", "decompose", "decompose_bf16", "decompose_f8e4m3", "das", "vernier"],
                     help="run three launches of one stage of the benchmark frame and exit "
@@ -176,6 +178,77 @@ def _vernier_pairs(w, kb):
     rx = kb.kk_scheme_angles(kb.KK_SCHEME_VERNIER, 8, dth, 16)
     pairs = np.array([(i, o) for i in sub for o in range(16)], dtype=np.int32)
     return rx, pairs
+
+
+def _batch_frames(kb, n_frames, seed0=4000, speckle_per_mm2=10.0):
+    """Frames of uneven size for the batched form: elements in {64, 128, 192,
+    256} (0.3 mm pitch), records of 1024-4096 samples, 8-75 transmits over
+    +-16 deg, pair sets of 32-512 pairs (vernier, shifted, confocal or hybrid
+    groups of three), square grids of 256^2-1024^2 pixels at 0.075 mm from 5 mm
+    depth; wires, cysts and speckle per frame, simulated on the GPU, 30 dB
+    noise, int16."""
+    import numpy as np
+    import torch
+    import kksynth
+    frames = []
+    for f in range(n_frames):
+        rng = np.random.default_rng(seed0 + f)
+        L = int(rng.choice([64, 128, 192, 256]))
+        T = int(rng.choice([1024, 1536, 2048, 3072, 4096]))
+        N = int(rng.integers(8, 76))
+        n = int(rng.choice([256, 384, 512, 640, 768, 1024]))
+        d = 0.075e-3
+        grid = (n, n, -d * (n - 1) / 2, d, 5e-3, d)
+        elem_x = kksynth.element_positions(L, 0.3e-3)
+        tx = kksynth.tx_angles_even(N, 16.0)
+        kind = rng.choice(["vernier", "shifted", "confocal", "hybrid"])
+        J = 3 if kind == "hybrid" else 1
+        while True:
+            a = int(rng.integers(4, min(N, 24) + 1))
+            m = int(rng.integers(3, 33))
+            if 32 <= a * m * J <= 512:
+                break
+        s = max(1, (N - 1) // max(a - 1, 1))
+        s -= s % 2 if s > 1 else 0
+        start = ((N - 1) - (a - 1) * s) // 2
+        sub = start + s * np.arange(a)
+        dth = float(tx[sub[-1]] - tx[sub[0]]) / max(a - 1, 1)
+        if kind == "hybrid":
+            groups = [kb.kk_scheme_angles(kb.KK_SCHEME_SHIFTED, a, dth, m, j) for j in (0, a // 4, a // 2)]
+        elif kind == "shifted":
+            groups = [kb.kk_scheme_angles(kb.KK_SCHEME_SHIFTED, a, dth, m, a // 2)]
+        elif kind == "confocal":
+            groups = [kb.kk_scheme_angles(kb.KK_SCHEME_CONFOCAL, a, dth, m)]
+        else:
+            groups = [kb.kk_scheme_angles(kb.KK_SCHEME_VERNIER, a, dth, m)]
+        rx = np.concatenate(groups)
+        pairs = np.array([(int(i), g * m + o) for g in range(J) for i in sub for o in range(m)], np.int32)
+        grp = np.repeat(np.arange(J, dtype=np.int32), a * m)
+        # phantom: speckle over the grid, wires every 6 mm, two cysts
+        xmax, zmax = -grid[2], 5e-3 + d * (n - 1)
+        ns = int(speckle_per_mm2 * (2 * xmax * 1e3) * ((zmax - 5e-3) * 1e3))
+        sx = rng.uniform(-xmax, xmax, ns)
+        sz = rng.uniform(5e-3, zmax, ns)
+        keep = np.ones(ns, bool)
+        for cx, cz in ((-0.25 * xmax, 5e-3 + 0.4 * (zmax - 5e-3)), (0.3 * xmax, 5e-3 + 0.7 * (zmax - 5e-3))):
+            keep &= (sx - cx) ** 2 + (sz - cz) ** 2 > (2e-3) ** 2
+        wx, wz = np.meshgrid(np.arange(-xmax + 2e-3, xmax, 6e-3), np.arange(8e-3, zmax, 6e-3))
+        x = np.concatenate([sx[keep], wx.ravel()])
+        z = np.concatenate([sz[keep], wz.ravel()])
+        amp = np.concatenate([rng.standard_normal(keep.sum()), np.full(wx.size, 10.0)])
+        sc = torch.tensor(np.stack([x, z, amp, np.zeros_like(x)], 1), dtype=torch.float32).cuda()
+        rf = kb.kk_simulate_rf(tx, elem_x, T, sc, kksynth.FS, kksynth.C_SOUND)
+        rms = float(rf.pow(2).mean().sqrt())
+        gen = torch.Generator(device="cuda").manual_seed(seed0 + f)
+        rf = rf + torch.randn(rf.shape, device="cuda", generator=gen) * rms * 10 ** (-30 / 20)
+        rf = torch.round(rf * (32767.0 / rf.abs().max())).clamp_(-32767, 32767).to(torch.int16)
+        comp = kb.KK_COMPOUND_INCOHERENT if J > 1 else kb.KK_COMPOUND_COHERENT
+        plan = kb.Plan(elem_x, tx, grid, kksynth.C_SOUND, kksynth.FS, T, kb.KK_RF_I16, rx_angles=rx,
+                       pairs=pairs, group_of_pair=grp, n_groups=J, compound=comp)
+        frames.append({"plan": plan, "rf": rf.contiguous(), "rf_theta": plan.empty_rf_theta(),
+                       "B": plan.empty_image(), "I": plan.empty_intensity(),
+                       "workspace": plan.empty_workspace()})
+    return frames
 
 
 def _time_loop(fn, reps, flush=None):
@@ -356,6 +429,25 @@ def run_ours(args):
         ms_d = _time_loop(lambda: dplan.das(d_rf, dB, dI, dws), 5, flush)
         side["das_75x128"] = {"frames_per_s": round(1e3 / ms_d, 1),
                               "gpixel_pairs_per_s": round(75 * 128 * npix / (ms_d / 1e3) / 1e9, 2)}
+        # batched form: 256 frames of uneven size, one CUDA graph
+        if not args.no_batch:
+            frames_b = _batch_frames(kb, args.batch_frames)
+            batch = kb.Batch(frames_b, shape=0)
+            for _ in range(2):
+                batch.run()
+            torch.cuda.synchronize()
+            ms_b = _time_loop(lambda: batch.run(), 5, flush)
+            bi = batch.info
+            side["batched_uneven"] = {
+                "frames": bi.n_frames, "frames_per_s": round(bi.n_frames / (ms_b / 1e3), 1),
+                "ms_per_batch": round(ms_b, 3),
+                "gpixel_pairs_per_s": round(bi.pixel_pairs / (ms_b / 1e3) / 1e9, 1),
+                "launch_shape": {"rows": bi.rows, "stage": bi.stage},
+                "autotuned_ms": {str(bi.tuned_shape[i]): round(bi.tuned_ms[i], 3) for i in range(bi.n_tuned)},
+                "graph_nodes": bi.graph_nodes, "work_items": bi.n_items,
+                "status": frames_b[0]["plan"].status()}
+            del batch, frames_b
+            torch.cuda.empty_cache()
         out["breakdown"] = side
 
         # end to end through the C ABI from pinned host memory

@@ -19,7 +19,7 @@
 
 namespace {
 
-constexpr int kCaptureStreams = 8;
+constexpr int kCaptureStreams = 32;
 constexpr size_t kAlign = 256;
 
 size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
