@@ -34,7 +34,12 @@ EXPORTS = ["kk_plan_create", "das_plan_create", "kk_plan_destroy", "kk_plan_get_
            "kk_beamform", "kk_beamform_noalloc", "das_beamform", "kk_run_host_scratch_size", "kk_run_host",
            "kk_scheme_angles", "kk_last_error", "kk_version",
            "kk_batch_create", "kk_batch_run", "kk_batch_get_info", "kk_batch_destroy",
-           "kk_simulate_rf"]
+           "kk_simulate_rf",
+           # include/kknet.h
+           "kk_net_create", "kk_net_destroy", "kk_net_info", "kk_net_get_params", "kk_net_set_params",
+           "kk_net_forward", "kk_net_loss_grad", "kk_net_adam", "kk_net_save", "kk_net_load",
+           "kk_net_judge_filter", "kk_net_judge", "kk_net_image_scale",
+           "kk_nn_conv3x3", "kk_nn_conv3x3_dgrad", "kk_nn_conv3x3_wgrad_workspace", "kk_nn_conv3x3_wgrad"]
 
 
 class KKError(RuntimeError):
@@ -89,6 +94,11 @@ class kk_batch_info(ctypes.Structure):
                 ("tuned_ms", ctypes.c_float * 16)]
 
 
+class kk_net_desc(ctypes.Structure):
+    _fields_ = [("max_batch", ctypes.c_int32), ("height", ctypes.c_int32), ("width", ctypes.c_int32),
+                ("base_channels", ctypes.c_int32), ("seed", ctypes.c_uint64)]
+
+
 _lib = None
 
 
@@ -138,6 +148,28 @@ def load(build_if_missing: bool = False):
                             ctypes.c_double, ctypes.c_uint64, vp, vp], st),
         "kk_last_error": ([], ctypes.c_char_p),
         "kk_version": ([], ctypes.c_char_p),
+        "kk_net_create": ([pp, ctypes.POINTER(kk_net_desc)], st),
+        "kk_net_destroy": ([vp], None),
+        "kk_net_info": ([vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)], st),
+        "kk_net_get_params": ([vp, vp, vp], st),
+        "kk_net_set_params": ([vp, vp, vp], st),
+        "kk_net_forward": ([vp, ctypes.c_int32, vp, vp, vp, vp], st),
+        "kk_net_loss_grad": ([vp, ctypes.c_int32, vp, vp, vp, vp, vp, vp, vp, vp], st),
+        "kk_net_adam": ([vp, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                         ctypes.c_float, vp], st),
+        "kk_net_save": ([vp, ctypes.c_char_p, vp], st),
+        "kk_net_load": ([vp, ctypes.c_char_p, vp], st),
+        "kk_net_judge_filter": ([vp, vp, vp, ctypes.c_float, vp], st),
+        "kk_net_judge": ([vp, ctypes.c_int32, vp, vp, vp, vp], st),
+        "kk_net_image_scale": ([vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, vp, vp], st),
+        "kk_nn_conv3x3": ([vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, vp,
+                           ctypes.c_int32, vp, ctypes.c_int32, vp, vp, vp], st),
+        "kk_nn_conv3x3_dgrad": ([vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, vp,
+                                 ctypes.c_int32, vp, vp, vp], st),
+        "kk_nn_conv3x3_wgrad_workspace": ([ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                           ctypes.c_int32, ctypes.POINTER(ctypes.c_size_t)], st),
+        "kk_nn_conv3x3_wgrad": ([vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, vp,
+                                 ctypes.c_int32, vp, vp, vp, vp], st),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -437,3 +469,128 @@ def kk_simulate_rf(tx_angles, elem_x, n_samples, scatterers, fs, c, f0=5e6, bw=0
                                  float(noise_sigma), int(seed) & (2**64 - 1), _ptr(out),
                                  _stream(stream)))
     return out
+
+
+# --------------------------------------------------------------------------
+# learned refiner (include/kknet.h)
+# --------------------------------------------------------------------------
+def kk_nn_conv3x3(x, w, bias=None, relu=False, y=None, yf=None, stream=None):
+    """x [n][h][w][cin] bf16, w [cout][3][3][cin] bf16 (CUDA, contiguous)."""
+    n, h, wd, cin = x.shape
+    cout = w.shape[0]
+    _check(load().kk_nn_conv3x3(_ptr(x), n, h, wd, cin, _ptr(w), cout, _ptr(bias), int(bool(relu)), _ptr(y),
+                                _ptr(yf), _stream(stream)))
+
+
+def kk_nn_conv3x3_dgrad(dy, w, dx, stream=None):
+    """dx [n][h][w][cin] = adjoint in x of conv3x3 applied to dy [n][h][w][cout]."""
+    import torch
+    n, h, wd, cout = dy.shape
+    cin = w.shape[3]
+    ws = torch.empty(cout * 9 * cin, dtype=torch.bfloat16, device=dy.device)
+    _check(load().kk_nn_conv3x3_dgrad(_ptr(dy), n, h, wd, cout, _ptr(w), cin, _ptr(dx), _ptr(ws),
+                                      _stream(stream)))
+
+
+def kk_nn_conv3x3_wgrad(x, dy, dw, db=None, stream=None):
+    import torch
+    n, h, wd, cin = x.shape
+    cout = dy.shape[3]
+    nb = ctypes.c_size_t()
+    _check(load().kk_nn_conv3x3_wgrad_workspace(n, h, wd, cin, cout, ctypes.byref(nb)))
+    ws = torch.empty(max(nb.value // 4, 1), dtype=torch.float32, device=x.device)
+    _check(load().kk_nn_conv3x3_wgrad(_ptr(x), n, h, wd, cin, _ptr(dy), cout, _ptr(dw), _ptr(db), _ptr(ws),
+                                      _stream(stream)))
+
+
+def kk_net_image_scale(img, out=None, stream=None):
+    """img [nb][h][w][2] float32 (complex) -> [nb] float32 of 1 / rms."""
+    import torch
+    nb, h, w = img.shape[0], img.shape[1], img.shape[2]
+    if out is None:
+        out = torch.empty(nb, dtype=torch.float32, device=img.device)
+    _check(load().kk_net_image_scale(_ptr(img), nb, h, w, _ptr(out), _stream(stream)))
+    return out
+
+
+class Net:
+    """Owner of a kk_net handle (the refiner network) with the ABI's calls as
+    methods.  Images are CUDA float32 tensors [nb][H][W][2] (complex)."""
+
+    def __init__(self, max_batch: int, height: int, width: int, base_channels: int = 32, seed: int = 0):
+        d = kk_net_desc(int(max_batch), int(height), int(width), int(base_channels), int(seed) & (2**64 - 1))
+        h = ctypes.c_void_p()
+        _check(load().kk_net_create(ctypes.byref(h), ctypes.byref(d)))
+        self.handle = h
+        self.max_batch, self.height, self.width, self.base_channels = max_batch, height, width, base_channels
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h:
+            try:
+                load().kk_net_destroy(h)
+            except Exception:
+                pass
+            self.handle = None
+
+    def info(self):
+        n, st = ctypes.c_int64(), ctypes.c_int64()
+        _check(load().kk_net_info(self.handle, ctypes.byref(n), ctypes.byref(st)))
+        return n.value, st.value
+
+    @property
+    def n_params(self) -> int:
+        return self.info()[0]
+
+    @property
+    def step(self) -> int:
+        return self.info()[1]
+
+    def get_params(self, out=None, stream=None):
+        import torch
+        if out is None:
+            out = torch.empty(self.n_params, dtype=torch.float32, device="cuda")
+        _check(load().kk_net_get_params(self.handle, _ptr(out), _stream(stream)))
+        return out
+
+    def set_params(self, params, stream=None):
+        _check(load().kk_net_set_params(self.handle, _ptr(params), _stream(stream)))
+
+    def forward(self, x, in_scale=None, out=None, stream=None):
+        import torch
+        if out is None:
+            out = torch.empty_like(x)
+        _check(load().kk_net_forward(self.handle, x.shape[0], _ptr(x), _ptr(in_scale), _ptr(out),
+                                     _stream(stream)))
+        return out
+
+    def loss_grad(self, x, target, in_scale=None, target_scale=None, loss=None, grad=None, out=None,
+                  stream=None):
+        import torch
+        if loss is None:
+            loss = torch.empty(1, dtype=torch.float32, device=x.device)
+        _check(load().kk_net_loss_grad(self.handle, x.shape[0], _ptr(x), _ptr(in_scale), _ptr(target),
+                                       _ptr(target_scale), _ptr(loss), _ptr(grad), _ptr(out),
+                                       _stream(stream)))
+        return loss
+
+    def adam(self, lr, beta1=0.9, beta2=0.999, eps=1e-8, weight_decay=0.0, stream=None):
+        _check(load().kk_net_adam(self.handle, float(lr), float(beta1), float(beta2), float(eps),
+                                  float(weight_decay), _stream(stream)))
+
+    def save(self, path, stream=None):
+        _check(load().kk_net_save(self.handle, os.fsencode(path), _stream(stream)))
+
+    def load(self, path, stream=None):
+        _check(load().kk_net_load(self.handle, os.fsencode(path), _stream(stream)))
+
+    def judge_filter(self, psf_c, psf_f, rho=0.1, stream=None):
+        _check(load().kk_net_judge_filter(self.handle, _ptr(psf_c), _ptr(psf_f), float(rho), _stream(stream)))
+
+    def judge(self, out, xc, stat=None, stream=None):
+        """[nb][2] float32: (consistency residual, out-of-band fraction)."""
+        import torch
+        if stat is None:
+            stat = torch.empty((out.shape[0], 2), dtype=torch.float32, device=out.device)
+        _check(load().kk_net_judge(self.handle, out.shape[0], _ptr(out), _ptr(xc), _ptr(stat), _stream(stream)))
+        return stat

@@ -36,7 +36,7 @@ def sources():
 
 def _deps_mtime():
     files = sources() + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".h")]
-    files.append(os.path.join(INCLUDE, "kkbeam.h"))
+    files += [os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE) if f.endswith(".h")]
     return max(os.path.getmtime(f) for f in files)
 
 

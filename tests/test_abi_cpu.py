@@ -12,7 +12,8 @@ import paper_2603_22496_gb300 as kb
 from paper_2603_22496_gb300 import build as kbuild
 from oracle import schemes
 
-HEADER = os.path.join(os.path.dirname(os.path.dirname(__file__)), "include", "kkbeam.h")
+INCLUDE = os.path.join(os.path.dirname(os.path.dirname(__file__)), "include")
+HEADERS = sorted(os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE) if f.endswith(".h"))
 
 
 @pytest.fixture(scope="module")
@@ -22,7 +23,7 @@ def lib():
 
 
 def _declared():
-    txt = open(HEADER).read()
+    txt = "".join(open(h).read() for h in HEADERS)
     txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
     return sorted(set(re.findall(r"\b(kk_\w+|das_\w+)\s*\(", txt)))
 
