@@ -42,8 +42,10 @@ def _args():
     ap.add_argument("--quick", action="store_true", help="skip the side measurements")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-form measurement")
     ap.add_argument("--batch-frames", type=int, default=256)
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned-refiner measurement")
     ap.add_argument("--profile", default=None,
-                    choices=["kk_image", "decompose", "decompose_bf16", "decompose_f8e4m3", "das", "vernier"],
+                    choices=["kk_image", "decompose", "decompose_bf16", "decompose_f8e4m3", "das", "vernier",
+                             "refiner_step"],
                     help="run three launches of one stage of the benchmark frame and exit "
                          "(a small, bounded target for ncu)")
     return ap.parse_args()
@@ -268,6 +270,82 @@ def _time_loop(fn, reps, flush=None):
     return sum(a.elapsed_time(b) for a, b in evs) / reps
 
 
+# (cin, cout, level) of the refiner's convolutions at base width 32
+REFINER_LAYERS = [(16, 32, 0), (32, 32, 0), (32, 64, 1), (64, 64, 1), (64, 128, 2), (128, 128, 2),
+                  (128, 256, 3), (256, 256, 4), (256, 128, 3), (128, 64, 2), (64, 32, 1), (32, 32, 0),
+                  (32, 16, 0)]
+
+
+def refiner_conv_flops(batch, H=256, W=256):
+    """(forward, training-step) convolution FLOPs: 2 x 9 cin cout per output
+    pixel; a training step adds the backward-data (all layers but the first)
+    and weight-gradient passes of the same size."""
+    fwd = sum(2.0 * 9 * ci * co * (H >> l) * (W >> l) for ci, co, l in REFINER_LAYERS) * batch
+    first = 2.0 * 9 * 16 * 32 * H * W * batch
+    return fwd, 3 * fwd - first
+
+
+def _learned(kb, dev, peaks, peak_src, flush, train_frames=512, eval_frames=32, steps=400, batch=16):
+    """Learned refiner on 256 x 256 images (6 x 12 vernier KK image in, full
+    75 x 128 KK image as target): throughput of inference (network + judge)
+    and of a training step, the convolutions' TFLOP/s against the BF16 peak,
+    and the held-out gain of a short training run from seeded phantoms
+    simulated and beamformed on the GPU."""
+    import numpy as np
+    import torch
+    from paper_2603_22496_gb300 import learned as L
+    syn = L.Synth()
+    t0 = time.perf_counter()
+    X, Y = syn.dataset(range(100_000, 100_000 + train_frames))
+    Xe, Ye = syn.dataset(range(900_000, 900_000 + eval_frames))
+    torch.cuda.synchronize()
+    data_s = time.perf_counter() - t0
+    ref = L.Refiner(syn, max_batch=batch, seed=0)
+    t1 = time.perf_counter()
+    losses = ref.train(X, Y, steps, batch, 3e-4, seed=0)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t1
+    ref.calibrate(X[:256])
+    e_in, e_net, st = ref.evaluate(Xe, Ye)
+    acc = ref.accept(torch.from_numpy(st).to(dev)).float().mean().item()
+    # kernel-level timings on one batch (CUDA events, L2 flushed between reps)
+    xb, yb = X[:batch].contiguous(), Y[:batch].contiguous()
+    sx, sy = kb.kk_net_image_scale(xb), kb.kk_net_image_scale(yb)
+    ob = torch.empty_like(xb)
+    stat = torch.empty((batch, 2), device=dev)
+    for _ in range(3):
+        ref.net.forward(xb, sx, out=ob)
+    ms_fwd = _time_loop(lambda: ref.net.forward(xb, sx, out=ob), 10, flush)
+    ms_inf = _time_loop(lambda: (ref.net.forward(xb, sx, out=ob), ref.net.judge(ob, xb, stat=stat)), 10, flush)
+    ms_step = _time_loop(lambda: (ref.net.loss_grad(xb, yb, sx, sy), ref.net.adam(1e-6)), 10, flush)
+    fwd_flops, step_flops = refiner_conv_flops(batch)
+    peak = float(peaks["bf16_tflops"])
+    tf_fwd = fwd_flops / (ms_fwd / 1e3) / 1e12
+    tf_step = step_flops / (ms_step / 1e3) / 1e12
+    return {
+        "workload": "256 x 256 IQ, 6 x 12 vernier -> 75 x 128 full pair set; 1.58 M parameters",
+        "batch": batch, "status": ref.net.status(),
+        "inference_images_per_s": round(batch / (ms_inf / 1e3), 1),
+        "forward_ms": round(ms_fwd, 4), "inference_ms": round(ms_inf, 4),
+        "train_step_ms": round(ms_step, 4), "train_images_per_s": round(batch / (ms_step / 1e3), 1),
+        "conv_roofline": {"bound": "tensor", "unit": "TFLOP/s",
+                          "forward_achieved": round(tf_fwd, 1), "train_step_achieved": round(tf_step, 1),
+                          "peak": peak, "frac_forward": round(tf_fwd / peak, 4),
+                          "frac_train_step": round(tf_step / peak, 4),
+                          "basis": f"convolution FLOPs (2 x 9 cin cout per pixel) over the whole pass; "
+                                   f"bf16_tflops burst ({peak_src})"},
+        "short_training": {"train_frames": train_frames, "steps": steps, "batch": batch,
+                           "loss_first": round(float(losses[:20].mean()), 5),
+                           "loss_last": round(float(losses[-20:].mean()), 5),
+                           "data_s": round(data_s, 2), "train_s": round(train_s, 2)},
+        "held_out": {"frames": eval_frames, "err_compressed": round(float(e_in.mean()), 4),
+                     "err_refined": round(float(e_net.mean()), 4),
+                     "gain": round(float(e_in.mean() / e_net.mean()), 4),
+                     "refined_better_frac": round(float((e_net < e_in).mean()), 3),
+                     "judge_accepted_frac": round(acc, 3),
+                     "metric": "LS-scaled relative L2 against the plain full-pair KK image"}}
+
+
 FORMS = (("bf16", "KK_PREC_BF16"), ("f32", "KK_PREC_F32"), ("f16", "KK_PREC_F16"),
          ("f8e4m3", "KK_PREC_F8E4M3"))
 CHOSEN = "bf16"
@@ -448,6 +526,9 @@ def run_ours(args):
                 "status": frames_b[0]["plan"].status()}
             del batch, frames_b
             torch.cuda.empty_cache()
+        if not args.no_learned:
+            side["learned_refiner"] = _learned(kb, dev, peaks, peak_src, flush)
+            torch.cuda.empty_cache()
         out["breakdown"] = side
 
         # end to end through the C ABI from pinned host memory
@@ -520,6 +601,19 @@ def run_profile(args):
     kbuild.build()
     import paper_2603_22496_gb300 as kb
     kb.load()
+    if args.profile == "refiner_step":
+        # three training steps of the refiner at batch 16 on 256 x 256 (random images; ~2 GB)
+        net = kb.Net(16, 256, 256, 32, seed=0)
+        g = torch.Generator(device="cuda").manual_seed(0)
+        x = torch.randn((16, 256, 256, 2), device="cuda", generator=g)
+        y = torch.randn((16, 256, 256, 2), device="cuda", generator=g)
+        sx, sy = kb.kk_net_image_scale(x), kb.kk_net_image_scale(y)
+        for _ in range(3):
+            net.loss_grad(x, y, sx, sy)
+            net.adam(1e-5)
+        torch.cuda.synchronize()
+        print(f"profile target {args.profile}: done (status {net.status()})")
+        return
     w = _workload(0)
     d_rf = torch.from_numpy(w.rf).cuda()
     if args.profile == "das":

@@ -63,6 +63,10 @@ kk_status kk_net_create(kk_net **out, const kk_net_desc *d);
 void kk_net_destroy(kk_net *net);
 /* number of parameters (floats of the flat vector) and Adam steps taken */
 kk_status kk_net_info(const kk_net *net, int64_t *n_params, int64_t *step);
+/* Device status word of the net's tensor-core kernels, read and reset
+ * (synchronous): KK_OK, or KK_ERR_TIMEOUT when a CTA gave up on a bounded
+ * wait (its outputs are then invalid). */
+kk_status kk_net_status(kk_net *net, int32_t *status);
 /* copy the FP32 master parameters out / in (device buffers of n_params
  * floats); set also refreshes the BF16 copies.  Enqueued on `stream`. */
 kk_status kk_net_get_params(const kk_net *net, float *d_dst, void *stream);
@@ -143,10 +147,13 @@ kk_status kk_net_image_scale(const void *d_img, int32_t nb, int32_t h, int32_t w
  * x: [n][h][w][cin] bf16 NHWC, w: [cout][3][3][cin] bf16, bias [cout] fp32
  * (nullable); cin, cout multiples of 16.
  *   kk_nn_conv3x3:       y = act(conv(x, w) + bias) into d_y (bf16, nullable)
- *                        and / or d_yf (fp32, nullable), [n][h][w][cout]
+ *                        and / or d_yf (fp32, nullable), [n][h][w][cout];
+ *                        tensor cores (tcgen05), FP32 accumulation
  *   kk_nn_conv3x3_dgrad: dx = conv(dy, flip(w)^T) (adjoint in x), bf16
  *                        [n][h][w][cin]; needs a workspace of
  *                        cout*9*cin*2 bytes
+ *   kk_nn_status:        status word of the layer calls' tensor-core
+ *                        kernels, read and reset (synchronous)
  *   kk_nn_conv3x3_wgrad: dw [cout][3][3][cin] and db [cout] (fp32,
  *                        overwritten) from x and dy [n][h][w][cout] bf16;
  *                        workspace size from kk_nn_conv3x3_wgrad_workspace
@@ -156,6 +163,7 @@ kk_status kk_nn_conv3x3(const void *d_x, int32_t n, int32_t h, int32_t w, int32_
                         void *stream);
 kk_status kk_nn_conv3x3_dgrad(const void *d_dy, int32_t n, int32_t h, int32_t w, int32_t cout,
                               const void *d_w, int32_t cin, void *d_dx, void *d_workspace, void *stream);
+kk_status kk_nn_status(int32_t *status);
 kk_status kk_nn_conv3x3_wgrad_workspace(int32_t n, int32_t h, int32_t w, int32_t cin, int32_t cout,
                                         size_t *bytes);
 kk_status kk_nn_conv3x3_wgrad(const void *d_x, int32_t n, int32_t h, int32_t w, int32_t cin,

@@ -36,7 +36,7 @@ EXPORTS = ["kk_plan_create", "das_plan_create", "kk_plan_destroy", "kk_plan_get_
            "kk_batch_create", "kk_batch_run", "kk_batch_get_info", "kk_batch_destroy",
            "kk_simulate_rf",
            # include/kknet.h
-           "kk_net_create", "kk_net_destroy", "kk_net_info", "kk_net_get_params", "kk_net_set_params",
+           "kk_net_create", "kk_net_destroy", "kk_net_info", "kk_net_status", "kk_nn_status", "kk_net_get_params", "kk_net_set_params",
            "kk_net_forward", "kk_net_loss_grad", "kk_net_adam", "kk_net_save", "kk_net_load",
            "kk_net_judge_filter", "kk_net_judge", "kk_net_image_scale",
            "kk_nn_conv3x3", "kk_nn_conv3x3_dgrad", "kk_nn_conv3x3_wgrad_workspace", "kk_nn_conv3x3_wgrad"]
@@ -152,6 +152,8 @@ def load(build_if_missing: bool = False):
         "kk_net_destroy": ([vp], None),
         "kk_net_info": ([vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)], st),
         "kk_net_get_params": ([vp, vp, vp], st),
+        "kk_net_status": ([vp, ctypes.POINTER(ctypes.c_int32)], st),
+        "kk_nn_status": ([ctypes.POINTER(ctypes.c_int32)], st),
         "kk_net_set_params": ([vp, vp, vp], st),
         "kk_net_forward": ([vp, ctypes.c_int32, vp, vp, vp, vp], st),
         "kk_net_loss_grad": ([vp, ctypes.c_int32, vp, vp, vp, vp, vp, vp, vp, vp], st),
@@ -482,6 +484,13 @@ def kk_nn_conv3x3(x, w, bias=None, relu=False, y=None, yf=None, stream=None):
                                 _ptr(yf), _stream(stream)))
 
 
+def kk_nn_status() -> int:
+    """Status word of the layer calls' tensor-core kernels (read and reset)."""
+    v = ctypes.c_int32()
+    _check(load().kk_nn_status(ctypes.byref(v)))
+    return v.value
+
+
 def kk_nn_conv3x3_dgrad(dy, w, dx, stream=None):
     """dx [n][h][w][cin] = adjoint in x of conv3x3 applied to dy [n][h][w][cout]."""
     import torch
@@ -537,6 +546,12 @@ class Net:
         n, st = ctypes.c_int64(), ctypes.c_int64()
         _check(load().kk_net_info(self.handle, ctypes.byref(n), ctypes.byref(st)))
         return n.value, st.value
+
+    def status(self) -> int:
+        """Status word of the net's tensor-core kernels (read and reset)."""
+        v = ctypes.c_int32()
+        _check(load().kk_net_status(self.handle, ctypes.byref(v)))
+        return v.value
 
     @property
     def n_params(self) -> int:

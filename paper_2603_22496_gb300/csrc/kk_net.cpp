@@ -74,6 +74,7 @@ struct kk_net {
   __nv_bfloat16 *wt = nullptr;  // flipped / transposed BF16 weights (backward-data)
   float *part = nullptr;        // weight-gradient split partials
   float *loss_part = nullptr;
+  int *status = nullptr;        // device status word of the tensor-core kernels
   // activations (for max_batch images)
   __nv_bfloat16 *x = nullptr;
   __nv_bfloat16 *a[12] = {};
@@ -173,6 +174,7 @@ void carve(kk_net &n, Arena &A) {
   n.wt = A.take<__nv_bfloat16>(np);
   n.part = A.take<float>(max_part_floats(n));
   n.loss_part = A.take<float>((size_t)kk::nn::residual_blocks(B, n.H * n.W));
+  n.status = A.take<int>(1);
   n.x = A.take<__nv_bfloat16>(px(0) * kInChannels);
   for (int i = 0; i < 12; ++i) n.a[i] = A.take<__nv_bfloat16>(px(n.layer[i].level) * n.layer[i].cout);
   const int pc[4] = {C, 2 * C, 4 * C, 8 * C};  // pooled p_l lives at level l + 1
@@ -196,24 +198,25 @@ kk_status check_net(const kk_net *n, int nb) {
 
 kk_status conv(const kk_net &n, int i, const Tensor4 &x, __nv_bfloat16 *y, float *yf, cudaStream_t s) {
   const Layer &L = n.layer[i];
-  KK_TRY(kk::nn::conv3x3(x, n.wb + L.w_off, L.cout, n.w + L.b_off, L.relu, y, yf, s), "conv launch");
+  KK_TRY(kk::nn::conv3x3_tc(x, n.wb + L.w_off, L.cout, n.w + L.b_off, L.relu, y, yf, n.status, s), "conv launch");
   return KK_OK;
 }
 
 // weight and bias gradient of layer i into n.g (W then b, contiguous)
 kk_status wgrad(const kk_net &n, int i, const Tensor4 &x, const __nv_bfloat16 *dy, cudaStream_t s) {
   const Layer &L = n.layer[i];
-  int splits = 0;
-  KK_TRY(kk::nn::conv3x3_wgrad(x, dy, L.cout, n.part, &splits, s), "wgrad launch");
-  const size_t stride = (size_t)L.cout * 9 * L.cin + L.cout;
-  KK_TRY(kk::nn::reduce_splits(n.part, splits, stride, stride, n.g + L.w_off, s), "wgrad reduce");
+  int splits = 0, nb = 0;
+  KK_TRY(kk::nn::conv3x3_wgrad(x, dy, L.cout, n.part, &splits, &nb, n.status, s), "wgrad launch");
+  const size_t nw = (size_t)L.cout * 9 * L.cin;
+  KK_TRY(kk::nn::reduce_splits(n.part, splits, nw, nw, n.g + L.w_off, s), "wgrad reduce");
+  KK_TRY(kk::nn::reduce_splits(n.part + (size_t)splits * nw, nb, L.cout, L.cout, n.g + L.b_off, s), "bias reduce");
   return KK_OK;
 }
 
 // gradient w.r.t. layer i's input: conv of dy with the flipped weights
 kk_status dgrad(const kk_net &n, int i, const Tensor4 &dy, __nv_bfloat16 *dx, cudaStream_t s) {
   const Layer &L = n.layer[i];
-  KK_TRY(kk::nn::conv3x3(dy, n.wt + L.w_off, L.cin, nullptr, false, dx, nullptr, s), "dgrad launch");
+  KK_TRY(kk::nn::conv3x3_tc(dy, n.wt + L.w_off, L.cin, nullptr, false, dx, nullptr, n.status, s), "dgrad launch");
   return KK_OK;
 }
 
@@ -348,6 +351,7 @@ kk_status kk_net_create(kk_net **out, const kk_net_desc *d) {
   e = cudaMemcpy(n->w, h.data(), h.size() * sizeof(float), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(n->m, 0, n->n_params * sizeof(float));
   if (e == cudaSuccess) e = cudaMemset(n->v, 0, n->n_params * sizeof(float));
+  if (e == cudaSuccess) e = cudaMemset(n->status, 0, sizeof(int));
   if (e == cudaSuccess) e = kk::nn::to_bf16(n->w, n->wb, n->n_params, 0);
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e != cudaSuccess) {
@@ -372,6 +376,16 @@ kk_status kk_net_info(const kk_net *n, int64_t *n_params, int64_t *step) {
   if (!n) { set_error("null net"); return KK_ERR_INVALID_ARG; }
   if (n_params) *n_params = (int64_t)n->n_params;
   if (step) *step = n->step;
+  return KK_OK;
+}
+
+kk_status kk_net_status(kk_net *n, int32_t *status) {
+  if (!n || !status) { set_error("null argument"); return KK_ERR_INVALID_ARG; }
+  kk::DeviceGuard g(n->device);
+  int v = 0, zero = 0;
+  KK_TRY(cudaMemcpy(&v, n->status, sizeof(int), cudaMemcpyDeviceToHost), "read status");
+  KK_TRY(cudaMemcpy(n->status, &zero, sizeof(int), cudaMemcpyHostToDevice), "reset status");
+  *status = v;
   return KK_OK;
 }
 
@@ -588,8 +602,8 @@ kk_status kk_nn_conv3x3(const void *d_x, int32_t n, int32_t h, int32_t w, int32_
   if (st != KK_OK) return st;
   if (!d_y && !d_yf) { set_error("no output"); return KK_ERR_INVALID_ARG; }
   Tensor4 x{(__nv_bfloat16 *)d_x, n, h, w, cin};
-  KK_TRY(kk::nn::conv3x3(x, (const __nv_bfloat16 *)d_w, cout, d_bias, relu != 0, (__nv_bfloat16 *)d_y, d_yf,
-                         (cudaStream_t)stream), "conv");
+  KK_TRY(kk::nn::conv3x3_tc(x, (const __nv_bfloat16 *)d_w, cout, d_bias, relu != 0, (__nv_bfloat16 *)d_y, d_yf,
+                            nullptr, (cudaStream_t)stream), "conv");
   return KK_OK;
 }
 
@@ -601,8 +615,16 @@ kk_status kk_nn_conv3x3_dgrad(const void *d_dy, int32_t n, int32_t h, int32_t w,
   const cudaStream_t s = (cudaStream_t)stream;
   KK_TRY(kk::nn::flip_transpose((const __nv_bfloat16 *)d_w, cout, cin, (__nv_bfloat16 *)d_ws, s), "flip");
   Tensor4 dy{(__nv_bfloat16 *)d_dy, n, h, w, cout};
-  KK_TRY(kk::nn::conv3x3(dy, (const __nv_bfloat16 *)d_ws, cin, nullptr, false, (__nv_bfloat16 *)d_dx, nullptr, s),
-         "dgrad");
+  KK_TRY(kk::nn::conv3x3_tc(dy, (const __nv_bfloat16 *)d_ws, cin, nullptr, false, (__nv_bfloat16 *)d_dx, nullptr,
+                            nullptr, s), "dgrad");
+  return KK_OK;
+}
+
+kk_status kk_nn_status(int32_t *status) {
+  if (!status) { set_error("null argument"); return KK_ERR_INVALID_ARG; }
+  int v = 0;
+  KK_TRY(kk::nn::conv_status(&v), "layer status");
+  *status = v;
   return KK_OK;
 }
 
@@ -623,11 +645,13 @@ kk_status kk_nn_conv3x3_wgrad(const void *d_x, int32_t n, int32_t h, int32_t w, 
   if (!d_dw || !d_ws) { set_error("null output or workspace"); return KK_ERR_INVALID_ARG; }
   const cudaStream_t s = (cudaStream_t)stream;
   Tensor4 x{(__nv_bfloat16 *)d_x, n, h, w, cin};
-  int splits = 0;
-  KK_TRY(kk::nn::conv3x3_wgrad(x, (const __nv_bfloat16 *)d_dy, cout, (float *)d_ws, &splits, s), "wgrad");
-  const size_t nw = (size_t)cout * 9 * cin, stride = nw + cout;
-  KK_TRY(kk::nn::reduce_splits((const float *)d_ws, splits, stride, nw, d_dw, s), "wgrad reduce");
-  if (d_db) KK_TRY(kk::nn::reduce_splits((const float *)d_ws + nw, splits, stride, cout, d_db, s), "bias reduce");
+  int splits = 0, nb = 0;
+  KK_TRY(kk::nn::conv3x3_wgrad(x, (const __nv_bfloat16 *)d_dy, cout, (float *)d_ws, &splits, &nb, nullptr, s),
+         "wgrad");
+  const size_t nw = (size_t)cout * 9 * cin;
+  KK_TRY(kk::nn::reduce_splits((const float *)d_ws, splits, nw, nw, d_dw, s), "wgrad reduce");
+  if (d_db)
+    KK_TRY(kk::nn::reduce_splits((const float *)d_ws + (size_t)splits * nw, nb, cout, cout, d_db, s), "bias reduce");
   return KK_OK;
 }
 

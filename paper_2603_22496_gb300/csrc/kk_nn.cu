@@ -1,20 +1,12 @@
-// kk_nn.cu -- kernels of the learned refiner: BF16 3x3 convolutions (forward,
-// backward-data, backward-weight) as implicit GEMMs on the tensor cores with
-// FP32 accumulation, and the small elementwise / pooling / loss / optimiser
-// kernels around them.
+// kk_nn.cu -- the learned refiner's kernels around its convolutions (which
+// are in kk_conv_tc.cu): split-partial reduction, backward-data weight
+// flip, ReLU backward, pooling and upsampling with their adjoints, input
+// packing, residual output and loss, Adam, and the fallback judge (2-D DFT,
+// k-space filter, consistency statistic).
 //
-// Activations are NHWC bfloat16 with the channel count a multiple of 16;
-// weights are [Cout][3][3][Cin] bfloat16 (FP32 master copies live in the
-// optimiser).  The convolution GEMM for a layer is
-//     Y[p][co] = sum_{kh,kw,ci} X[p + (kh-1, kw-1)][ci] W[co][kh][kw][ci]
-// with M = pixels, N = Cout, K = 9 Cin, zero padding at the image border.
-// This file holds the warp-level form (mma.sync.m16n8k16, bf16 in, fp32
-// accumulate), which every layer shape supports; it also serves the weight
-// gradient, whose K dimension (pixels) is split over CTAs.
-//
-// Every reduction here runs in a fixed order (per-split partial buffers and
-// fixed trees, no floating-point atomics), so a training step is bitwise
-// reproducible.
+// Activations are NHWC bfloat16.  Every reduction here runs in a fixed
+// order (per-split partial buffers and fixed trees, no floating-point
+// atomics), so a training step is bitwise reproducible.
 #include <cuda_bf16.h>
 
 #include "kk_internal.h"
@@ -26,231 +18,30 @@ namespace kk {
 namespace nn {
 namespace {
 
-__device__ __forceinline__ void mma_bf16_16816(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-      "{%0,%1,%2,%3};\n"
-      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
-
 __device__ __forceinline__ uint32_t pack2(__nv_bfloat16 lo, __nv_bfloat16 hi) {
   return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
 }
 
-// ---------------------------------------------------------------------------
-// Forward convolution (also backward-data with flipped, transposed weights).
-// CTA tile: 64 pixels x 64 output channels, 4 warps as 2 x 2, each warp
-// 32 x 32 = 2 (m16) x 4 (n8) mma tiles; K chunks of 16 (one mma K).
-// ---------------------------------------------------------------------------
-constexpr int kTM = 64, kTN = 64, kTK = 16;
-
-__global__ void __launch_bounds__(128)
-    k_conv3x3(const __nv_bfloat16 *__restrict__ X, int Nb, int H, int W, int Cin,
-              const __nv_bfloat16 *__restrict__ Wt, int Cout, const float *__restrict__ bias,
-              int relu, __nv_bfloat16 *__restrict__ Y, float *__restrict__ Yf) {
-  __shared__ __align__(16) __nv_bfloat16 As[kTM][kTK + 8];  // pixels x k (padded rows)
-  __shared__ __align__(16) __nv_bfloat16 Bs[kTN][kTK + 8];  // cout x k
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int wm = warp >> 1, wn = warp & 1;
-  const int P = Nb * H * W;
-  const int m0 = blockIdx.x * kTM, n0 = blockIdx.y * kTN;
-  const int K = 9 * Cin;
-  float acc[2][4][4];
-#pragma unroll
-  for (int a = 0; a < 2; ++a)
-#pragma unroll
-    for (int b = 0; b < 4; ++b)
-#pragma unroll
-      for (int c = 0; c < 4; ++c) acc[a][b][c] = 0.f;
-
-  // loader mapping: 128 threads; A: 64 rows x 16 k = 64 x 2 chunks of 8 bf16
-  const int lr = tid >> 1, lc = (tid & 1) * 8;
-  const int pm = m0 + lr;
-  int pn = 0, ph = 0, pw = 0;
-  if (pm < P) {
-    pn = pm / (H * W);
-    const int r = pm - pn * H * W;
-    ph = r / W;
-    pw = r - ph * W;
-  }
-  for (int k0 = 0; k0 < K; k0 += kTK) {
-    const int tap = k0 / Cin, ci0 = k0 - tap * Cin;
-    const int kh = tap / 3, kw = tap - kh * 3;
-    // A: pixel lr, channels ci0 + lc .. +7 at tap (kh, kw)
-    {
-      uint4 v = make_uint4(0u, 0u, 0u, 0u);
-      const int hh = ph + kh - 1, ww = pw + kw - 1;
-      if (pm < P && hh >= 0 && hh < H && ww >= 0 && ww < W)
-        v = *reinterpret_cast<const uint4 *>(X + (((size_t)pn * H + hh) * W + ww) * Cin + ci0 + lc);
-      *reinterpret_cast<uint4 *>(&As[lr][lc]) = v;
-    }
-    // B: output channel lr, k0 + lc .. +7
-    {
-      uint4 v = make_uint4(0u, 0u, 0u, 0u);
-      const int co = n0 + lr;
-      if (co < Cout) v = *reinterpret_cast<const uint4 *>(Wt + (size_t)co * K + k0 + lc);
-      *reinterpret_cast<uint4 *>(&Bs[lr][lc]) = v;
-    }
-    __syncthreads();
-    const int g = lane >> 2, t2 = (lane & 3) * 2;
-    uint32_t af[2][4], bf[4][2];
-#pragma unroll
-    for (int a = 0; a < 2; ++a) {
-      const int r = wm * 32 + a * 16 + g;
-      af[a][0] = *reinterpret_cast<const uint32_t *>(&As[r][t2]);
-      af[a][1] = *reinterpret_cast<const uint32_t *>(&As[r + 8][t2]);
-      af[a][2] = *reinterpret_cast<const uint32_t *>(&As[r][t2 + 8]);
-      af[a][3] = *reinterpret_cast<const uint32_t *>(&As[r + 8][t2 + 8]);
-    }
-#pragma unroll
-    for (int b = 0; b < 4; ++b) {
-      const int c = wn * 32 + b * 8 + g;
-      bf[b][0] = *reinterpret_cast<const uint32_t *>(&Bs[c][t2]);
-      bf[b][1] = *reinterpret_cast<const uint32_t *>(&Bs[c][t2 + 8]);
-    }
-#pragma unroll
-    for (int a = 0; a < 2; ++a)
-#pragma unroll
-      for (int b = 0; b < 4; ++b) mma_bf16_16816(acc[a][b], af[a], bf[b]);
-    __syncthreads();
-  }
-  // epilogue: rows (pixels) g, g+8; cols t2, t2+1
-  const int g = lane >> 2, t2 = (lane & 3) * 2;
-#pragma unroll
-  for (int a = 0; a < 2; ++a)
-#pragma unroll
-    for (int hrow = 0; hrow < 2; ++hrow) {
-      const int p = m0 + wm * 32 + a * 16 + g + hrow * 8;
-      if (p >= P) continue;
-#pragma unroll
-      for (int b = 0; b < 4; ++b) {
-        const int co = n0 + wn * 32 + b * 8 + t2;
-        if (co >= Cout) continue;
-        float v0 = acc[a][b][hrow * 2], v1 = acc[a][b][hrow * 2 + 1];
-        if (bias) {
-          v0 += bias[co];
-          if (co + 1 < Cout) v1 += bias[co + 1];
-        }
-        if (relu) {
-          v0 = fmaxf(v0, 0.f);
-          v1 = fmaxf(v1, 0.f);
-        }
-        if (Y) {
-          Y[(size_t)p * Cout + co] = __float2bfloat16_rn(v0);
-          if (co + 1 < Cout) Y[(size_t)p * Cout + co + 1] = __float2bfloat16_rn(v1);
-        }
-        if (Yf) {
-          Yf[(size_t)p * Cout + co] = v0;
-          if (co + 1 < Cout) Yf[(size_t)p * Cout + co + 1] = v1;
-        }
-      }
-    }
-}
-
-// Weight and bias gradients: part[split][co][tap][ci] = sum_p dY[p][co] X[p + tap][ci]
-// over the split's pixel range, and part[split][Cout*9*Cin + co] = sum_p dY[p][co].
-// GEMM M = Cout, N = 9 Cin, K = pixels; CTA tile 64 x 64, pixel chunks of 16.
-__global__ void __launch_bounds__(128)
-    k_conv3x3_wgrad(const __nv_bfloat16 *__restrict__ X, int Nb, int H, int W, int Cin,
-                    const __nv_bfloat16 *__restrict__ dY, int Cout, int pix_per_split,
-                    float *__restrict__ part) {
-  __shared__ __align__(16) __nv_bfloat16 As[kTM][kTK + 8];  // cout x pixels (dY^T)
-  __shared__ __align__(16) __nv_bfloat16 Bs[kTN][kTK + 8];  // (tap, ci) x pixels (patches^T)
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int wm = warp >> 1, wn = warp & 1;
-  const int P = Nb * H * W;
-  const int Ncol = 9 * Cin;
-  const size_t stride = (size_t)Cout * Ncol + Cout;
-  const int m0 = blockIdx.x * kTM, n0 = blockIdx.y * kTN;
-  const int pb = blockIdx.z * pix_per_split, pe = min(P, pb + pix_per_split);
-  const bool do_bias = blockIdx.y == 0;
-  float bsum = 0.f;
-  float acc[2][4][4];
-#pragma unroll
-  for (int a = 0; a < 2; ++a)
-#pragma unroll
-    for (int b = 0; b < 4; ++b)
-#pragma unroll
-      for (int c = 0; c < 4; ++c) acc[a][b][c] = 0.f;
-  const int px = tid >> 3, c8 = (tid & 7) * 8;  // loaders: 16 pixels x 8 chunks of 8
-  for (int k0 = pb; k0 < pe; k0 += kTK) {
-    const int p = k0 + px;
-    {
-      uint4 v = make_uint4(0u, 0u, 0u, 0u);
-      if (p < pe && m0 + c8 < Cout) v = *reinterpret_cast<const uint4 *>(dY + (size_t)p * Cout + m0 + c8);
-      const __nv_bfloat16 *e = reinterpret_cast<const __nv_bfloat16 *>(&v);
-#pragma unroll
-      for (int q = 0; q < 8; ++q) As[c8 + q][px] = e[q];
-    }
-    {
-      const int col = n0 + c8;
-      uint4 v = make_uint4(0u, 0u, 0u, 0u);
-      if (p < pe && col < Ncol) {
-        const int tap = col / Cin, ci = col - tap * Cin;
-        const int kh = tap / 3, kw = tap - kh * 3;
-        const int n = p / (H * W), r = p - n * H * W;
-        const int hh = r / W + kh - 1, ww = r % W + kw - 1;
-        if (hh >= 0 && hh < H && ww >= 0 && ww < W)
-          v = *reinterpret_cast<const uint4 *>(X + (((size_t)n * H + hh) * W + ww) * Cin + ci);
-      }
-      const __nv_bfloat16 *e = reinterpret_cast<const __nv_bfloat16 *>(&v);
-#pragma unroll
-      for (int q = 0; q < 8; ++q) Bs[c8 + q][px] = e[q];
-    }
-    __syncthreads();
-    if (do_bias && tid < kTM) {
-#pragma unroll
-      for (int q = 0; q < kTK; ++q) bsum += __bfloat162float(As[tid][q]);
-    }
-    const int g = lane >> 2, t2 = (lane & 3) * 2;
-    uint32_t af[2][4], bf[4][2];
-#pragma unroll
-    for (int a = 0; a < 2; ++a) {
-      const int r = wm * 32 + a * 16 + g;
-      af[a][0] = *reinterpret_cast<const uint32_t *>(&As[r][t2]);
-      af[a][1] = *reinterpret_cast<const uint32_t *>(&As[r + 8][t2]);
-      af[a][2] = *reinterpret_cast<const uint32_t *>(&As[r][t2 + 8]);
-      af[a][3] = *reinterpret_cast<const uint32_t *>(&As[r + 8][t2 + 8]);
-    }
-#pragma unroll
-    for (int b = 0; b < 4; ++b) {
-      const int c = wn * 32 + b * 8 + g;
-      bf[b][0] = *reinterpret_cast<const uint32_t *>(&Bs[c][t2]);
-      bf[b][1] = *reinterpret_cast<const uint32_t *>(&Bs[c][t2 + 8]);
-    }
-#pragma unroll
-    for (int a = 0; a < 2; ++a)
-#pragma unroll
-      for (int b = 0; b < 4; ++b) mma_bf16_16816(acc[a][b], af[a], bf[b]);
-    __syncthreads();
-  }
-  float *dst = part + (size_t)blockIdx.z * stride;
-  const int g = lane >> 2, t2 = (lane & 3) * 2;
-#pragma unroll
-  for (int a = 0; a < 2; ++a)
-#pragma unroll
-    for (int hrow = 0; hrow < 2; ++hrow) {
-      const int co = m0 + wm * 32 + a * 16 + g + hrow * 8;
-      if (co >= Cout) continue;
-#pragma unroll
-      for (int b = 0; b < 4; ++b) {
-        const int col = n0 + wn * 32 + b * 8 + t2;  // Ncol is a multiple of 16: col + 1 < Ncol too
-        if (col < Ncol)
-          *reinterpret_cast<float2 *>(dst + (size_t)co * Ncol + col) =
-              make_float2(acc[a][b][hrow * 2], acc[a][b][hrow * 2 + 1]);
-      }
-    }
-  if (do_bias && tid < kTM && m0 + tid < Cout) dst[(size_t)Cout * Ncol + m0 + tid] = bsum;
-}
-
-__global__ void k_reduce_splits(const float *__restrict__ part, int n_part, size_t stride, size_t n_out,
-                                float *__restrict__ out) {
-  const size_t j = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-  if (j >= n_out) return;
+// out[j] = sum_i part[i * stride + j]: 32 outputs per block, 8 groups of
+// partials (group g sums i = g, g + 8, ... in order), then the 8 group sums
+// in order -- a fixed summation tree
+__global__ void __launch_bounds__(256)
+    k_reduce_splits(const float *__restrict__ part, int n_part, size_t stride, size_t n_out,
+                    float *__restrict__ out) {
+  __shared__ float red[8][33];
+  const int jl = threadIdx.x & 31, g = threadIdx.x >> 5;
+  const size_t j = blockIdx.x * (size_t)32 + jl;
   float s = 0.f;
-  for (int i = 0; i < n_part; ++i) s += part[(size_t)i * stride + j];
-  out[j] = s;
+  if (j < n_out)
+    for (int i = g; i < n_part; i += 8) s += part[(size_t)i * stride + j];
+  red[g][jl] = s;
+  __syncthreads();
+  if (g == 0 && j < n_out) {
+    float t = red[0][jl];
+#pragma unroll
+    for (int q = 1; q < 8; ++q) t += red[q][jl];
+    out[j] = t;
+  }
 }
 
 // W[co][kh][kw][ci] -> Wt[ci][2-kh][2-kw][co] (backward-data weights)
@@ -263,60 +54,124 @@ __global__ void k_flip_transpose(const __nv_bfloat16 *__restrict__ Wsrc, int Cou
   Wdst[((size_t)ci * 9 + (2 - kh) * 3 + (2 - kw)) * Cout + co] = Wsrc[i];
 }
 
-// dY *= (Y > 0)  in place (ReLU backward, Y is the post-ReLU activation)
-__global__ void k_relu_bwd(__nv_bfloat16 *__restrict__ dY, const __nv_bfloat16 *__restrict__ Y, size_t n) {
-  const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-  if (i < n && !(__bfloat162float(Y[i]) > 0.f)) dY[i] = __float2bfloat16_rn(0.f);
+// Eight bf16 channels as four bf16x2 <-> eight floats.
+struct V8 {
+  float f[8];
+};
+__device__ __forceinline__ V8 ld8(const __nv_bfloat16 *p) {
+  const uint4 u = *reinterpret_cast<const uint4 *>(p);
+  const __nv_bfloat162 *h = reinterpret_cast<const __nv_bfloat162 *>(&u);
+  V8 r;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const float2 t = __bfloat1622float2(h[q]);
+    r.f[2 * q] = t.x;
+    r.f[2 * q + 1] = t.y;
+  }
+  return r;
+}
+__device__ __forceinline__ void st8(__nv_bfloat16 *p, const V8 &v) {
+  uint4 u;
+  __nv_bfloat162 *h = reinterpret_cast<__nv_bfloat162 *>(&u);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) h[q] = __floats2bfloat162_rn(v.f[2 * q], v.f[2 * q + 1]);
+  *reinterpret_cast<uint4 *>(p) = u;
 }
 
-// 2x2 average pooling (H, W even) and its adjoint
+// dY *= (Y > 0) in place (ReLU backward, Y is the post-ReLU activation);
+// 8 channels per thread
+__global__ void k_relu_bwd(__nv_bfloat16 *__restrict__ dY, const __nv_bfloat16 *__restrict__ Y, size_t n8) {
+  const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (i >= n8) return;
+  V8 d = ld8(dY + 8 * i);
+  const V8 y = ld8(Y + 8 * i);
+#pragma unroll
+  for (int q = 0; q < 8; ++q)
+    if (!(y.f[q] > 0.f)) d.f[q] = 0.f;
+  st8(dY + 8 * i, d);
+}
+
+// 2x2 average pooling (H, W even) and its adjoint; one thread per 8 channels
+// of a coarse pixel
 __global__ void k_pool2(const __nv_bfloat16 *__restrict__ X, int Nb, int H, int W, int C,
                         __nv_bfloat16 *__restrict__ Y) {
   const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-  const int Ho = H / 2, Wo = W / 2;
-  if (i >= (size_t)Nb * Ho * Wo * C) return;
-  const int c = i % C;
-  const size_t q = i / C;
+  const int Ho = H / 2, Wo = W / 2, C8 = C / 8;
+  if (i >= (size_t)Nb * Ho * Wo * C8) return;
+  const int c = (int)(i % C8) * 8;
+  const size_t q = i / C8;
   const int wo = q % Wo, ho = (q / Wo) % Ho, n = q / ((size_t)Wo * Ho);
   const size_t b = (((size_t)n * H + 2 * ho) * W + 2 * wo) * C + c;
   const size_t row = (size_t)W * C;
-  const float s = (__bfloat162float(X[b]) + __bfloat162float(X[b + C])) +
-                  (__bfloat162float(X[b + row]) + __bfloat162float(X[b + row + C]));
-  Y[i] = __float2bfloat16_rn(0.25f * s);
+  const V8 a0 = ld8(X + b), a1 = ld8(X + b + C), a2 = ld8(X + b + row), a3 = ld8(X + b + row + C);
+  V8 o;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) o.f[k] = 0.25f * ((a0.f[k] + a1.f[k]) + (a2.f[k] + a3.f[k]));
+  st8(Y + q * C + c, o);
 }
 __global__ void k_pool2_bwd(const __nv_bfloat16 *__restrict__ dY, int Nb, int H, int W, int C,
                             __nv_bfloat16 *__restrict__ dX, int accumulate) {
   const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-  if (i >= (size_t)Nb * H * W * C) return;
-  const int c = i % C;
-  const size_t q = i / C;
-  const int w = q % W, h = (q / W) % H, n = q / ((size_t)W * H);
-  const float g = 0.25f * __bfloat162float(dY[(((size_t)n * (H / 2) + h / 2) * (W / 2) + w / 2) * C + c]);
-  dX[i] = __float2bfloat16_rn(accumulate ? __bfloat162float(dX[i]) + g : g);
+  const int Ho = H / 2, Wo = W / 2, C8 = C / 8;
+  if (i >= (size_t)Nb * Ho * Wo * C8) return;
+  const int c = (int)(i % C8) * 8;
+  const size_t q = i / C8;
+  const int wo = q % Wo, ho = (q / Wo) % Ho, n = q / ((size_t)Wo * Ho);
+  V8 g = ld8(dY + q * C + c);
+#pragma unroll
+  for (int k = 0; k < 8; ++k) g.f[k] *= 0.25f;
+  const size_t b = (((size_t)n * H + 2 * ho) * W + 2 * wo) * C + c;
+  const size_t off[4] = {0, (size_t)C, (size_t)W * C, (size_t)W * C + C};
+#pragma unroll
+  for (int t = 0; t < 4; ++t) {
+    V8 o = g;
+    if (accumulate) {
+      const V8 d = ld8(dX + b + off[t]);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) o.f[k] = d.f[k] + g.f[k];
+    }
+    st8(dX + b + off[t], o);
+  }
 }
-// nearest 2x upsampling plus a skip tensor, and the adjoint of the upsampling
+// nearest 2x upsampling plus a skip tensor (nullable), and the adjoint of
+// the upsampling; one thread per 8 channels of a coarse pixel
 __global__ void k_up2_add(const __nv_bfloat16 *__restrict__ X, const __nv_bfloat16 *__restrict__ skip, int Nb,
                           int H, int W, int C, __nv_bfloat16 *__restrict__ Y) {
   const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-  const int Ho = 2 * H, Wo = 2 * W;
-  if (i >= (size_t)Nb * Ho * Wo * C) return;
-  const int c = i % C;
-  const size_t q = i / C;
-  const int wo = q % Wo, ho = (q / Wo) % Ho, n = q / ((size_t)Wo * Ho);
-  const __nv_bfloat16 v = X[(((size_t)n * H + ho / 2) * W + wo / 2) * C + c];
-  Y[i] = skip ? __float2bfloat16_rn(__bfloat162float(v) + __bfloat162float(skip[i])) : v;
+  const int C8 = C / 8;
+  if (i >= (size_t)Nb * H * W * C8) return;
+  const int c = (int)(i % C8) * 8;
+  const size_t q = i / C8;
+  const int w = q % W, h = (q / W) % H, n = q / ((size_t)W * H);
+  const V8 v = ld8(X + q * C + c);
+  const size_t b = (((size_t)n * 2 * H + 2 * h) * 2 * W + 2 * w) * C + c;
+  const size_t off[4] = {0, (size_t)C, (size_t)2 * W * C, (size_t)2 * W * C + C};
+#pragma unroll
+  for (int t = 0; t < 4; ++t) {
+    V8 o = v;
+    if (skip) {
+      const V8 k8 = ld8(skip + b + off[t]);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) o.f[k] = v.f[k] + k8.f[k];
+    }
+    st8(Y + b + off[t], o);
+  }
 }
 __global__ void k_up2_bwd(const __nv_bfloat16 *__restrict__ dY, int Nb, int H, int W, int C,
                           __nv_bfloat16 *__restrict__ dX) {
   const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-  if (i >= (size_t)Nb * H * W * C) return;
-  const int c = i % C;
-  const size_t q = i / C;
+  const int C8 = C / 8;
+  if (i >= (size_t)Nb * H * W * C8) return;
+  const int c = (int)(i % C8) * 8;
+  const size_t q = i / C8;
   const int w = q % W, h = (q / W) % H, n = q / ((size_t)W * H);
   const size_t b = (((size_t)n * 2 * H + 2 * h) * 2 * W + 2 * w) * C + c;
   const size_t row = (size_t)2 * W * C;
-  dX[i] = __float2bfloat16_rn((__bfloat162float(dY[b]) + __bfloat162float(dY[b + C])) +
-                              (__bfloat162float(dY[b + row]) + __bfloat162float(dY[b + row + C])));
+  const V8 a0 = ld8(dY + b), a1 = ld8(dY + b + C), a2 = ld8(dY + b + row), a3 = ld8(dY + b + row + C);
+  V8 o;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) o.f[k] = (a0.f[k] + a1.f[k]) + (a2.f[k] + a3.f[k]);
+  st8(dX + q * C + c, o);
 }
 
 // Complex images [Nb][HW] (float2) -> NHWC bf16 with C channels: (re, im)
@@ -528,44 +383,9 @@ inline unsigned blocks(size_t n, int t = 256) { return (unsigned)((n + t - 1) / 
 
 }  // namespace
 
-cudaError_t conv3x3(const Tensor4 &x, const __nv_bfloat16 *w, int cout, const float *bias, bool relu,
-                    __nv_bfloat16 *y, float *yf, cudaStream_t s) {
-  const int P = x.n * x.h * x.w;
-  dim3 grid((P + kTM - 1) / kTM, (cout + kTN - 1) / kTN);
-  k_conv3x3<<<grid, 128, 0, s>>>(x.p, x.n, x.h, x.w, x.c, w, cout, bias, relu ? 1 : 0, y, yf);
-  return cudaGetLastError();
-}
-
-// Pixel splits of the weight gradient: about 4 x 152 CTAs in total (a fixed
-// count, so that results do not depend on the device), at least 256 pixels
-// per split.
-int wgrad_splits(const Tensor4 &x, int cout) {
-  const int P = x.n * x.h * x.w;
-  const int tiles = ((cout + kTM - 1) / kTM) * ((9 * x.c + kTN - 1) / kTN);
-  int want = std::max(1, (608 + tiles - 1) / tiles);
-  want = std::min(want, std::max(1, P / 256));
-  const int per = ((P + want - 1) / want + kTK - 1) / kTK * kTK;
-  return (P + per - 1) / per;
-}
-
-size_t wgrad_part_floats(const Tensor4 &x, int cout) {
-  return (size_t)wgrad_splits(x, cout) * ((size_t)cout * 9 * x.c + cout);
-}
-
-cudaError_t conv3x3_wgrad(const Tensor4 &x, const __nv_bfloat16 *dy, int cout, float *part, int *n_split,
-                          cudaStream_t s) {
-  const int P = x.n * x.h * x.w;
-  const int splits = wgrad_splits(x, cout);
-  const int per = ((P + splits - 1) / splits + kTK - 1) / kTK * kTK;
-  dim3 grid((cout + kTM - 1) / kTM, (9 * x.c + kTN - 1) / kTN, splits);
-  k_conv3x3_wgrad<<<grid, 128, 0, s>>>(x.p, x.n, x.h, x.w, x.c, dy, cout, per, part);
-  *n_split = splits;
-  return cudaGetLastError();
-}
-
 cudaError_t reduce_splits(const float *part, int n_part, size_t stride, size_t n_out, float *out,
                           cudaStream_t s) {
-  k_reduce_splits<<<blocks(n_out), 256, 0, s>>>(part, n_part, stride, n_out, out);
+  k_reduce_splits<<<(unsigned)((n_out + 31) / 32), 256, 0, s>>>(part, n_part, stride, n_out, out);
   return cudaGetLastError();
 }
 
@@ -575,29 +395,29 @@ cudaError_t flip_transpose(const __nv_bfloat16 *w, int cout, int cin, __nv_bfloa
 }
 
 cudaError_t relu_bwd(__nv_bfloat16 *dy, const __nv_bfloat16 *y, size_t n, cudaStream_t s) {
-  k_relu_bwd<<<blocks(n), 256, 0, s>>>(dy, y, n);
+  k_relu_bwd<<<blocks(n / 8), 256, 0, s>>>(dy, y, n / 8);
   return cudaGetLastError();
 }
 
 cudaError_t pool2(const Tensor4 &x, __nv_bfloat16 *y, cudaStream_t s) {
-  k_pool2<<<blocks(x.count() / 4), 256, 0, s>>>(x.p, x.n, x.h, x.w, x.c, y);
+  k_pool2<<<blocks(x.count() / 32), 256, 0, s>>>(x.p, x.n, x.h, x.w, x.c, y);
   return cudaGetLastError();
 }
 
 cudaError_t pool2_bwd(const __nv_bfloat16 *dy, const Tensor4 &dx, bool accumulate, cudaStream_t s) {
-  k_pool2_bwd<<<blocks(dx.count()), 256, 0, s>>>(dy, dx.n, dx.h, dx.w, dx.c, dx.p, accumulate ? 1 : 0);
+  k_pool2_bwd<<<blocks(dx.count() / 32), 256, 0, s>>>(dy, dx.n, dx.h, dx.w, dx.c, dx.p, accumulate ? 1 : 0);
   return cudaGetLastError();
 }
 
 cudaError_t up2(const Tensor4 &x, __nv_bfloat16 *y, cudaStream_t s) { return up2_add(x, nullptr, y, s); }
 
 cudaError_t up2_add(const Tensor4 &x, const __nv_bfloat16 *skip, __nv_bfloat16 *y, cudaStream_t s) {
-  k_up2_add<<<blocks(x.count() * 4), 256, 0, s>>>(x.p, skip, x.n, x.h, x.w, x.c, y);
+  k_up2_add<<<blocks(x.count() / 8), 256, 0, s>>>(x.p, skip, x.n, x.h, x.w, x.c, y);
   return cudaGetLastError();
 }
 
 cudaError_t up2_bwd(const __nv_bfloat16 *dy, const Tensor4 &dx, cudaStream_t s) {
-  k_up2_bwd<<<blocks(dx.count()), 256, 0, s>>>(dy, dx.n, dx.h, dx.w, dx.c, dx.p);
+  k_up2_bwd<<<blocks(dx.count() / 8), 256, 0, s>>>(dy, dx.n, dx.h, dx.w, dx.c, dx.p);
   return cudaGetLastError();
 }
 

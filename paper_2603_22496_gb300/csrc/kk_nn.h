@@ -17,20 +17,37 @@ struct Tensor4 {
   size_t count() const { return (size_t)n * h * w * c; }
 };
 
-// y = act(conv3x3(x, w) + bias), zero padding 1, stride 1.  w is
-// [cout][3][3][cin] bf16; bias (nullable) fp32; y bf16 and / or yf fp32
-// (either nullable), both [pixels][cout].
-cudaError_t conv3x3(const Tensor4 &x, const __nv_bfloat16 *w, int cout, const float *bias, bool relu,
-                    __nv_bfloat16 *y, float *yf, cudaStream_t s);
+// y = act(conv3x3(x, w) + bias), zero padding 1, stride 1, on the tensor
+// cores (tcgen05, TMEM accumulator).  w is [cout][3][3][cin] bf16; bias
+// (nullable) fp32; y bf16 and / or yf fp32 (either nullable), both
+// [pixels][cout]; cin, cout multiples of 16.  A CTA that gives up on a
+// bounded wait writes KK_ERR_TIMEOUT to *status (nullable: the library's
+// layer status word).
+cudaError_t conv3x3_tc(const Tensor4 &x, const __nv_bfloat16 *w, int cout, const float *bias, bool relu,
+                       __nv_bfloat16 *y, float *yf, int *status, cudaStream_t s);
+// read and reset the layer status word
+cudaError_t conv_status(int *out);
 
-// Weight (and bias) gradient of a 3x3 convolution.  Per pixel split the
-// partial sums go to part[split][cout * 9 * cin + cout] (weights, then
-// bias); reduce_splits then sums them in split order (deterministic).
+// TMA-fed forms (kk_conv_tma.cu) for shapes whose pixel tiles are whole row
+// segments or rows of one image: return false (nothing launched) when the
+// shape does not qualify, else launch and put the launch error in *err.
+bool conv3x3_tma(const Tensor4 &x, const __nv_bfloat16 *w, int cout, const float *bias, bool relu,
+                 __nv_bfloat16 *y, float *yf, int *status, cudaStream_t s, cudaError_t *err);
+bool wgrad_tma(const Tensor4 &x, const __nv_bfloat16 *dy, int cout, float *part, int splits, int pix_per_split,
+               int *status, cudaStream_t s, cudaError_t *err);
+cudaError_t tma_status(int *out);
+
+// Weight (and bias) gradient of a 3x3 convolution on the tensor cores.  The
+// weight partial sums of pixel split i go to part[i][cout * 9 * cin]
+// (n_split splits), then the bias partials of pixel block b to
+// part[n_split * cout * 9 * cin + b * cout + co] (n_bias blocks);
+// reduce_splits sums each in a fixed order (deterministic).
 int wgrad_splits(const Tensor4 &x, int cout);
+int bias_blocks(int pixels, int cout);
 size_t wgrad_part_floats(const Tensor4 &x, int cout);
 cudaError_t conv3x3_wgrad(const Tensor4 &x, const __nv_bfloat16 *dy, int cout, float *part, int *n_split,
-                          cudaStream_t s);
-// out[j] = sum_{i < n_part} part[i * stride + j] for j < n_out, i ascending
+                          int *n_bias, int *status, cudaStream_t s);
+// out[j] = sum_{i < n_part} part[i * stride + j] for j < n_out, in a fixed order
 cudaError_t reduce_splits(const float *part, int n_part, size_t stride, size_t n_out, float *out,
                           cudaStream_t s);
 

@@ -40,7 +40,11 @@ def _rel(a, b):
     return float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / np.linalg.norm(np.ravel(b)))
 
 
-SHAPES = [(2, 13, 21, 16, 16), (1, 32, 40, 32, 48), (3, 9, 70, 64, 32), (1, 1, 5, 16, 64), (2, 16, 16, 256, 128)]
+# shapes gathered with cp.async (tiles that cross rows or images) ...
+SHAPES = [(2, 13, 21, 16, 16), (1, 32, 40, 32, 48), (3, 9, 70, 64, 32), (1, 1, 5, 16, 64)]
+# ... and shapes fed by TMA (128-pixel tiles = row segments or whole rows; 64 for the weight gradient)
+SHAPES += [(2, 16, 16, 256, 128), (1, 4, 256, 32, 32), (2, 8, 128, 64, 64), (1, 16, 32, 128, 256),
+           (3, 32, 64, 16, 48), (2, 8, 64, 16, 16)]
 
 
 @pytest.mark.parametrize("n,h,w,cin,cout", SHAPES)
@@ -55,6 +59,7 @@ def test_conv3x3_forward(n, h, w, cin, cout):
     yb = torch.empty((n, h, w, cout), dtype=torch.bfloat16, device="cuda")
     kb.kk_nn_conv3x3(xt, wt, bt, relu=True, y=yb, yf=yf)
     torch.cuda.synchronize()
+    assert kb.kk_nn_status() == kb.KK_OK
     ref = nn.relu(nn.conv3x3(x, wd, b.astype(np.float64)))
     assert _rel(yf.cpu().numpy(), ref) <= 1e-5
     # the BF16 output is the FP32 result rounded once
@@ -70,6 +75,7 @@ def test_conv3x3_backward_data(n, h, w, cin, cout):
     dx = torch.empty((n, h, w, cin), dtype=torch.bfloat16, device="cuda")
     kb.kk_nn_conv3x3_dgrad(dyt, wt, dx)
     torch.cuda.synchronize()
+    assert kb.kk_nn_status() == kb.KK_OK
     assert _rel(dx.float().cpu().numpy(), nn.conv3x3_dx(dy, wd)) <= 3e-3
 
 
@@ -165,6 +171,29 @@ def test_network_forward_loss_and_gradient_match_oracle():
     out2 = net.forward(_c2t(img), torch.from_numpy(s_in).cuda())
     torch.cuda.synchronize()
     assert torch.equal(out2, out)
+    assert net.status() == kb.KK_OK
+
+
+def test_network_gradient_at_256_matches_oracle():
+    """One 256 x 256 image: every layer runs on the TMA-fed kernels."""
+    import torch
+    C = 32
+    net, theta, img, tgt = _net_case(C, n=1, H=256, W=256, seed=13)
+    s_in = np.array([0.5], np.float32)
+    g = torch.empty(net.n_params, dtype=torch.float32, device="cuda")
+    loss = net.loss_grad(_c2t(img), _c2t(tgt), torch.from_numpy(s_in).cuda(), grad=g)
+    torch.cuda.synchronize()
+    assert net.status() == kb.KK_OK
+    th, xin = _oracle_operands(theta, img, s_in.astype(np.float64), C)
+    L, rg = nn.backward(th, C, xin, None, tgt, None)
+    assert abs(float(loss) - L) <= 1e-2 * L
+    gg = g.cpu().numpy().astype(np.float64)
+    assert _rel(gg, rg) <= 2e-2
+    off = 0
+    for i, (ci, co, _) in enumerate(nn.layer_shapes(C)):
+        k = co * 9 * ci + co
+        assert _rel(gg[off:off + k], rg[off:off + k]) <= 5e-2, i
+        off += k
 
 
 def test_adam_steps_match_oracle():
