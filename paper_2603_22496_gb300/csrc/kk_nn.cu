@@ -286,6 +286,74 @@ __global__ void k_dft_axis(const float2 *__restrict__ in, int Nb, int H, int W, 
   out[i] = acc;
 }
 
+// Radix-2 Stockham FFT along one axis of complex [Nb][H][W] images, for a
+// power-of-two length L (the row length W or the column length H).  A block
+// takes 16 lines (16 consecutive columns for the column pass, so that each
+// row of the tile is one 128-byte segment) and ping-pongs them through shared
+// memory: at span Ns, element j and j + L/2 combine with the twiddle
+// exp(sign 2 pi i (j mod Ns) / (2 Ns)) into positions (j / Ns) 2 Ns + j mod Ns
+// and that + Ns, which leaves the result in natural order.
+constexpr int kFftLines = 16;
+__global__ void __launch_bounds__(256)
+    k_fft_axis(const float2 *__restrict__ in, int Nb, int H, int W, int axis, int sign, int logL,
+               float2 *__restrict__ out) {
+  extern __shared__ float2 fbuf[];  // 2 x kFftLines x L
+  const int L = 1 << logL;
+  float2 *x = fbuf, *y = fbuf + kFftLines * L;
+  const int lines_per_img = axis == 0 ? W : H;  // columns (axis 0) or rows (axis 1)
+  const int line0 = blockIdx.x * kFftLines;     // over Nb * lines_per_img
+  const int img = line0 / lines_per_img, l0 = line0 - img * lines_per_img;
+  const size_t base = (size_t)img * H * W;
+  // load: element e of line q at x[q * L + e]
+  for (int t = threadIdx.x; t < kFftLines * L; t += blockDim.x) {
+    int q, e;
+    size_t g;
+    if (axis == 0) {  // columns l0 + q, rows e: tile rows are contiguous
+      q = t % kFftLines;
+      e = t / kFftLines;
+      g = base + (size_t)e * W + l0 + q;
+    } else {          // rows l0 + q
+      q = t / L;
+      e = t % L;
+      g = base + (size_t)(l0 + q) * W + e;
+    }
+    x[q * L + e] = in[g];
+  }
+  __syncthreads();
+  for (int ls = 0; ls < logL; ++ls) {
+    const int Ns = 1 << ls;
+    for (int t = threadIdx.x; t < kFftLines * (L / 2); t += blockDim.x) {
+      const int q = t / (L / 2), j = t % (L / 2);
+      const int k = j & (Ns - 1);
+      float sn, cs;
+      sincospif((float)sign * (float)k / (float)Ns, &sn, &cs);  // angle = sign 2 pi k / (2 Ns)
+      const float2 v0 = x[q * L + j], a = x[q * L + j + L / 2];
+      const float2 v1 = make_float2(a.x * cs - a.y * sn, a.x * sn + a.y * cs);
+      const int d = ((j >> ls) << (ls + 1)) + k;
+      y[q * L + d] = make_float2(v0.x + v1.x, v0.y + v1.y);
+      y[q * L + d + Ns] = make_float2(v0.x - v1.x, v0.y - v1.y);
+    }
+    __syncthreads();
+    float2 *tmp = x;
+    x = y;
+    y = tmp;
+  }
+  for (int t = threadIdx.x; t < kFftLines * L; t += blockDim.x) {
+    int q, e;
+    size_t g;
+    if (axis == 0) {
+      q = t % kFftLines;
+      e = t / kFftLines;
+      g = base + (size_t)e * W + l0 + q;
+    } else {
+      q = t / L;
+      e = t % L;
+      g = base + (size_t)(l0 + q) * W + e;
+    }
+    out[g] = x[q * L + e];
+  }
+}
+
 // one block: maxima of |Sc|, |Sf|, then G = Sc / Sf on the joint mask
 __global__ void __launch_bounds__(kRedThreads)
     k_judge_filter(const float2 *__restrict__ Sc, const float2 *__restrict__ Sf, int hw, float rho,
@@ -453,11 +521,34 @@ cudaError_t to_bf16(const float *a, __nv_bfloat16 *b, size_t n, cudaStream_t s) 
   return cudaGetLastError();
 }
 
-cudaError_t dft2(const float2 *in, int nb, int h, int w, int sign, float2 *tmp, float2 *out, cudaStream_t s) {
-  const size_t n = (size_t)nb * h * w;
-  k_dft_axis<<<blocks(n), 256, 0, s>>>(in, nb, h, w, 1, sign, tmp);
-  k_dft_axis<<<blocks(n), 256, 0, s>>>(tmp, nb, h, w, 0, sign, out);
+namespace {
+int log2_exact(int n) {
+  int l = 0;
+  while ((1 << l) < n) ++l;
+  return (1 << l) == n ? l : -1;
+}
+}  // namespace
+
+// Stockham FFT along an axis when its length is a power of two (and the
+// lines split into blocks of 16), else the direct DFT
+cudaError_t dft_axis(const float2 *in, int nb, int h, int w, int axis, int sign, float2 *out, cudaStream_t s) {
+  const int L = axis == 0 ? h : w, lines = axis == 0 ? w : h;
+  const int lg = log2_exact(L);
+  if (lg >= 1 && L <= 512 && lines % kFftLines == 0) {
+    const size_t smem = 2 * (size_t)kFftLines * L * sizeof(float2);
+    cudaError_t e = cudaFuncSetAttribute(k_fft_axis, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_fft_axis<<<(unsigned)((size_t)nb * lines / kFftLines), 256, smem, s>>>(in, nb, h, w, axis, sign, lg, out);
+  } else {
+    k_dft_axis<<<blocks((size_t)nb * h * w), 256, 0, s>>>(in, nb, h, w, axis, sign, out);
+  }
   return cudaGetLastError();
+}
+
+cudaError_t dft2(const float2 *in, int nb, int h, int w, int sign, float2 *tmp, float2 *out, cudaStream_t s) {
+  cudaError_t e = dft_axis(in, nb, h, w, 1, sign, tmp, s);
+  if (e == cudaSuccess) e = dft_axis(tmp, nb, h, w, 0, sign, out, s);
+  return e;
 }
 
 cudaError_t judge_filter(const float2 *Sc, const float2 *Sf, int hw, float rho, float2 *G, cudaStream_t s) {
