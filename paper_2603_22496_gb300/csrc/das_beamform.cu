@@ -12,6 +12,16 @@
 // ~30 FP32 operations per pixel per element against N gathers.
 // Index bound: W0 = floor(min s_in) + floor(min R) - 2 over the tile and the
 // staged window length >= span_in + span_out + 6 keep every read in [0, win).
+//
+// Two kernels:
+//  * k_das_gather_staged (windows of up to 256 entries, i.e. pixels up to
+//    about 0.3 mm at 20 MHz): 32 x 16 tiles, 4 warps of 4 rows; channels
+//    (i, l) in stages of 4-16 transmits of one element; the raw samples of
+//    stage s+1 are loaded into registers while stage s is gathered (as in the
+//    KK gather), the per-channel tables are double-buffered, and the receive
+//    delay of the thread's pixels is recomputed only when the element
+//    changes;
+//  * k_das_gather (any window): 32 x 32 tiles, synchronous staging.
 #include "kk_internal.h"
 
 namespace kk {
@@ -188,6 +198,184 @@ __global__ void __launch_bounds__(kGatherThreads)
   }
 }
 
+// Staged-window DAS gather for windows of at most 256 entries (see above).
+// Entries E[k] = (y[k], y[k+1] - y[k]) (zero outside [0, T-2]): one 16-byte
+// load and two FMAs per pixel-pair.
+template <int STAGE, int NPT, int MINB>
+__global__ void __launch_bounds__(kGatherThreads, MINB)
+    k_das_gather_staged(const float2 *__restrict__ y, int N, int L, int T, const long long *__restrict__ dA,
+                        const long long *__restrict__ dB, const long long *__restrict__ dC,
+                        const float *__restrict__ dAf, const float *__restrict__ dBf,
+                        const float2 *__restrict__ xs, const float2 *__restrict__ zs,
+                        const float2 *__restrict__ us, int nx, int nz, int tiles_x, int win, int split,
+                        float2 *__restrict__ B, float *__restrict__ I) {
+  constexpr int ROWS = 4, TZ = 16;
+  constexpr int PPW = STAGE / 4;   // channels staged by each warp
+  constexpr int QPP = NPT / PPW;   // entries per lane per staged channel
+  static_assert(QPP * PPW == NPT && STAGE % 4 == 0 && STAGE <= 32, "stage shape");
+  extern __shared__ float4 sw[];   // [STAGE][win]
+  __shared__ WarpChan s_wc[2][4][STAGE];
+  __shared__ float2 s_ab[2][STAGE];
+  __shared__ int s_w0[2][STAGE];
+  __shared__ int s_row[2][STAGE];
+
+  const int tid = threadIdx.x;
+  const int warp = tid >> 5, lane = tid & 31;
+  const int tile = blockIdx.x;
+  const int ix0 = (tile % tiles_x) * kTileX;
+  const int iz0 = (tile / tiles_x) * TZ;
+  const int ix = ix0 + lane;
+  const int izb = iz0 + warp * ROWS;
+  const float dl = (float)(lane - 16);
+  const float2 xq = __ldg(xs + ix);
+  float2 z2[ROWS];
+#pragma unroll
+  for (int r = 0; r < ROWS; ++r) z2[r] = df_sqr(__ldg(zs + izb + r));
+  const float xlo = __ldg(xs + ix0).x, xhi = __ldg(xs + ix0 + kTileX - 1).x;
+  const float zlo = __ldg(zs + iz0).x;
+
+  float2 acc[ROWS];
+#pragma unroll
+  for (int r = 0; r < ROWS; ++r) acc[r] = make_float2(0.f, 0.f);
+
+  const int sidx = blockIdx.y;
+  const int lb = (int)(((long long)L * sidx) / split), le = (int)(((long long)L * (sidx + 1)) / split);
+  const int spl = (N + STAGE - 1) / STAGE;  // stages per element
+  const int nq = (le - lb) * spl;
+
+  // tables of stage q into buffer b_: transmits ps.. of element l
+#define DAS_TABLES(Q, B_)                                                                             \
+  {                                                                                                   \
+    const int l_ = lb + (Q) / spl, ps_ = ((Q) % spl) * STAGE, ns_ = min(STAGE, N - ps_);             \
+    if (lane < ns_) {                                                                                 \
+      const float2 u_ = __ldg(us + l_);                                                               \
+      const float xc_ = fminf(fmaxf(u_.x, xlo), xhi) - u_.x;                                          \
+      const int kmin_ = (int)floorf(sqrtf(fmaf(xc_, xc_, zlo * zlo)));                                \
+      const int i_ = ps_ + lane;                                                                      \
+      const long long A_ = __ldg(dA + i_), Bq_ = __ldg(dB + i_), Cq_ = __ldg(dC + i_);                \
+      const long long smin_ = Cq_ + Bq_ * (long long)iz0 + A_ * (long long)(A_ >= 0 ? ix0 : ix0 + kTileX - 1); \
+      const int w0_ = (int)(smin_ >> 32) + kmin_ - 2;                                                 \
+      const long long sref_ = Cq_ + Bq_ * (long long)(iz0 + warp * ROWS + ROWS / 2) + A_ * (long long)(ix0 + 16); \
+      const int kref_ = (int)(sref_ >> 32);                                                           \
+      WarpChan wc_;                                                                                   \
+      wc_.phi = (float)(unsigned)(sref_ & 0xffffffffLL) * 0x1p-32f;                                   \
+      wc_.off = (unsigned)(lane * win + (kref_ - w0_)) * 16u - (unsigned)kFloorMagicBits * 16u;       \
+      s_wc[B_][warp][lane] = wc_;                                                                     \
+      if (warp == 0) {                                                                                \
+        s_ab[B_][lane] = make_float2(__ldg(dAf + i_), __ldg(dBf + i_));                                \
+        s_w0[B_][lane] = w0_;                                                                         \
+        s_row[B_][lane] = i_ * L + l_;                                                                \
+      }                                                                                               \
+    }                                                                                                 \
+  }
+  // raw samples of stage q (tables in buffer b_) into registers
+#define DAS_LOAD_RAW(Q, B_)                                                                          \
+  {                                                                                                  \
+    const int ns_ = min(STAGE, N - ((Q) % spl) * STAGE);                                             \
+    _Pragma("unroll") for (int u = 0; u < PPW; ++u) {                                                \
+      const int j = warp + 4 * u;                                                                    \
+      const int jj = j < ns_ ? j : 0;                                                                \
+      const float2 *yr = y + (size_t)s_row[B_][jj] * T;                                              \
+      const int w0 = s_w0[B_][jj];                                                                   \
+      _Pragma("unroll") for (int i = 0; i < QPP; ++i) {                                              \
+        const int m = lane + 32 * i;                                                                 \
+        const int k = w0 + m;                                                                        \
+        float2 a = make_float2(0.f, 0.f), b = make_float2(0.f, 0.f);                                 \
+        if (j < ns_ && m < win && (unsigned)k <= (unsigned)(T - 2)) {                                \
+          a = __ldg(yr + k);                                                                         \
+          b = __ldg(yr + k + 1);                                                                     \
+        }                                                                                            \
+        raw0[u * QPP + i] = a;                                                                       \
+        raw1[u * QPP + i] = b;                                                                       \
+      }                                                                                              \
+    }                                                                                                \
+  }
+
+  float2 raw0[NPT], raw1[NPT];
+  int buf = 0;
+  if (nq > 0) {
+    DAS_TABLES(0, 0);
+    __syncthreads();
+    DAS_LOAD_RAW(0, 0);
+  }
+  int cur_l = -1;
+  unsigned kout16[ROWS];
+  float fout[ROWS];
+  const char *swb = reinterpret_cast<const char *>(sw);
+  for (int q = 0; q < nq; ++q) {
+    const int l = lb + q / spl;
+    const int ns = min(STAGE, N - (q % spl) * STAGE);
+    __syncthreads();  // everyone is done gathering from sw
+#pragma unroll
+    for (int u = 0; u < PPW; ++u) {
+      const int j = warp + 4 * u;
+#pragma unroll
+      for (int i = 0; i < QPP; ++i) {
+        const int m = lane + 32 * i;
+        if (j < ns && m < win) {
+          const float2 a = raw0[u * QPP + i], b = raw1[u * QPP + i];
+          sw[(size_t)j * win + m] = make_float4(a.x, a.y, b.x - a.x, b.y - a.y);
+        }
+      }
+    }
+    if (q + 1 < nq) DAS_TABLES(q + 1, buf ^ 1);
+    __syncthreads();  // entries of this stage and tables of the next visible
+    if (q + 1 < nq) DAS_LOAD_RAW(q + 1, buf ^ 1);  // in flight during the gathers
+    if (l != cur_l) {
+      // receive delay of this thread's pixels for element l: integer (x16) + fraction
+      cur_l = l;
+      const float2 u = __ldg(us + l);
+      const float2 dx2 = df_sqr(df_sub(xq, u));
+#pragma unroll
+      for (int r = 0; r < ROWS; ++r) {
+        const float2 S = df_add(dx2, z2[r]);
+        const float rh = sqrtf(S.x);
+        const float t = fmaf(-rh, rh, S.x) + S.y;
+        const float corr = (rh > 0.f) ? t / (2.f * rh) : 0.f;
+        const float kf = floorf(rh);
+        kout16[r] = (unsigned)(int)kf * 16u;
+        fout[r] = (rh - kf) + corr;
+      }
+    }
+    float2 sacc[ROWS];
+#pragma unroll
+    for (int r = 0; r < ROWS; ++r) sacc[r] = make_float2(0.f, 0.f);
+#pragma unroll 2
+    for (int j = 0; j < ns; ++j) {
+      const float2 ab = s_ab[buf][j];
+      const WarpChan wc = s_wc[buf][warp][j];
+      const float base = fmaf(ab.x, dl, wc.phi);
+#pragma unroll
+      for (int r = 0; r < ROWS; ++r) {
+        const float s = fmaf(ab.y, (float)(r - ROWS / 2), base) + fout[r];
+        const float t = __fadd_rd(s, kFloorMagic);
+        const float f = s - (t - kFloorMagic);
+        const unsigned addr = wc.off + kout16[r] + ((unsigned)__float_as_int(t) << 4);
+        const float4 e = *reinterpret_cast<const float4 *>(swb + addr);
+        sacc[r].x += fmaf(f, e.z, e.x);
+        sacc[r].y += fmaf(f, e.w, e.y);
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < ROWS; ++r) {
+      acc[r].x += sacc[r].x;
+      acc[r].y += sacc[r].y;
+    }
+    buf ^= 1;
+  }
+#undef DAS_TABLES
+#undef DAS_LOAD_RAW
+  float2 *dst = B + (size_t)sidx * nx * nz;
+#pragma unroll
+  for (int r = 0; r < ROWS; ++r) {
+    const int iz = izb + r;
+    if (ix < nx && iz < nz) {
+      dst[(size_t)iz * nx + ix] = acc[r];
+      if (split == 1 && I != nullptr) I[(size_t)iz * nx + ix] = fmaf(acc[r].x, acc[r].x, acc[r].y * acc[r].y);
+    }
+  }
+}
+
 // Sum element-slice partials in slice order.
 __global__ void k_das_reduce(const float2 *__restrict__ part, int split, int npix,
                              float2 *__restrict__ B, float *__restrict__ I) {
@@ -205,16 +393,54 @@ __global__ void k_das_reduce(const float2 *__restrict__ part, int split, int npi
 
 }  // namespace
 
+namespace {
+template <int STAGE, int NPT>
+cudaError_t launch_staged(const kk_plan &p, const float2 *y, float2 *dst, float *I, cudaStream_t s) {
+  constexpr int MINB = 5;
+  const size_t smem = sizeof(float4) * (size_t)STAGE * p.bf_win;
+  auto k = k_das_gather_staged<STAGE, NPT, MINB>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const dim3 grid(p.tiles_x * p.tiles_z, p.bf_split);
+  k<<<grid, kGatherThreads, smem, s>>>(y, p.N, p.L, p.T, p.t.das_A, p.t.das_B, p.t.das_C, p.t.das_Af,
+                                       p.t.das_Bf, p.t.xs, p.t.zs, p.t.us, p.grid.nx, p.grid.nz, p.tiles_x,
+                                       p.bf_win, p.bf_split, dst, I);
+  return cudaGetLastError();
+}
+}  // namespace
+
+// launch shape of the staged DAS gather for a window: stage 16 / 8 / 4
+// transmits with 2 / 4 / 8 staged entries per lane and channel; 0 when the
+// window is wider than 256 entries (the synchronous kernel takes it)
+int das_staged_stage(int win) {
+  const int q = gather_entries_per_lane(win);
+  if (q == 1 || q == 2) return 16;
+  if (q == 4) return 8;
+  if (q == 8) return 4;
+  return 0;
+}
+
 cudaError_t launch_das_gather(const kk_plan &p, const float2 *y, float2 *B, float *I,
                               float2 *partial, cudaStream_t s) {
-  const size_t smem = sizeof(float4) * (size_t)p.bf_stage * p.bf_win;
-  cudaFuncSetAttribute(k_das_gather, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  const dim3 grid(p.tiles_x * p.tiles_z, p.bf_split);
-  k_das_gather<<<grid, kGatherThreads, smem, s>>>(
-      y, p.N, p.L, p.T, p.t.das_A, p.t.das_B, p.t.das_C, p.t.das_Af, p.t.das_Bf, p.t.xs, p.t.zs,
-      p.t.us, p.grid.nx, p.grid.nz, p.tiles_x, p.bf_win, p.bf_stage, p.bf_split,
-      p.bf_split > 1 ? partial : B, I);
-  cudaError_t e = cudaGetLastError();
+  float2 *dst = p.bf_split > 1 ? partial : B;
+  cudaError_t e;
+  if (p.bf_rows == 4) {
+    const int q = gather_entries_per_lane(p.bf_win);
+    switch (p.bf_stage) {
+      case 16: e = q == 1 ? launch_staged<16, 4>(p, y, dst, I, s) : launch_staged<16, 8>(p, y, dst, I, s); break;
+      case 8: e = launch_staged<8, 8>(p, y, dst, I, s); break;
+      case 4: e = launch_staged<4, 8>(p, y, dst, I, s); break;
+      default: return cudaErrorInvalidValue;
+    }
+  } else {
+    const size_t smem = sizeof(float4) * (size_t)p.bf_stage * p.bf_win;
+    cudaFuncSetAttribute(k_das_gather, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const dim3 grid(p.tiles_x * p.tiles_z, p.bf_split);
+    k_das_gather<<<grid, kGatherThreads, smem, s>>>(
+        y, p.N, p.L, p.T, p.t.das_A, p.t.das_B, p.t.das_C, p.t.das_Af, p.t.das_Bf, p.t.xs, p.t.zs,
+        p.t.us, p.grid.nx, p.grid.nz, p.tiles_x, p.bf_win, p.bf_stage, p.bf_split, dst, I);
+    e = cudaGetLastError();
+  }
   if (e != cudaSuccess || p.bf_split == 1) return e;
   const int npix = p.grid.nx * p.grid.nz;
   k_das_reduce<<<(npix + 255) / 256, 256, 0, s>>>(partial, p.bf_split, npix, B, I);

@@ -99,6 +99,8 @@ namespace kk {
 // staged entries a lane of the gather kernels holds in registers
 constexpr int kMaxStagedEntries = 8;
 int gather_entries_per_lane(int win);
+// stage (transmits) of the staged DAS gather for a window, 0 = window too wide
+int das_staged_stage(int win);
 bool gather_config_supported(int rows, int stage, int win);
 
 // Arguments of one frame's KK gather (also the batched form's per-frame

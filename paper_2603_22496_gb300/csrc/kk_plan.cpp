@@ -353,7 +353,11 @@ kk_status make_das(kk_plan &p, const kk_plan_desc *d) {
   const double k_s = d->fs / d->c;
   std::vector<long long> A(p.N), Bv(p.N), C(p.N);
   std::vector<float> Af(p.N), Bf(p.N);
-  double span_in = 0;
+  // staged kernel: 32 x 16 tiles, window from the transmit-delay span plus the
+  // receive-delay span, which the tile diameter bounds (|grad R| <= 1);
+  // windows over 256 entries go to the synchronous 32 x 32 kernel
+  const double diam16 = std::hypot(g.dx * (kTileX - 1), g.dz * 15.0);
+  double span_in16 = 0, span_in32 = 0;
   for (int i = 0; i < p.N; ++i) {
     const double th = d->tx_angles[i];
     const double a = k_s * g.dx * std::sin(th), b = k_s * g.dz * std::cos(th);
@@ -363,24 +367,35 @@ kk_status make_das(kk_plan &p, const kk_plan_desc *d) {
     C[i] = to_fixed32(c0);
     Af[i] = (float)a;
     Bf[i] = (float)b;
-    span_in = std::max(span_in, std::fabs(a) * (kTileX - 1) + b * (kTileZ - 1));
+    span_in16 = std::max(span_in16, std::fabs(a) * (kTileX - 1) + b * 15.0);
+    span_in32 = std::max(span_in32, std::fabs(a) * (kTileX - 1) + b * (kTileZ - 1));
   }
+  const int win16 = (int)std::ceil(span_in16 + k_s * diam16) + 6;
+  const int stage16 = das_staged_stage(win16);
+  const int TZ = stage16 > 0 ? 16 : kTileZ;
   p.tiles_x = (g.nx + kTileX - 1) / kTileX;
-  p.tiles_z = (g.nz + kTileZ - 1) / kTileZ;
+  p.tiles_z = (g.nz + TZ - 1) / TZ;
   auto split_df = [](double v) {
     const float hi = (float)v;
     return make_float2(hi, (float)(v - (double)hi));
   };
-  std::vector<float2> xs(p.tiles_x * kTileX), zs(p.tiles_z * kTileZ), us(p.L);
+  std::vector<float2> xs(p.tiles_x * kTileX), zs(p.tiles_z * TZ), us(p.L);
   for (size_t k = 0; k < xs.size(); ++k) xs[k] = split_df(k_s * (g.x0 + g.dx * (double)k));
   for (size_t k = 0; k < zs.size(); ++k) zs[k] = split_df(k_s * (g.z0 + g.dz * (double)k));
   for (int l = 0; l < p.L; ++l) us[l] = split_df(k_s * d->elem_x[l]);
   const size_t off_A = blob.add(A), off_B = blob.add(Bv), off_C = blob.add(C);
   const size_t off_Af = blob.add(Af), off_Bf = blob.add(Bf);
   const size_t off_xs = blob.add(xs), off_zs = blob.add(zs), off_us = blob.add(us);
-  const double span_out = k_s * (g.dx * (kTileX - 1) + g.dz * (kTileZ - 1));
-  p.bf_win = (int)std::ceil(span_in + span_out) + 6;
-  p.bf_stage = choose_stage(p.bf_win);
+  if (stage16 > 0) {
+    p.bf_rows = 4;
+    p.bf_win = win16;
+    p.bf_stage = stage16;
+  } else {
+    const double span_out = k_s * (g.dx * (kTileX - 1) + g.dz * (kTileZ - 1));
+    p.bf_rows = 8;
+    p.bf_win = (int)std::ceil(span_in32 + span_out) + 6;
+    p.bf_stage = choose_stage(p.bf_win);
+  }
   // split the element loop so the grid covers the GPU (~4 CTAs per SM)
   int sms = 148;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p.device);
