@@ -158,8 +158,9 @@ kk_status kk_plan_get_info(const kk_plan *p, kk_plan_info *info);
  * 32 x (4 rows) pixels; stage in {4, 8, 16}: pairs staged per batch.  Results
  * do not depend on it beyond FP32 rounding order.  Returns
  * KK_ERR_UNSUPPORTED when the grid's staged window is too long for the shape
- * (the plan keeps its previous shape).  Changes workspace_bytes: call before
- * allocating the workspace, never while work is in flight.
+ * (the plan keeps its previous shape).  workspace_bytes covers every shape,
+ * so a workspace allocated before the call stays valid; never call it while
+ * work is in flight.
  */
 kk_status kk_plan_set_gather(kk_plan *p, int32_t rows, int32_t stage);
 

@@ -11,9 +11,9 @@
 //    offset, ROWS z rows per thread;
 //  * pairs are processed in stages of STAGE pairs: for each pair the CTA
 //    stages the window of y_p its tile can touch into shared memory as
-//    16-byte entries E[k] = (y[k], y[k+1]), so one load gives a linear
-//    interpolation; E[k] = 0 outside k in [0, T-2], which implements the
-//    record-end rule exactly;
+//    16-byte entries E[k] = (y[k], y[k+1] - y[k]), so one load and two FMAs
+//    give a linear interpolation y[k] + f (y[k+1] - y[k]); E[k] = 0 outside
+//    k in [0, T-2], which implements the record-end rule exactly;
 //  * staging goes through registers: lane m of a warp reads y[k] and y[k+1]
 //    and writes E[k], so a warp's 16-byte stores are contiguous (no bank
 //    conflicts); the loads of stage s+1 are issued before the gathers of
@@ -212,7 +212,7 @@ __device__ __forceinline__ void gather_tile(const GatherArgs &a, int tile, int s
   while (cur_g < J) {
     cp_async_wait_all();  // inputs of the next stage have landed
     __syncthreads();      // everyone is done gathering from sw
-    // entries E[k] = (y[k], y[k+1]) of this stage (zero outside [0, T-2])
+    // entries E[k] = (y[k], y[k+1] - y[k]) of this stage (zero outside [0, T-2])
 #pragma unroll
     for (int u = 0; u < PPW; ++u) {
       const int j = warp + 4 * u;
@@ -221,7 +221,7 @@ __device__ __forceinline__ void gather_tile(const GatherArgs &a, int tile, int s
         const int m = lane + 32 * i;
         if (j < cur_n && m < win) {
           const float2 a = raw0[u * QPP + i], b = raw1[u * QPP + i];
-          sw[(size_t)j * win + m] = make_float4(a.x, a.y, b.x, b.y);
+          sw[(size_t)j * win + m] = make_float4(a.x, a.y, b.x - a.x, b.y - a.y);
         }
       }
     }
@@ -266,13 +266,10 @@ __device__ __forceinline__ void gather_tile(const GatherArgs &a, int tile, int s
         const float s = fmaf(wp.b, (float)(r - ROWS / 2), base);
         const float t = __fadd_rd(s, kFloorMagic);
         const float f = s - (t - kFloorMagic);
-        const float gg = 1.0f - f;
         const unsigned addr = wp.off + ((unsigned)__float_as_int(t) << 4);
         const float4 e = *reinterpret_cast<const float4 *>(swb + addr);
-        sacc[r].x = fmaf(gg, e.x, sacc[r].x);
-        sacc[r].x = fmaf(f, e.z, sacc[r].x);
-        sacc[r].y = fmaf(gg, e.y, sacc[r].y);
-        sacc[r].y = fmaf(f, e.w, sacc[r].y);
+        sacc[r].x += fmaf(f, e.z, e.x);
+        sacc[r].y += fmaf(f, e.w, e.y);
       }
     }
 #pragma unroll
@@ -371,8 +368,8 @@ cudaError_t launch_cfg(const kk_plan &p, const float2 *rf_theta, float2 *dst, fl
                        cudaStream_t s) {
   // registers held to 64 for ROWS <= 4 (8 CTAs of 128 threads per SM) and
   // to 102 for ROWS = 8 (5 CTAs)
-  auto k = (p.J > 1) ? k_kk_gather<ROWS, STAGE, NPT, (ROWS <= 4 ? 8 : 5), true>
-                     : k_kk_gather<ROWS, STAGE, NPT, (ROWS <= 4 ? 8 : 5), false>;
+  auto k = (p.J > 1) ? k_kk_gather<ROWS, STAGE, NPT, (ROWS <= 4 ? 7 : 5), true>
+                     : k_kk_gather<ROWS, STAGE, NPT, (ROWS <= 4 ? 7 : 5), false>;
   const size_t smem = sizeof(float4) * (size_t)STAGE * p.bf_win;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -431,7 +428,7 @@ GatherArgs gather_args(const kk_plan &p, const float2 *rf_theta, float2 *dst, fl
 template <int ROWS, int STAGE, int NPT>
 static cudaError_t batch_cfg(const GatherArgs *frames, const int2 *items, int n_items, int *counter,
                              int max_win, int grid, cudaStream_t s) {
-  auto k = k_kk_gather_batch<ROWS, STAGE, NPT, (ROWS <= 4 ? 8 : 5)>;
+  auto k = k_kk_gather_batch<ROWS, STAGE, NPT, (ROWS <= 4 ? 7 : 5)>;
   const size_t smem = sizeof(float4) * (size_t)STAGE * max_win;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;

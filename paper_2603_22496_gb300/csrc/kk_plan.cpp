@@ -148,8 +148,21 @@ kk_status upload(kk_plan &p, const Blob &blob) {
   return KK_OK;
 }
 
-// Window length, tile grid, pair-range split and workspace of the KK gather
-// for a (rows, stage) configuration.
+// Pair-range split of the KK gather for a shape: the grid covers the GPU
+// (~4 CTAs per SM), keeping >= 2 stages of work per slice.
+int gather_split(const kk_plan &p, int rows, int stage) {
+  const int tz = 4 * rows;
+  int sms = 148;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p.device);
+  const int tiles = ((p.grid.nx + kTileX - 1) / kTileX) * ((p.grid.nz + tz - 1) / tz);
+  const int split = (4 * sms + tiles - 1) / tiles;
+  const int max_by_pairs = std::max(1, (p.P / p.J) / (2 * stage));
+  return std::max(1, std::min(split, max_by_pairs));
+}
+
+// Window length, tile grid and pair-range split of the KK gather for a
+// (rows, stage) configuration.  The workspace reserves partial images for the
+// largest split of any shape (make_kk), so it does not depend on the shape.
 kk_status configure_kk_gather(kk_plan &p, int rows, int stage) {
   const kk_grid &g = p.grid;
   const int tz = 4 * rows;
@@ -168,17 +181,7 @@ kk_status configure_kk_gather(kk_plan &p, int rows, int stage) {
   p.bf_win = win;
   p.tiles_x = (g.nx + kTileX - 1) / kTileX;
   p.tiles_z = (g.nz + tz - 1) / tz;
-  // split the pair list so the grid covers the GPU (~4 CTAs per SM), keeping
-  // >= 2 stages of work per slice
-  int sms = 148;
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p.device);
-  const int tiles = p.tiles_x * p.tiles_z;
-  const int split = (4 * sms + tiles - 1) / tiles;
-  const int max_by_pairs = std::max(1, (p.P / p.J) / (2 * stage));
-  p.bf_split = std::max(1, std::min(split, max_by_pairs));
-  size_t off = p.ws_part;
-  if (p.bf_split > 1) off = align_up(off + sizeof(float2) * (size_t)p.bf_split * p.J * g.nx * g.nz);
-  p.ws_total = off;
+  p.bf_split = gather_split(p, rows, stage);
   return KK_OK;
 }
 
@@ -314,6 +317,11 @@ kk_status make_kk(kk_plan &p, const kk_plan_desc *d) {
                         (const int[2]){2, 8}, (const int[2]){2, 4}})
     if ((cst = configure_kk_gather(p, rs[0], rs[1])) == KK_OK) break;
   if (cst != KK_OK) return cst;
+  // partial images for the largest split any shape can take
+  int max_split = 1;
+  for (int rows : {2, 4, 8})
+    for (int stage : {4, 8, 16}) max_split = std::max(max_split, gather_split(p, rows, stage));
+  p.ws_total = max_split > 1 ? align_up(off + sizeof(float2) * (size_t)max_split * p.J * p.grid.nx * p.grid.nz) : off;
 
   kk_status st = upload(p, blob);
   if (st != KK_OK) return st;

@@ -287,3 +287,32 @@ def test_gather_configuration_rejects_bad_shapes():
     with pytest.raises(kb.KKError):      # small grid's window too long for 32 x 32 tiles x 16 pairs
         plan.set_gather(8, 16)
     plan.set_gather(4, 8)
+
+
+def test_workspace_allocated_before_a_shape_change_stays_valid():
+    """workspace_bytes covers every launch shape: a workspace allocated at the
+    default shape serves every other shape (the grid is chosen so that the
+    pair-slice split grows from 2 to 5 across shapes), with nothing written
+    past its end (canary) and the same image from every shape."""
+    import torch
+    w = kksynth.workload_small()
+    grid = (512, 256, -19e-3, 0.075e-3, 5e-3, 0.075e-3)
+    ops, (rx, pairs, grp, J) = kc.scheme_both("confocal", w.tx_angles, 11)
+    plan = kc.kk_plan_for(w, rx, pairs, grp, J, kb.KK_COMPOUND_COHERENT, grid)
+    nbytes = plan.info.workspace_bytes
+    canary = 1 << 20
+    raw = torch.full((nbytes + canary,), 0x5A, dtype=torch.uint8, device="cuda")
+    ws = raw[:nbytes]
+    rt, I = plan.empty_rf_theta(), plan.empty_intensity()
+    plan.decompose(kc.to_dev(w.rf), rt, ws)
+    images = []
+    for rows, stage in [(4, 16), (8, 4), (8, 8), (2, 4), (4, 4)]:
+        plan.set_gather(rows, stage)
+        assert plan.info.workspace_bytes == nbytes
+        B = plan.empty_image()
+        plan.beamform(rt, B, I, ws)
+        torch.cuda.synchronize()
+        images.append(kc.cplx(B))
+    assert bool((raw[nbytes:] == 0x5A).all())
+    for img in images[1:]:
+        assert kc.rel_l2(img, images[0]) <= 1e-6
