@@ -396,7 +396,7 @@ __global__ void k_das_reduce(const float2 *__restrict__ part, int split, int npi
 namespace {
 template <int STAGE, int NPT>
 cudaError_t launch_staged(const kk_plan &p, const float2 *y, float2 *dst, float *I, cudaStream_t s) {
-  constexpr int MINB = 5;
+  constexpr int MINB = 7;
   const size_t smem = sizeof(float4) * (size_t)STAGE * p.bf_win;
   auto k = k_das_gather_staged<STAGE, NPT, MINB>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -257,7 +257,7 @@ __device__ __forceinline__ void gather_tile(const GatherArgs &a, int tile, int s
 #pragma unroll
     for (int r = 0; r < ROWS; ++r) sacc[r] = make_float2(0.f, 0.f);
     const WarpPair *tab = s_wp[buf][warp];
-#pragma unroll 2
+#pragma unroll 1
     for (int j = 0; j < cur_n; ++j) {
       const WarpPair wp = tab[j];
       const float base = fmaf(wp.a, dl, wp.phi);
