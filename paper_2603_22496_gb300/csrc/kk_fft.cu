@@ -100,9 +100,10 @@ template <> __device__ __forceinline__ void dft<4>(float2 *v) {
   v[3] = make_float2(t1.x - t3.y, t1.y + t3.x);  // t1 + i t3
 }
 
-// One Stockham pass over NTR transforms of F points stored with row stride FS.
+// One Stockham pass over NTR transforms of F points stored with row stride FS;
+// tw is the twiddle table staged in shared memory.
 template <int R, int NS, int F, int FS, int NTR, int NT>
-__device__ __forceinline__ void stockham_pass(float2 *buf, const float2 *__restrict__ tw, int tid) {
+__device__ __forceinline__ void stockham_pass(float2 *buf, const float2 *tw, int tid) {
   constexpr int NBF = NTR * (F / R);
   constexpr int NB = (NBF + NT - 1) / NT;
   float2 v[NB][R];
@@ -118,7 +119,7 @@ __device__ __forceinline__ void stockham_pass(float2 *buf, const float2 *__restr
       for (int r = 0; r < R; ++r) v[b][r] = src[r * (F / R)];
       if (NS > 1) {
 #pragma unroll
-        for (int r = 1; r < R; ++r) v[b][r] = cmul(v[b][r], __ldg(tw + k * (R - 1) + (r - 1)));
+        for (int r = 1; r < R; ++r) v[b][r] = cmul(v[b][r], tw[k * (R - 1) + (r - 1)]);
       }
       dft<R>(v[b]);
     }
@@ -140,7 +141,7 @@ __device__ __forceinline__ void stockham_pass(float2 *buf, const float2 *__restr
 }
 
 template <int F, int FS, int NTR, int NT, int I>
-__device__ __forceinline__ void run_passes(float2 *buf, const float2 *__restrict__ tw, int tid) {
+__device__ __forceinline__ void run_passes(float2 *buf, const float2 *tw, int tid) {
   if constexpr (I < fft_npass(F)) {
     constexpr int R = fft_radix(F, I);
     constexpr int NS = fft_ns(F, I);
@@ -168,7 +169,20 @@ __device__ __forceinline__ void store_x(__half2 *X, size_t idx, float2 v) {
   X[idx] = __floats2half2_rn(v.x, v.y);
 }
 
-template <int F, int C, int NT, typename TIn, typename TOut>
+// 16-byte vector of a real record -> VE / 2 complex points
+__device__ __forceinline__ void unpack16(const uint4 &u, const int16_t *, float2 *z) {
+  const short2 *h = reinterpret_cast<const short2 *>(&u);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) z[q] = make_float2((float)h[q].x, (float)h[q].y);
+}
+__device__ __forceinline__ void unpack16(const uint4 &u, const float *, float2 *z) {
+  const float *f = reinterpret_cast<const float *>(&u);
+  z[0] = make_float2(f[0], f[1]);
+  z[1] = make_float2(f[2], f[3]);
+}
+
+// VEC: the records are 16-byte aligned (read with 16-byte vector loads)
+template <int F, int C, int NT, typename TIn, typename TOut, bool VEC>
 __global__ void __launch_bounds__(NT) k_spectrum(const TIn *__restrict__ rf,
                                                  const int32_t *__restrict__ tx_rows, int L,
                                                  int n_ch, const float2 *__restrict__ tw,
@@ -177,21 +191,49 @@ __global__ void __launch_bounds__(NT) k_spectrum(const TIn *__restrict__ rf,
   constexpr int FS = F + 1;
   constexpr int T = 2 * F;
   extern __shared__ float2 sm[];
+  __shared__ long long s_row[C];  // first sample of each record, -1 past the last channel
   const int tid = threadIdx.x;
   const int c0 = blockIdx.x * C;
-  for (int idx = tid; idx < C * F; idx += NT) {
-    const int cc = idx / F, n = idx - cc * F;
-    const int c = c0 + cc;
-    float2 z = make_float2(0.f, 0.f);
+  float2 *s_tw = sm + C * FS;  // twiddles of every pass
+  for (int i = tid; i < fft_twoff(F, fft_npass(F)); i += NT) s_tw[i] = __ldg(tw + i);
+  if (tid < C) {
+    const int c = c0 + tid;
+    long long r = -1;
     if (c < n_ch) {
       const int iu = c / L, l = c - iu * L;
-      const size_t row = (size_t)__ldg(tx_rows + iu) * L + l;
-      z = load_pair(rf + row * T + 2 * n);
+      r = ((long long)__ldg(tx_rows + iu) * L + l) * T;
     }
-    sm[cc * FS + n] = z;
+    s_row[tid] = r;
   }
   __syncthreads();
-  run_passes<F, FS, C, NT, 0>(sm, tw, tid);
+  if constexpr (VEC) {
+    constexpr int VE = 16 / (int)sizeof(TIn);  // samples per vector
+    constexpr int NV = T / VE;                 // vectors per record
+#pragma unroll 4
+    for (int idx = tid; idx < C * NV; idx += NT) {
+      const int cc = idx / NV, v = idx - cc * NV;
+      const long long r = s_row[cc];
+      float2 z[VE / 2];
+      if (r >= 0) {
+        const uint4 u = __ldg(reinterpret_cast<const uint4 *>(rf + r) + v);
+        unpack16(u, rf, z);
+      } else {
+#pragma unroll
+        for (int q = 0; q < VE / 2; ++q) z[q] = make_float2(0.f, 0.f);
+      }
+#pragma unroll
+      for (int q = 0; q < VE / 2; ++q) sm[cc * FS + v * (VE / 2) + q] = z[q];
+    }
+  } else {
+#pragma unroll 4
+    for (int idx = tid; idx < C * F; idx += NT) {
+      const int cc = idx / F, n = idx - cc * F;
+      const long long r = s_row[cc];
+      sm[cc * FS + n] = r >= 0 ? load_pair(rf + r + 2 * n) : make_float2(0.f, 0.f);
+    }
+  }
+  __syncthreads();
+  run_passes<F, FS, C, NT, 0>(sm, s_tw, tid);
   for (int idx = tid; idx < C * F; idx += NT) {
     const int k = idx / C, cc = idx - k * C;
     const int c = c0 + cc;
@@ -222,14 +264,20 @@ __global__ void __launch_bounds__(NT) k_inverse(const float2 *__restrict__ Y, in
   extern __shared__ float2 sm[];
   const int tid = threadIdx.x;
   const int r0 = blockIdx.x * C;
+  __shared__ int s_q[C];  // column of Y for each row, -1 past the last row
+  float2 *s_tw = sm + 2 * C * FS;  // twiddles of every pass
+  for (int i = tid; i < fft_twoff(F, fft_npass(F)); i += NT) s_tw[i] = __ldg(tw + i);
+  if (tid < C) {
+    const int row = r0 + tid;
+    s_q[tid] = row < nrow ? (col_of_row ? __ldg(col_of_row + row) : row) : -1;
+  }
+  __syncthreads();
+#pragma unroll 4
   for (int idx = tid; idx < C * F; idx += NT) {
     const int k = idx / C, rr = idx - k * C;
-    const int row = r0 + rr;
+    const int q = s_q[rr];
     float2 y = make_float2(0.f, 0.f);
-    if (row < nrow) {
-      const int q = col_of_row ? __ldg(col_of_row + row) : row;
-      y = Y[(size_t)k * ncol + q];
-    }
+    if (q >= 0) y = __ldg(Y + (size_t)k * ncol + q);
     // inverse via conj(FFT(conj(.))): even samples from conj(Y),
     // odd samples from conj(Y e^{+2 pi i k/T}) = conj(Y) e^{-2 pi i k/T}
     const float2 a = make_float2(y.x, -y.y);
@@ -237,7 +285,7 @@ __global__ void __launch_bounds__(NT) k_inverse(const float2 *__restrict__ Y, in
     sm[(2 * rr + 1) * FS + k] = cmul(a, __ldg(rw + k));
   }
   __syncthreads();
-  run_passes<F, FS, 2 * C, NT, 0>(sm, tw, tid);
+  run_passes<F, FS, 2 * C, NT, 0>(sm, s_tw, tid);
   for (int idx = tid; idx < C * F; idx += NT) {
     const int rr = idx / F, m = idx - rr * F;
     const int row = r0 + rr;
@@ -261,9 +309,10 @@ template <int F, typename TIn, typename TOut>
 static cudaError_t spectrum_ft(const kk_plan &p, const void *rf, void *X, int n_ch,
                                const int32_t *rows, cudaStream_t s) {
   using Cfg = FftCfg<F>;
-  const size_t smem = sizeof(float2) * Cfg::CS * (F + 1);
+  const size_t smem = sizeof(float2) * (Cfg::CS * (F + 1) + fft_twoff(F, fft_npass(F)));
   const dim3 grid((n_ch + Cfg::CS - 1) / Cfg::CS);
-  auto k = k_spectrum<F, Cfg::CS, Cfg::NT, TIn, TOut>;
+  const bool vec = ((uintptr_t)rf % 16) == 0;
+  auto k = vec ? k_spectrum<F, Cfg::CS, Cfg::NT, TIn, TOut, true> : k_spectrum<F, Cfg::CS, Cfg::NT, TIn, TOut, false>;
   cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   k<<<grid, Cfg::NT, smem, s>>>((const TIn *)rf, rows, p.L, n_ch, p.t.fft_tw, p.t.rfft_w, (TOut *)X,
                                 p.x_scale);
@@ -293,7 +342,7 @@ template <int F>
 static cudaError_t inverse_f(const kk_plan &p, const float2 *Y, int ncol, const int32_t *col,
                              int nrow, float2 *out, cudaStream_t s) {
   using Cfg = FftCfg<F>;
-  const size_t smem = sizeof(float2) * 2 * Cfg::CI * (F + 1);
+  const size_t smem = sizeof(float2) * (2 * Cfg::CI * (F + 1) + fft_twoff(F, fft_npass(F)));
   auto k = k_inverse<F, Cfg::CI, Cfg::NT>;
   cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   const dim3 grid((nrow + Cfg::CI - 1) / Cfg::CI);

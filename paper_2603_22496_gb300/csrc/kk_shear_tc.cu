@@ -150,6 +150,7 @@ __global__ void __launch_bounds__(kTcThreads, 2)
       // row holds 4 consecutive complex X
       const uint32_t *Xk = reinterpret_cast<const uint32_t *>(Xv) + (size_t)k * Nu * L;
       const bool vec = (L & 3) == 0;
+#pragma unroll 4
       for (int e = tid; e < NP * (kKC / 8); e += kTcThreads) {
         const int i = e / (kKC / 8), c = e - i * (kKC / 8);
         const int l0 = c * 4;
@@ -174,6 +175,7 @@ __global__ void __launch_bounds__(kTcThreads, 2)
       constexpr int EPC = FM::EPC;                       // elements per core row
       constexpr int LPR = EPC / 2;                       // array elements per core row
       const float wscale = (KIND == 2) ? 64.f : 1.f;
+#pragma unroll 2
       for (int e = tid; e < (kRowsM / 2) * (kKC / EPC); e += kTcThreads) {
         const int ol = e / (kKC / EPC), c = e - ol * (kKC / EPC);
         const int o = m0 + ol;
