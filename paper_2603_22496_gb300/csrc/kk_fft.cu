@@ -7,7 +7,8 @@
 //  * k_spectrum: one T-sample real record per channel -> X[k] for k < F = T/2,
 //    with weights h_0 = 1, h_k = 2 (the Nyquist bin is dropped).  The record
 //    is packed as F complex points z[n] = x[2n] + i x[2n+1], transformed with
-//    an F-point Stockham FFT in shared memory, and split into the T-point
+//    an F-point Stockham FFT in shared memory (radix-16 passes computed in
+//    registers, then radix 4 / 2 / 3), and split into the T-point
 //    spectrum by X[k] = E[k] + e^{-2 pi i k / T} O[k].
 //    Output layout X[k][c] (bin-major) feeds the per-bin contraction.
 //  * k_inverse: y[t] = (1/T) sum_{k<F} Y[k] e^{+2 pi i k t / T} for t < T,
@@ -26,8 +27,10 @@
 namespace kk {
 
 // ---- radix plan (shared by host and device) --------------------------------
+// passes of radix 16 first (computed in registers as 4 x 4), then 4, 2, 3
 __host__ __device__ constexpr int fft_npass(int F) {
   int n = 0;
+  while (F % 16 == 0) { F /= 16; ++n; }
   while (F % 4 == 0) { F /= 4; ++n; }
   while (F % 2 == 0) { F /= 2; ++n; }
   while (F % 3 == 0) { F /= 3; ++n; }
@@ -35,11 +38,17 @@ __host__ __device__ constexpr int fft_npass(int F) {
 }
 __host__ __device__ constexpr int fft_radix(int F, int i) {
   int n = 0;
+  while (F % 16 == 0) { if (n == i) return 16; F /= 16; ++n; }
   while (F % 4 == 0) { if (n == i) return 4; F /= 4; ++n; }
   while (F % 2 == 0) { if (n == i) return 2; F /= 2; ++n; }
   while (F % 3 == 0) { if (n == i) return 3; F /= 3; ++n; }
   return 1;
 }
+// Shared-memory position of point e of a transform: one padding slot per 32
+// points, so that the radix-16 pass's stride-16 writes hit distinct banks.
+__host__ __device__ constexpr int fft_pad(int e) { return e + (e >> 5); }
+// row stride (complex points) of one transform in shared memory
+__host__ __device__ constexpr int fft_row(int F) { return F + F / 32 + 1; }
 __host__ __device__ constexpr int fft_ns(int F, int i) {
   int ns = 1;
   for (int k = 0; k < i; ++k) ns *= fft_radix(F, k);
@@ -100,6 +109,39 @@ template <> __device__ __forceinline__ void dft<4>(float2 *v) {
   v[3] = make_float2(t1.x - t3.y, t1.y + t3.x);  // t1 + i t3
 }
 
+// 16-point DFT as 4 x 4: n = 4 n1 + n2, k = k1 + 4 k2; DFT-4 over n1, twiddle
+// exp(-2 pi i n2 k1 / 16), DFT-4 over n2.
+template <> __device__ __forceinline__ void dft<16>(float2 *v) {
+  constexpr float C1 = 0.923879532511286756128f;  // cos(pi/8)
+  constexpr float S1 = 0.382683432365089771728f;  // sin(pi/8)
+  constexpr float H = 0.707106781186547524401f;   // sqrt(1/2)
+  float2 y[4][4];
+#pragma unroll
+  for (int n2 = 0; n2 < 4; ++n2) {
+    float2 a[4] = {v[n2], v[4 + n2], v[8 + n2], v[12 + n2]};
+    dft<4>(a);
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) y[n2][k1] = a[k1];
+  }
+  // exp(-2 pi i m / 16) for m = n2 k1 in {1, 2, 3, 4, 6, 9}
+  y[1][1] = cmul(y[1][1], make_float2(C1, -S1));
+  y[1][2] = cmul(y[1][2], make_float2(H, -H));
+  y[1][3] = cmul(y[1][3], make_float2(S1, -C1));
+  y[2][1] = cmul(y[2][1], make_float2(H, -H));
+  y[2][2] = make_float2(y[2][2].y, -y[2][2].x);  // times -i
+  y[2][3] = cmul(y[2][3], make_float2(-H, -H));
+  y[3][1] = cmul(y[3][1], make_float2(S1, -C1));
+  y[3][2] = cmul(y[3][2], make_float2(-H, -H));
+  y[3][3] = cmul(y[3][3], make_float2(-C1, S1));
+#pragma unroll
+  for (int k1 = 0; k1 < 4; ++k1) {
+    float2 b[4] = {y[0][k1], y[1][k1], y[2][k1], y[3][k1]};
+    dft<4>(b);
+#pragma unroll
+    for (int k2 = 0; k2 < 4; ++k2) v[k1 + 4 * k2] = b[k2];
+  }
+}
+
 // One Stockham pass over NTR transforms of F points stored with row stride FS;
 // tw is the twiddle table staged in shared memory.
 template <int R, int NS, int F, int FS, int NTR, int NT>
@@ -114,9 +156,9 @@ __device__ __forceinline__ void stockham_pass(float2 *buf, const float2 *tw, int
       const int tr = j / (F / R);
       const int jj = j - tr * (F / R);
       const int k = jj % NS;
-      const float2 *src = buf + tr * FS + jj;
+      const float2 *src = buf + tr * FS;
 #pragma unroll
-      for (int r = 0; r < R; ++r) v[b][r] = src[r * (F / R)];
+      for (int r = 0; r < R; ++r) v[b][r] = src[fft_pad(jj + r * (F / R))];
       if (NS > 1) {
 #pragma unroll
         for (int r = 1; r < R; ++r) v[b][r] = cmul(v[b][r], tw[k * (R - 1) + (r - 1)]);
@@ -132,9 +174,10 @@ __device__ __forceinline__ void stockham_pass(float2 *buf, const float2 *tw, int
       const int tr = j / (F / R);
       const int jj = j - tr * (F / R);
       const int k = jj % NS;
-      float2 *dst = buf + tr * FS + (jj - k) * R + k;
+      float2 *dst = buf + tr * FS;
+      const int d0 = (jj - k) * R + k;
 #pragma unroll
-      for (int r = 0; r < R; ++r) dst[r * NS] = v[b][r];
+      for (int r = 0; r < R; ++r) dst[fft_pad(d0 + r * NS)] = v[b][r];
     }
   }
   __syncthreads();
@@ -188,7 +231,7 @@ __global__ void __launch_bounds__(NT) k_spectrum(const TIn *__restrict__ rf,
                                                  int n_ch, const float2 *__restrict__ tw,
                                                  const float2 *__restrict__ rw,
                                                  TOut *__restrict__ X, float xscale) {
-  constexpr int FS = F + 1;
+  constexpr int FS = fft_row(F);
   constexpr int T = 2 * F;
   extern __shared__ float2 sm[];
   __shared__ long long s_row[C];  // first sample of each record, -1 past the last channel
@@ -222,14 +265,14 @@ __global__ void __launch_bounds__(NT) k_spectrum(const TIn *__restrict__ rf,
         for (int q = 0; q < VE / 2; ++q) z[q] = make_float2(0.f, 0.f);
       }
 #pragma unroll
-      for (int q = 0; q < VE / 2; ++q) sm[cc * FS + v * (VE / 2) + q] = z[q];
+      for (int q = 0; q < VE / 2; ++q) sm[cc * FS + fft_pad(v * (VE / 2) + q)] = z[q];
     }
   } else {
 #pragma unroll 4
     for (int idx = tid; idx < C * F; idx += NT) {
       const int cc = idx / F, n = idx - cc * F;
       const long long r = s_row[cc];
-      sm[cc * FS + n] = r >= 0 ? load_pair(rf + r + 2 * n) : make_float2(0.f, 0.f);
+      sm[cc * FS + fft_pad(n)] = r >= 0 ? load_pair(rf + r + 2 * n) : make_float2(0.f, 0.f);
     }
   }
   __syncthreads();
@@ -238,8 +281,8 @@ __global__ void __launch_bounds__(NT) k_spectrum(const TIn *__restrict__ rf,
     const int k = idx / C, cc = idx - k * C;
     const int c = c0 + cc;
     if (c >= n_ch) continue;
-    const float2 zk = sm[cc * FS + k];
-    const float2 zm = sm[cc * FS + (k == 0 ? 0 : F - k)];
+    const float2 zk = sm[cc * FS + fft_pad(k)];
+    const float2 zm = sm[cc * FS + fft_pad(k == 0 ? 0 : F - k)];
     // E = (Z[k] + conj Z[F-k]) / 2,  O = (Z[k] - conj Z[F-k]) / (2i)
     const float2 e = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
     const float2 o = make_float2(0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
@@ -259,7 +302,7 @@ __global__ void __launch_bounds__(NT) k_inverse(const float2 *__restrict__ Y, in
                                                 const float2 *__restrict__ tw,
                                                 const float2 *__restrict__ rw,
                                                 float2 *__restrict__ out, float scale) {
-  constexpr int FS = F + 1;
+  constexpr int FS = fft_row(F);
   constexpr int T = 2 * F;
   extern __shared__ float2 sm[];
   const int tid = threadIdx.x;
@@ -281,8 +324,8 @@ __global__ void __launch_bounds__(NT) k_inverse(const float2 *__restrict__ Y, in
     // inverse via conj(FFT(conj(.))): even samples from conj(Y),
     // odd samples from conj(Y e^{+2 pi i k/T}) = conj(Y) e^{-2 pi i k/T}
     const float2 a = make_float2(y.x, -y.y);
-    sm[(2 * rr) * FS + k] = a;
-    sm[(2 * rr + 1) * FS + k] = cmul(a, __ldg(rw + k));
+    sm[(2 * rr) * FS + fft_pad(k)] = a;
+    sm[(2 * rr + 1) * FS + fft_pad(k)] = cmul(a, __ldg(rw + k));
   }
   __syncthreads();
   run_passes<F, FS, 2 * C, NT, 0>(sm, s_tw, tid);
@@ -290,8 +333,8 @@ __global__ void __launch_bounds__(NT) k_inverse(const float2 *__restrict__ Y, in
     const int rr = idx / F, m = idx - rr * F;
     const int row = r0 + rr;
     if (row >= nrow) continue;
-    const float2 ev = sm[(2 * rr) * FS + m];
-    const float2 od = sm[(2 * rr + 1) * FS + m];
+    const float2 ev = sm[(2 * rr) * FS + fft_pad(m)];
+    const float2 od = sm[(2 * rr + 1) * FS + fft_pad(m)];
     const float4 o = make_float4(ev.x * scale, -ev.y * scale, od.x * scale, -od.y * scale);
     *reinterpret_cast<float4 *>(out + (size_t)row * T + 2 * m) = o;
   }
@@ -309,7 +352,7 @@ template <int F, typename TIn, typename TOut>
 static cudaError_t spectrum_ft(const kk_plan &p, const void *rf, void *X, int n_ch,
                                const int32_t *rows, cudaStream_t s) {
   using Cfg = FftCfg<F>;
-  const size_t smem = sizeof(float2) * (Cfg::CS * (F + 1) + fft_twoff(F, fft_npass(F)));
+  const size_t smem = sizeof(float2) * (Cfg::CS * fft_row(F) + fft_twoff(F, fft_npass(F)));
   const dim3 grid((n_ch + Cfg::CS - 1) / Cfg::CS);
   const bool vec = ((uintptr_t)rf % 16) == 0;
   auto k = vec ? k_spectrum<F, Cfg::CS, Cfg::NT, TIn, TOut, true> : k_spectrum<F, Cfg::CS, Cfg::NT, TIn, TOut, false>;
@@ -342,7 +385,7 @@ template <int F>
 static cudaError_t inverse_f(const kk_plan &p, const float2 *Y, int ncol, const int32_t *col,
                              int nrow, float2 *out, cudaStream_t s) {
   using Cfg = FftCfg<F>;
-  const size_t smem = sizeof(float2) * (2 * Cfg::CI * (F + 1) + fft_twoff(F, fft_npass(F)));
+  const size_t smem = sizeof(float2) * (2 * Cfg::CI * fft_row(F) + fft_twoff(F, fft_npass(F)));
   auto k = k_inverse<F, Cfg::CI, Cfg::NT>;
   cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   const dim3 grid((nrow + Cfg::CI - 1) / Cfg::CI);

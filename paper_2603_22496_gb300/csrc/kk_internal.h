@@ -47,6 +47,7 @@ struct DevTables {
   int32_t *tx_used = nullptr; // [Nu] row of rf for used transmit iu
   // decomposition
   unsigned long long *phase = nullptr; // [Mu][L] frac(D/T) * 2^64
+  uint32_t *phase32 = nullptr;         // [Mu][L] the same, rounded to 0.32 turns (tensor-core forms)
   int32_t *pair_q = nullptr;           // [P] (caller order) column of Y
   // KK gather (pairs in group-sorted order)
   int32_t *bf_row = nullptr;           // [P] row of rf_theta

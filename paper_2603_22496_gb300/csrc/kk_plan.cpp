@@ -258,6 +258,11 @@ kk_status make_kk(kk_plan &p, const kk_plan_desc *d) {
     }
   }
   const size_t off_phase = blob.add(phase);
+  // 0.32 fixed-point copy for the reduced-precision contraction: k phi mod
+  // 2^32 is then off by at most k 2^-33 turns (< 8e-7 rad for k < 1024)
+  std::vector<uint32_t> phase32(phase.size());
+  for (size_t q = 0; q < phase.size(); ++q) phase32[q] = (uint32_t)((phase[q] + (1ull << 31)) >> 32);
+  const size_t off_phase32 = blob.add(phase32);
 
   std::vector<int32_t> pair_q(P);
   for (int q = 0; q < P; ++q)
@@ -330,6 +335,7 @@ kk_status make_kk(kk_plan &p, const kk_plan_desc *d) {
   p.t.rfft_w = at<float2>(b, off_rw);
   p.t.tx_used = at<int32_t>(b, off_txu);
   p.t.phase = at<unsigned long long>(b, off_phase);
+  p.t.phase32 = at<uint32_t>(b, off_phase32);
   p.t.pair_q = at<int32_t>(b, off_pq);
   p.t.bf_row = at<int32_t>(b, off_row);
   p.t.bf_A = at<long long>(b, off_A);
