@@ -20,8 +20,8 @@
 //   wgrad   B  dY [P][cout] as (cout, P), box {AC, 64}; MN-major atoms.
 // One thread issues a chunk's copies (lanes of warp 0 when there are
 // several), all completing on the stage's mbarrier (expect_tx = its bytes).
-// Warp 0 issues the copies, warp 1's lane 0 the MMAs, all four warps run the
-// epilogue.  Every wait is bounded; a CTA that gives up records
+// Weight gradient: warp 0 issues the copies, warp 1's lane 0 the MMAs, all
+// four warps run the epilogue.  Every wait is bounded; a CTA that gives up records
 // KK_ERR_TIMEOUT, waits (bounded) for the copies it issued, frees its TMEM
 // and returns.
 #include <cuda.h>
@@ -164,38 +164,52 @@ struct TmaConvArgs {
   int *status;
 };
 
+// Forward / backward-data convolution, persistent: 1-4 CTAs per SM (as many
+// as TMEM holds with two accumulators each) loop over (pixel tile, channel
+// tile) items with one continuous copy ring each (up to 16 stages, about
+// 200 KB per SM) and two TMEM accumulators, so that the epilogue of one item
+// overlaps the MMAs of the next.  Warp 0 issues the
+// copies, warp 1's lane 0 the MMAs, warps 2-5 run the epilogue (warp w reads
+// TMEM lane quarter w % 4).  Barriers: full / empty per stage; acc_full[b]
+// (MMA commit) and acc_empty[b] (the 128 epilogue threads) per accumulator.
+constexpr int kPersThreads = 192;
+constexpr int kPersMaxStages = 16;
+constexpr int kPersBudget = 200 * 1024;
+
 template <int KC>
-__global__ void __launch_bounds__(kThreads)
-    k_conv3x3_tma(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmW,
-                  const TmaConvArgs a, const int N, const int S) {
+__global__ void __launch_bounds__(kPersThreads)
+    k_conv3x3_tma_pers(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmW,
+                       const TmaConvArgs a, const int N, const int S, const int n_items, const int n_ntiles) {
   extern __shared__ __align__(1024) unsigned char smem[];
-  __shared__ __align__(8) uint64_t full_bar[kMaxStages], empty_bar[kMaxStages], done_bar;
+  __shared__ __align__(8) uint64_t full_bar[kPersMaxStages], empty_bar[kPersMaxStages];
+  __shared__ __align__(8) uint64_t accf_bar[2], acce_bar[2], done_bar;
   __shared__ uint32_t tmem_slot;
   __shared__ int s_abort;
 
   constexpr uint32_t A_BYTES = kTileM * KC * 2;
-  constexpr uint32_t ROW = KC * 2;                 // bytes of one swizzled row
+  constexpr uint32_t ROW = KC * 2;
   constexpr uint32_t LAYOUT = layout_code(KC);
   const uint32_t B_BYTES = (uint32_t)N * KC * 2;
   const uint32_t STAGE = A_BYTES + B_BYTES;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int n0 = blockIdx.y * N;
   const int cpt = a.cin / KC;
   const int nK = 9 * cpt;
   int *status = a.status ? a.status : &g_tma_status;
-  int img, h0, w0;
-  tile_origin(blockIdx.x, kTileM, a.h, a.w, a.bw, img, h0, w0);
 
   uint32_t ncols = 32;
   while ((int)ncols < N) ncols <<= 1;
   if (warp == 0) {
-    tmem_alloc(&tmem_slot, ncols);
+    tmem_alloc(&tmem_slot, 2 * ncols);
     tmem_relinquish();
   }
   if (tid == 0) {
-    for (int s = 0; s < S; ++s) {
-      mbar_init(&full_bar[s], 1);
-      mbar_init(&empty_bar[s], 1);
+    for (int q = 0; q < S; ++q) {
+      mbar_init(&full_bar[q], 1);
+      mbar_init(&empty_bar[q], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&accf_bar[b], 1);
+      mbar_init(&acce_bar[b], 128);
     }
     mbar_init(&done_bar, 1);
     s_abort = 0;
@@ -208,97 +222,129 @@ __global__ void __launch_bounds__(kThreads)
   const uint32_t sbase = smem_u32(smem);
 
   if (warp == 0) {
-    int issued = 0;
-    for (int k = 0; k < nK; ++k) {
-      const int s = k % S;
-      int go = 1;
-      if (lane == 0) {
-        if (k >= S && !mbar_wait(&empty_bar[s], (uint32_t)((k / S) - 1) & 1u)) go = 0;
-        if (go) mbar_expect_tx(&full_bar[s], STAGE);
+    // ---- copies: every chunk of every item of this CTA through one ring ----
+    int g = 0;
+    bool ok = true;
+    for (int it = blockIdx.x; it < n_items && ok; it += gridDim.x) {
+      const int tile = it / n_ntiles, n0 = (it - tile * n_ntiles) * N;
+      int img, h0, w0;
+      tile_origin(tile, kTileM, a.h, a.w, a.bw, img, h0, w0);
+      for (int k = 0; k < nK; ++k, ++g) {
+        const int s = g % S;
+        int go = 1;
+        if (lane == 0) {
+          if (g >= S && !mbar_wait(&empty_bar[s], (uint32_t)((g / S) - 1) & 1u)) go = 0;
+          if (go) {
+            mbar_expect_tx(&full_bar[s], STAGE);
+            const int tap = k / cpt, c0 = (k - tap * cpt) * KC;
+            const int kh = tap / 3, kw = tap - kh * 3;
+            const uint32_t sA = sbase + (uint32_t)s * STAGE;
+            tma_4d(sA, &tmX, c0, w0 + kw - 1, h0 + kh - 1, img, &full_bar[s]);
+            tma_2d(sA + A_BYTES, &tmW, tap * a.cin + c0, n0, &full_bar[s]);
+          }
+        }
+        go = __shfl_sync(0xffffffffu, go, 0);
+        if (!go) {
+          s_abort = 1;
+          ok = false;
+          break;
+        }
       }
-      go = __shfl_sync(0xffffffffu, go, 0);
-      if (!go) {
-        s_abort = 1;
-        break;
-      }
-      if (lane == 0) {
-        const int tap = k / cpt, c0 = (k - tap * cpt) * KC;
-        const int kh = tap / 3, kw = tap - kh * 3;
-        const uint32_t sA = sbase + (uint32_t)s * STAGE, sB = sA + A_BYTES;
-        tma_4d(sA, &tmX, c0, w0 + kw - 1, h0 + kh - 1, img, &full_bar[s]);
-        tma_2d(sB, &tmW, tap * a.cin + c0, n0, &full_bar[s]);
-      }
-      issued = k + 1;
     }
-    // no copy may still be in flight when the CTA exits (bounded waits)
+    // no copy may still be in flight at exit (bounded waits)
     if (lane == 0)
-      for (int j = std::max(0, issued - S); j < issued; ++j) mbar_wait(&full_bar[j % S], (uint32_t)(j / S) & 1u);
+      for (int j = max(0, g - S); j < g; ++j) mbar_wait(&full_bar[j % S], (uint32_t)(j / S) & 1u);
     __syncwarp();
   } else if (warp == 1) {
+    // ---- MMAs: item li accumulates into TMEM buffer li & 1 ----
     if (lane == 0) {
       const uint32_t idesc = instr_desc(1u /* bf16 */, kTileM, (uint32_t)N);
-      for (int k = 0; k < nK; ++k) {
-        const int s = k % S;
-        if (!mbar_wait(&full_bar[s], (uint32_t)(k / S) & 1u)) {
+      int g = 0, li = 0;
+      bool ok = true;
+      for (int it = blockIdx.x; it < n_items && ok; it += gridDim.x, ++li) {
+        const int b = li & 1;
+        if (li >= 2 && !mbar_wait(&acce_bar[b], (uint32_t)((li >> 1) - 1) & 1u)) {
           s_abort = 1;
           break;
         }
         tc_fence_after();
-        const uint32_t sA = sbase + (uint32_t)s * STAGE, sB = sA + A_BYTES;
+        const uint32_t acc = tmem + (uint32_t)b * ncols;
+        for (int k = 0; k < nK; ++k, ++g) {
+          const int s = g % S;
+          if (!mbar_wait(&full_bar[s], (uint32_t)(g / S) & 1u)) {
+            s_abort = 1;
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t sA = sbase + (uint32_t)s * STAGE, sB = sA + A_BYTES;
 #pragma unroll
-        for (int kk = 0; kk < KC / 16; ++kk) {
-          const uint64_t ad = smem_desc_sw(sA + (uint32_t)kk * 32, 16, 8 * ROW, LAYOUT);
-          const uint64_t bd = smem_desc_sw(sB + (uint32_t)kk * 32, 16, 8 * ROW, LAYOUT);
-          mma_bf16(tmem, ad, bd, idesc, (k | kk) != 0 ? 1u : 0u);
+          for (int kk = 0; kk < KC / 16; ++kk) {
+            const uint64_t ad = smem_desc_sw(sA + (uint32_t)kk * 32, 16, 8 * ROW, LAYOUT);
+            const uint64_t bd = smem_desc_sw(sB + (uint32_t)kk * 32, 16, 8 * ROW, LAYOUT);
+            mma_bf16(acc, ad, bd, idesc, (k | kk) != 0 ? 1u : 0u);
+          }
+          mma_commit(&empty_bar[s]);
         }
-        mma_commit(&empty_bar[s]);
+        if (ok) mma_commit(&accf_bar[b]);
       }
-      mma_commit(&done_bar);
+      mma_commit(&done_bar);  // arrives when every MMA issued above has completed
     }
     __syncwarp();
-  }
-
-  __syncwarp();
-  const bool done = mbar_wait(&done_bar, 0);
-  tc_fence_after();
-  __syncthreads();  // s_abort final
-  if (!done || s_abort) {
-    if (tid == 0) atomicExch(status, (int)KK_ERR_TIMEOUT);
   } else {
-    const int row = warp * 32 + lane;
-    const size_t p = (size_t)blockIdx.x * kTileM + row;
-    const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
-    for (int c = 0; c < N; c += 16) {
-      float v[16];
-      tmem_ld16(trow + (uint32_t)c, v);
-      const int co = n0 + c;
-      if (co >= a.cout) continue;
-      if (a.bias) {
+    // ---- epilogue: warps 2-5, TMEM lane quarter warp % 4 ----
+    const int q = warp & 3;
+    const int row = q * 32 + lane;
+    int li = 0;
+    for (int it = blockIdx.x; it < n_items; it += gridDim.x, ++li) {
+      const int b = li & 1;
+      if (!mbar_wait(&accf_bar[b], (uint32_t)(li >> 1) & 1u)) {
+        s_abort = 1;
+        break;
+      }
+      tc_fence_after();
+      const int tile = it / n_ntiles, n0 = (it - tile * n_ntiles) * N;
+      const size_t p = (size_t)tile * kTileM + row;
+      const uint32_t trow = tmem + (uint32_t)b * ncols + ((uint32_t)(q * 32) << 16);
+      for (int c = 0; c < N; c += 16) {
+        float v[16];
+        tmem_ld16(trow + (uint32_t)c, v);
+        const int co = n0 + c;
+        if (co >= a.cout) continue;
+        if (a.bias) {
 #pragma unroll
-        for (int q = 0; q < 16; ++q) v[q] += __ldg(a.bias + co + q);
-      }
-      if (a.relu) {
+          for (int u = 0; u < 16; ++u) v[u] += __ldg(a.bias + co + u);
+        }
+        if (a.relu) {
 #pragma unroll
-        for (int q = 0; q < 16; ++q) v[q] = fmaxf(v[q], 0.f);
-      }
-      if (a.y) {
-        uint4 *dst = reinterpret_cast<uint4 *>(a.y + p * a.cout + co);
-        dst[0] = make_uint4(pack_bf16x2(v[0], v[1]), pack_bf16x2(v[2], v[3]), pack_bf16x2(v[4], v[5]),
-                            pack_bf16x2(v[6], v[7]));
-        dst[1] = make_uint4(pack_bf16x2(v[8], v[9]), pack_bf16x2(v[10], v[11]), pack_bf16x2(v[12], v[13]),
-                            pack_bf16x2(v[14], v[15]));
-      }
-      if (a.yf) {
-        float4 *dst = reinterpret_cast<float4 *>(a.yf + p * a.cout + co);
+          for (int u = 0; u < 16; ++u) v[u] = fmaxf(v[u], 0.f);
+        }
+        if (a.y) {
+          uint4 *dst = reinterpret_cast<uint4 *>(a.y + p * a.cout + co);
+          dst[0] = make_uint4(pack_bf16x2(v[0], v[1]), pack_bf16x2(v[2], v[3]), pack_bf16x2(v[4], v[5]),
+                              pack_bf16x2(v[6], v[7]));
+          dst[1] = make_uint4(pack_bf16x2(v[8], v[9]), pack_bf16x2(v[10], v[11]), pack_bf16x2(v[12], v[13]),
+                              pack_bf16x2(v[14], v[15]));
+        }
+        if (a.yf) {
+          float4 *dst = reinterpret_cast<float4 *>(a.yf + p * a.cout + co);
 #pragma unroll
-        for (int q = 0; q < 4; ++q) dst[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+          for (int u = 0; u < 4; ++u) dst[u] = make_float4(v[4 * u], v[4 * u + 1], v[4 * u + 2], v[4 * u + 3]);
+        }
       }
+      tc_fence_before();
+      mbar_arrive(&acce_bar[b]);
     }
+  }
+  __syncthreads();
+  if (warp == 0) {
+    const bool done = mbar_wait(&done_bar, 0);
+    if ((!done || s_abort) && lane == 0) atomicExch(status, (int)KK_ERR_TIMEOUT);
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if (warp == 0) tmem_dealloc(tmem, ncols);
+  if (warp == 0) tmem_dealloc(tmem, 2 * ncols);
 }
 
 struct TmaWgradArgs {
@@ -463,16 +509,30 @@ bool tile_shape(int H, int W, int tp, int &bw, int &bh) {
   return false;
 }
 
+int sm_count() {
+  int dev = 0, n = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+  return n;
+}
+
 template <int KC>
 cudaError_t launch_fwd(const CUtensorMap &mx, const CUtensorMap &mw, const TmaConvArgs &a, int N, int tiles,
                        cudaStream_t s) {
+  // persistent CTAs per SM: as many as TMEM holds (2 accumulators each), at most 4
+  uint32_t ncols = 32;
+  while ((int)ncols < N) ncols <<= 1;
+  const int cps = std::max(1, std::min(4, (int)(512 / (2 * ncols))));
   const size_t stage = (size_t)kTileM * KC * 2 + (size_t)N * KC * 2;
-  const int S = ring_stages(stage);
+  const int S = (int)std::max<size_t>(3, std::min<size_t>(kPersMaxStages, kPersBudget / cps / stage));
   const size_t smem = (size_t)S * stage;
-  cudaError_t e = cudaFuncSetAttribute(k_conv3x3_tma<KC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e =
+      cudaFuncSetAttribute(k_conv3x3_tma_pers<KC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  dim3 grid(tiles, (a.cout + N - 1) / N);
-  k_conv3x3_tma<KC><<<grid, kThreads, smem, s>>>(mx, mw, a, N, S);
+  const int n_ntiles = (a.cout + N - 1) / N;
+  const int n_items = tiles * n_ntiles;
+  const int grid = std::min(n_items, cps * sm_count());
+  k_conv3x3_tma_pers<KC><<<grid, kPersThreads, smem, s>>>(mx, mw, a, N, S, n_items, n_ntiles);
   return cudaGetLastError();
 }
 
