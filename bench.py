@@ -161,9 +161,20 @@ def _traffic(kernel: str, source: str):
     return None
 
 
+def _workload_seed(rank: int) -> int:
+    """Seed of a rank's frame: ranks shard frames, none shares a frame."""
+    return 2000 + rank
+
+
 def _workload(rank: int):
     import kksynth
-    return kksynth.workload_large(seed=2000 + rank)
+    return kksynth.workload_large(seed=_workload_seed(rank))
+
+
+def whole_job_rate(steps: int, world: int, ms_total_max: float) -> float:
+    """Frames per second of the whole job: every rank forms `steps` frames of
+    its own; the time is the slowest rank's."""
+    return steps * world / (ms_total_max / 1e3)
 
 
 def _full_pairs(w):
@@ -415,8 +426,7 @@ def run_ours(args):
     ms_total = sum(a.elapsed_time(b) for a, b in evs)
     ms_total = _max_over_ranks(ms_total, world)
     ms_step = ms_total / args.steps
-    frames = args.steps * world
-    value = frames / (ms_total / 1e3)
+    value = whole_job_rate(args.steps, world, ms_total)
     launches = args.steps * (info.launches_decompose + info.launches_beamform)
     status = plan.status()
 
