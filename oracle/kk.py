@@ -60,9 +60,9 @@ def _load():
             ip = ctypes.POINTER(ctypes.c_int32)
             ci, cd = ctypes.c_int, ctypes.c_double
             lib.orc_kk_beamform.argtypes = [ci, ci, dp, dp, dp, dp, dp, dp, ip, ci, ci, dp, dp,
-                                            cd, cd, dp]
+                                            cd, cd, dp, dp]
             lib.orc_kk_beamform.restype = ci
-            lib.orc_das_beamform.argtypes = [ci, ci, ci, dp, dp, dp, dp, ci, dp, dp, cd, cd, dp]
+            lib.orc_das_beamform.argtypes = [ci, ci, ci, dp, dp, dp, dp, ci, dp, dp, cd, cd, cd, ci, dp]
             lib.orc_das_beamform.restype = ci
             _lib = lib
     return _lib
@@ -175,8 +175,10 @@ def grid_pixels(grid, pixels=None):
 
 
 def kk_beamform(y: np.ndarray, elem_x, ps: "_schemes.PairSet", grid, fs: float, c: float,
-                pixels=None, rule: str = "advance") -> np.ndarray:
-    """B[J][nz][nx] (or B[J][n_pix] for a pixel list), complex128, Eq. (KK)."""
+                pixels=None, rule: str = "advance", weights=None) -> np.ndarray:
+    """B[J][nz][nx] (or B[J][n_pix] for a pixel list), complex128, Eq. (KK);
+    with `weights` [P], pair p's term is multiplied by weights[p] (the
+    apodization the paper leaves out of Eq. (KK) for simplicity)."""
     lib = _load()
     P, T = y.shape
     yc = np.ascontiguousarray(y, dtype=np.complex128)
@@ -191,9 +193,12 @@ def kk_beamform(y: np.ndarray, elem_x, ps: "_schemes.PairSet", grid, fs: float, 
     px, pz = np.ascontiguousarray(px), np.ascontiguousarray(pz)
     npix = px.shape[0]
     B = np.zeros((ps.n_groups, npix), dtype=np.complex128)
+    wv = None if weights is None else np.ascontiguousarray(weights, dtype=np.float64)
+    if wv is not None and wv.shape != (P,):
+        raise ValueError("weights must have one entry per pair")
     rc = lib.orc_kk_beamform(P, T, _d(yc.view(np.float64)), _d(si), _d(ci_), _d(so), _d(co),
                              _d(xref), _i(grp), ps.n_groups, npix, _d(px), _d(pz), float(fs),
-                             float(c), _d(B.view(np.float64)))
+                             float(c), _d(wv) if wv is not None else None, _d(B.view(np.float64)))
     if rc:
         raise RuntimeError(f"orc_kk_beamform: {rc}")
     if pixels is None:
@@ -212,18 +217,23 @@ def compound(B: np.ndarray, mode: str) -> np.ndarray:
     raise ValueError(mode)
 
 
-def kk_image(rf, elem_x, ps, grid, fs, c, pixels=None, rule="advance"):
+def kk_image(rf, elem_x, ps, grid, fs, c, pixels=None, rule="advance", weights=None):
     """Decomposition then image formation: B[J][...] complex128."""
     y = decompose(rf, elem_x, ps, fs, c, rule)
-    return kk_beamform(y, elem_x, ps, grid, fs, c, pixels, rule)
+    return kk_beamform(y, elem_x, ps, grid, fs, c, pixels, rule, weights)
 
 
 # --------------------------------------------------------------------------
 # Step 8: DAS, Eq. (DAS)
 # --------------------------------------------------------------------------
+APERTURE_WINDOWS = {"boxcar": 0, "hann": 1}
+
+
 def das_beamform_analytic(y: np.ndarray, tx_angles, elem_x, grid, fs: float, c: float,
-                          pixels=None) -> np.ndarray:
-    """B[nz][nx] (or [n_pix]) from analytic channel data y[N][L][T]."""
+                          pixels=None, f_number: float = 0.0, window: str = "boxcar") -> np.ndarray:
+    """B[nz][nx] (or [n_pix]) from analytic channel data y[N][L][T].  With
+    f_number > 0 each element is weighted by the receive aperture of half-width
+    z / (2 F) about the pixel (boxcar or Hann); 0 = full aperture."""
     lib = _load()
     N, L, T = y.shape
     yc = np.ascontiguousarray(y, dtype=np.complex128)
@@ -235,7 +245,8 @@ def das_beamform_analytic(y: np.ndarray, tx_angles, elem_x, grid, fs: float, c: 
     npix = px.shape[0]
     B = np.zeros(npix, dtype=np.complex128)
     rc = lib.orc_das_beamform(N, L, T, _d(yc.view(np.float64)), _d(si), _d(ci_), _d(ex), npix,
-                              _d(px), _d(pz), float(fs), float(c), _d(B.view(np.float64)))
+                              _d(px), _d(pz), float(fs), float(c), float(f_number),
+                              APERTURE_WINDOWS[window], _d(B.view(np.float64)))
     if rc:
         raise RuntimeError(f"orc_das_beamform: {rc}")
     if pixels is None:
@@ -243,9 +254,10 @@ def das_beamform_analytic(y: np.ndarray, tx_angles, elem_x, grid, fs: float, c: 
     return B
 
 
-def das_image(rf, tx_angles, elem_x, grid, fs, c, pixels=None):
+def das_image(rf, tx_angles, elem_x, grid, fs, c, pixels=None, f_number=0.0, window="boxcar"):
     """Hilbert transform of every channel, then Eq. (DAS)."""
-    return das_beamform_analytic(analytic_signal(rf), tx_angles, elem_x, grid, fs, c, pixels)
+    return das_beamform_analytic(analytic_signal(rf), tx_angles, elem_x, grid, fs, c, pixels,
+                                 f_number, window)
 
 
 def rel_l2(a, b) -> float:

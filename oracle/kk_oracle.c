@@ -54,7 +54,7 @@ int orc_kk_beamform(int P, int T, const double *y, const double *sin_i,
                     const double *cos_o, const double *xref_o,
                     const int32_t *group, int J, int n_pix,
                     const double *pix_x, const double *pix_z, double fs,
-                    double c, double *B) {
+                    double c, const double *w, double *B) {
   if (P < 0 || T < 2 || J < 1 || n_pix < 0) return 1;
   for (int p = 0; p < P; ++p)
     if (group[p] < 0 || group[p] >= J) return 2;
@@ -70,23 +70,40 @@ int orc_kk_beamform(int P, int T, const double *y, const double *sin_i,
       const double tau_out = ((x - xref_o[p]) * sin_o[p] + z * cos_o[p]) / c;
       double re, im;
       lerp(y + 2L * p * T, T, fs * (tau_in + tau_out), &re, &im);
-      B[2 * ((long)group[p] * n_pix + q)] += re;
-      B[2 * ((long)group[p] * n_pix + q) + 1] += im;
+      const double wp = w ? w[p] : 1.0;
+      B[2 * ((long)group[p] * n_pix + q)] += wp * re;
+      B[2 * ((long)group[p] * n_pix + q) + 1] += wp * im;
     }
   }
   return 0;
 }
 
 /*
+ * Receive aperture weight of element offset d = |x - u_l| at depth z for an
+ * F-number F (Table 1 lists the F-numbers of the acquisitions; Eq. (DAS) is
+ * stated without apodization): half-width h = z / (2 F); boxcar 1 for
+ * d <= h, Hann (1 + cos(pi d / h)) / 2 for d <= h, 0 beyond; F <= 0 means the
+ * full aperture (weight 1).
+ */
+static double aperture(double d, double z, double F, int window) {
+  if (F <= 0.0) return 1.0;
+  const double h = z / (2.0 * F);
+  if (!(d <= h)) return 0.0;
+  if (window == 0) return 1.0;
+  return 0.5 * (1.0 + cos(M_PI * d / h));
+}
+
+/*
  * CPWC delay-and-sum, Eq. (DAS) of Section II-B:
- *   B(r) = sum_{i,l} y_il( tau_in(r, theta_i) + |r - (u_l, 0)| / c )
+ *   B(r) = sum_{i,l} a_l(r) y_il( tau_in(r, theta_i) + |r - (u_l, 0)| / c )
+ * with the receive aperture weight a_l(r) above (1 for the full aperture).
  * y   [N][L][T] complex analytic channel data
  * B   [n_pix] complex (overwritten)
  */
 int orc_das_beamform(int N, int L, int T, const double *y, const double *sin_i,
                      const double *cos_i, const double *elem_x, int n_pix,
                      const double *pix_x, const double *pix_z, double fs,
-                     double c, double *B) {
+                     double c, double f_number, int window, double *B) {
   if (N < 0 || L < 0 || T < 2 || n_pix < 0) return 1;
 #pragma omp parallel for schedule(static)
   for (int q = 0; q < n_pix; ++q) {
@@ -97,10 +114,11 @@ int orc_das_beamform(int N, int L, int T, const double *y, const double *sin_i,
       for (int l = 0; l < L; ++l) {
         const double dx = x - elem_x[l];
         const double tau_out = sqrt(dx * dx + z * z) / c;
+        const double a = aperture(fabs(dx), z, f_number, window);
         double re, im;
         lerp(y + 2L * ((long)i * L + l) * T, T, fs * (tau_in + tau_out), &re, &im);
-        accr += re;
-        acci += im;
+        accr += a * re;
+        acci += a * im;
       }
     }
     B[2 * q] = accr;
