@@ -69,6 +69,11 @@ typedef enum kk_compound {
   KK_COMPOUND_INCOHERENT = 2  /* I = sum_j |B_j|^2, Eq. (incoherent) */
 } kk_compound;
 
+typedef enum kk_aperture {
+  KK_APERTURE_BOXCAR = 0,  /* 1 inside the half-width, 0 outside */
+  KK_APERTURE_HANN = 1     /* (1 + cos(pi d / h)) / 2 inside, 0 outside */
+} kk_aperture;
+
 typedef enum kk_scheme {
   KK_SCHEME_SAME = 0,     /* theta_o = theta_i (Section II-C, redundant) */
   KK_SCHEME_VERNIER = 1,  /* theta_o = 2 o dtheta_i / M (Section II-C) */
@@ -106,6 +111,17 @@ typedef struct kk_plan_desc {
                                  contraction on tensor cores and need
                                  n_elem <= 128 and <= 256 transmits in use */
   int32_t device;             /* CUDA device ordinal the plan lives on */
+  /* Apodization (the paper states Eqs. (DAS) and (KK) without it and notes
+   * it folds in directly; zero-initialised fields mean none): */
+  const double *pair_weight;  /* [P] weight of pair p's term in Eq. (KK)
+                                 (KK only; NULL = 1).  It scales pair p's
+                                 decomposed record (row p of the rf_theta
+                                 that kk_decompose / kk_inverse write), so
+                                 kk_beamform sums weighted terms */
+  double f_number;            /* DAS receive aperture: element l reaches pixel
+                                 (x, z) when |x - u_l| <= z / (2 f_number),
+                                 weighted by `aperture`; <= 0 = full aperture */
+  int32_t aperture;           /* kk_aperture window over that half-width */
 } kk_plan_desc;
 
 typedef struct kk_plan kk_plan;

@@ -24,6 +24,7 @@ KK_RF_I16, KK_RF_F32 = 0, 1
 KK_PREC_F32, KK_PREC_BF16, KK_PREC_F16, KK_PREC_F8E4M3 = 0, 1, 2, 3
 KK_COMPOUND_NONE, KK_COMPOUND_COHERENT, KK_COMPOUND_INCOHERENT = 0, 1, 2
 KK_SCHEME_SAME, KK_SCHEME_VERNIER, KK_SCHEME_SHIFTED, KK_SCHEME_CONFOCAL = 0, 1, 2, 3
+KK_APERTURE_BOXCAR, KK_APERTURE_HANN = 0, 1
 
 _STATUS = {0: "KK_OK", 1: "KK_ERR_INVALID_ARG", 2: "KK_ERR_UNSUPPORTED", 3: "KK_ERR_CUDA",
            4: "KK_ERR_OOM", 5: "KK_ERR_TIMEOUT"}
@@ -66,7 +67,8 @@ class kk_plan_desc(ctypes.Structure):
                 ("compound", ctypes.c_int32), ("grid", kk_grid),
                 ("c", ctypes.c_double), ("fs", ctypes.c_double),
                 ("n_samples", ctypes.c_int32), ("rf_dtype", ctypes.c_int32),
-                ("precision", ctypes.c_int32), ("device", ctypes.c_int32)]
+                ("precision", ctypes.c_int32), ("device", ctypes.c_int32),
+                ("pair_weight", _dp), ("f_number", ctypes.c_double), ("aperture", ctypes.c_int32)]
 
 
 class kk_plan_info(ctypes.Structure):
@@ -232,7 +234,7 @@ def kk_scheme_angles(kind: int, n_tx: int, dtheta: float, M: int, j: float = 0.0
 
 def _desc(elem_x, tx_angles, grid, c, fs, n_samples, rf_dtype, rx_angles=None, pairs=None,
           group_of_pair=None, n_groups=1, compound=KK_COMPOUND_NONE, precision=KK_PREC_F32,
-          device=0):
+          device=0, pair_weight=None, f_number=0.0, aperture=KK_APERTURE_BOXCAR):
     keep = []
     ex = _f64(elem_x); keep.append(ex)
     tx = _f64(tx_angles); keep.append(tx)
@@ -261,6 +263,11 @@ def _desc(elem_x, tx_angles, grid, c, fs, n_samples, rf_dtype, rx_angles=None, p
     d.rf_dtype = int(rf_dtype)
     d.precision = int(precision)
     d.device = int(device)
+    if pair_weight is not None:
+        pw = _f64(pair_weight); keep.append(pw)
+        d.pair_weight = pw.ctypes.data_as(_dp)
+    d.f_number = float(f_number)
+    d.aperture = int(aperture)
     return d, keep
 
 
@@ -346,10 +353,11 @@ class Plan:
 
     def __init__(self, elem_x, tx_angles, grid, c, fs, n_samples, rf_dtype=KK_RF_F32,
                  rx_angles=None, pairs=None, group_of_pair=None, n_groups=1,
-                 compound=KK_COMPOUND_NONE, precision=KK_PREC_F32, device=0, das=False):
+                 compound=KK_COMPOUND_NONE, precision=KK_PREC_F32, device=0, das=False,
+                 pair_weight=None, f_number=0.0, aperture=KK_APERTURE_BOXCAR):
         self.desc, self._keep = _desc(elem_x, tx_angles, grid, c, fs, n_samples, rf_dtype,
                                       rx_angles, pairs, group_of_pair, n_groups, compound,
-                                      precision, device)
+                                      precision, device, pair_weight, f_number, aperture)
         self.handle = das_plan_create(self.desc) if das else kk_plan_create(self.desc)
         self.info = kk_plan_get_info(self.handle)
         self.is_das = das

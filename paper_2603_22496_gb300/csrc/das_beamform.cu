@@ -1,6 +1,8 @@
 // das_beamform.cu -- CPWC delay-and-sum reference, Eq. (DAS).
 //
-//   B(ix, iz) = sum_{i,l} lerp(y_il, s_in(i; ix, iz) + R_l(ix, iz)),
+//   B(ix, iz) = sum_{i,l} a_l(ix, iz) lerp(y_il, s_in(i; ix, iz) + R_l(ix, iz)),
+//   a_l = receive-aperture weight (1 for the full aperture), applied once
+//   per (pixel, element, stage) to the stage's partial sum,
 //   s_in = fs (x sin theta_i + z cos theta_i) / c     (affine, 32.32 fixed point)
 //   R_l  = fs sqrt((x - u_l)^2 + z^2) / c              (per pixel and element)
 //
@@ -65,13 +67,23 @@ __device__ __forceinline__ float2 df_add(float2 a, float2 b) {
   return make_float2(h, s.y - (h - s.x));
 }
 
+// Receive-aperture weight of an element at lateral offset d (samples) from a
+// pixel at depth z (samples): t = 2 F d / z, boxcar 1 for t <= 1, Hann
+// (1 + cos(pi t)) / 2 for t <= 1, 0 beyond; two_f = 0 is the full aperture.
+__device__ __forceinline__ float aperture_weight(float d, float z, float two_f, int window) {
+  if (two_f <= 0.f) return 1.f;
+  const float t = two_f * d / z;
+  if (!(t <= 1.f)) return 0.f;
+  return window == KK_APERTURE_HANN ? 0.5f * (1.f + cospif(t)) : 1.f;
+}
+
 __global__ void __launch_bounds__(kGatherThreads)
     k_das_gather(const float2 *__restrict__ y, int N, int L, int T, const long long *__restrict__ dA,
                  const long long *__restrict__ dB, const long long *__restrict__ dC,
                  const float *__restrict__ dAf, const float *__restrict__ dBf,
                  const float2 *__restrict__ xs, const float2 *__restrict__ zs,
                  const float2 *__restrict__ us, int nx, int nz, int tiles_x, int win, int stage,
-                 int split, float2 *__restrict__ B, float *__restrict__ I) {
+                 int split, float two_f, int window, float2 *__restrict__ B, float *__restrict__ I) {
   extern __shared__ float4 sw[];
   __shared__ WarpChan s_wc[4][kMaxStage];
   __shared__ float2 s_ab[kMaxStage];
@@ -105,9 +117,10 @@ __global__ void __launch_bounds__(kGatherThreads)
     // receive delay of this thread's pixels: integer part (x16 bytes) + fraction
     const float2 dx2 = df_sqr(df_sub(xq, u));
     unsigned kout16[kRowsPerThread];
-    float fout[kRowsPerThread];
+    float fout[kRowsPerThread], aw[kRowsPerThread];
 #pragma unroll
     for (int r = 0; r < kRowsPerThread; ++r) {
+      aw[r] = aperture_weight(fabsf(xq.x - u.x), __ldg(zs + izb + r).x, two_f, window);
       const float2 S = df_add(dx2, z2[r]);
       const float rh = sqrtf(S.x);
       const float t = fmaf(-rh, rh, S.x) + S.y;
@@ -181,8 +194,8 @@ __global__ void __launch_bounds__(kGatherThreads)
       }
 #pragma unroll
       for (int r = 0; r < kRowsPerThread; ++r) {
-        acc[r].x += sacc[r].x;
-        acc[r].y += sacc[r].y;
+        acc[r].x = fmaf(aw[r], sacc[r].x, acc[r].x);
+        acc[r].y = fmaf(aw[r], sacc[r].y, acc[r].y);
       }
     }
   }
@@ -208,7 +221,7 @@ __global__ void __launch_bounds__(kGatherThreads, MINB)
                         const float *__restrict__ dAf, const float *__restrict__ dBf,
                         const float2 *__restrict__ xs, const float2 *__restrict__ zs,
                         const float2 *__restrict__ us, int nx, int nz, int tiles_x, int win, int split,
-                        float2 *__restrict__ B, float *__restrict__ I) {
+                        float two_f, int window, float2 *__restrict__ B, float *__restrict__ I) {
   constexpr int ROWS = 4, TZ = 16;
   constexpr int PPW = STAGE / 4;   // channels staged by each warp
   constexpr int QPP = NPT / PPW;   // entries per lane per staged channel
@@ -356,10 +369,21 @@ __global__ void __launch_bounds__(kGatherThreads, MINB)
         sacc[r].y += fmaf(f, e.w, e.y);
       }
     }
+    if (two_f > 0.f) {
+      // receive-aperture weight of element l at this thread's pixels
+      const float d = fabsf(xq.x - __ldg(us + l).x);
 #pragma unroll
-    for (int r = 0; r < ROWS; ++r) {
-      acc[r].x += sacc[r].x;
-      acc[r].y += sacc[r].y;
+      for (int r = 0; r < ROWS; ++r) {
+        const float aw = aperture_weight(d, __ldg(zs + izb + r).x, two_f, window);
+        acc[r].x = fmaf(aw, sacc[r].x, acc[r].x);
+        acc[r].y = fmaf(aw, sacc[r].y, acc[r].y);
+      }
+    } else {
+#pragma unroll
+      for (int r = 0; r < ROWS; ++r) {
+        acc[r].x += sacc[r].x;
+        acc[r].y += sacc[r].y;
+      }
     }
     buf ^= 1;
   }
@@ -404,7 +428,7 @@ cudaError_t launch_staged(const kk_plan &p, const float2 *y, float2 *dst, float 
   const dim3 grid(p.tiles_x * p.tiles_z, p.bf_split);
   k<<<grid, kGatherThreads, smem, s>>>(y, p.N, p.L, p.T, p.t.das_A, p.t.das_B, p.t.das_C, p.t.das_Af,
                                        p.t.das_Bf, p.t.xs, p.t.zs, p.t.us, p.grid.nx, p.grid.nz, p.tiles_x,
-                                       p.bf_win, p.bf_split, dst, I);
+                                       p.bf_win, p.bf_split, p.das_two_f, p.das_window, dst, I);
   return cudaGetLastError();
 }
 }  // namespace
@@ -438,7 +462,8 @@ cudaError_t launch_das_gather(const kk_plan &p, const float2 *y, float2 *B, floa
     const dim3 grid(p.tiles_x * p.tiles_z, p.bf_split);
     k_das_gather<<<grid, kGatherThreads, smem, s>>>(
         y, p.N, p.L, p.T, p.t.das_A, p.t.das_B, p.t.das_C, p.t.das_Af, p.t.das_Bf, p.t.xs, p.t.zs,
-        p.t.us, p.grid.nx, p.grid.nz, p.tiles_x, p.bf_win, p.bf_stage, p.bf_split, dst, I);
+        p.t.us, p.grid.nx, p.grid.nz, p.tiles_x, p.bf_win, p.bf_stage, p.bf_split, p.das_two_f,
+        p.das_window, dst, I);
     e = cudaGetLastError();
   }
   if (e != cudaSuccess || p.bf_split == 1) return e;

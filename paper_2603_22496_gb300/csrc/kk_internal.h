@@ -53,6 +53,7 @@ struct DevTables {
   int32_t *bf_row = nullptr;           // [P] row of rf_theta
   long long *bf_A = nullptr, *bf_B = nullptr, *bf_C = nullptr; // 32.32 samples
   float *bf_Af = nullptr, *bf_Bf = nullptr;                    // samples per pixel
+  float *pair_w = nullptr;             // [P] pair weights, caller's order (null: all 1)
   int32_t *group_start = nullptr;      // [J+1]
   // DAS
   long long *das_A = nullptr, *das_B = nullptr, *das_C = nullptr; // [N] tau_in 32.32
@@ -93,6 +94,9 @@ struct kk_plan {
   // of two, 2^-ceil(log2(2T)), so |X| <= 2 T 32768 stays below the FP16
   // maximum; the contraction's epilogue multiplies by 1 / x_scale
   float x_scale = 1.f;
+  // DAS receive aperture: 2 F (0 = full aperture) and window (kk_aperture)
+  float das_two_f = 0.f;
+  int das_window = KK_APERTURE_BOXCAR;
 };
 
 namespace kk {
@@ -138,8 +142,9 @@ kk_status cuda_fail(cudaError_t e, const char *what);
 // X is complex FP32, BF16 or FP16 per the plan's precision (spectrum_bytes)
 cudaError_t launch_spectrum(const kk_plan &p, const void *rf, void *X, int n_tx_rows,
                             const int32_t *tx_rows, cudaStream_t s);
+// row r of out is scaled by row_w[r] (nullable: 1)
 cudaError_t launch_inverse(const kk_plan &p, const float2 *Y, int ncol, const int32_t *col_of_row,
-                           int nrow, float2 *out, cudaStream_t s);
+                           int nrow, float2 *out, cudaStream_t s, const float *row_w = nullptr);
 cudaError_t launch_shear_f32(const kk_plan &p, const float2 *X, float2 *Y, cudaStream_t s);
 cudaError_t launch_shear_tc(const kk_plan &p, const void *X, float2 *Y, cudaStream_t s);
 size_t tc_shear_smem_bytes(int precision, int NP);

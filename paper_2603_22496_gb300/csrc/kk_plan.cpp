@@ -195,6 +195,9 @@ kk_status make_kk(kk_plan &p, const kk_plan_desc *d) {
   if (d->n_rx < 1 || !d->rx_angles) { set_error("n_rx < 1 or rx_angles null"); return KK_ERR_INVALID_ARG; }
   if (d->n_pairs < 1 || !d->pairs) { set_error("n_pairs < 1 or pairs null"); return KK_ERR_INVALID_ARG; }
   if (d->n_groups < 1) { set_error("n_groups < 1"); return KK_ERR_INVALID_ARG; }
+  if (d->pair_weight)
+    for (int q = 0; q < d->n_pairs; ++q)
+      if (!std::isfinite(d->pair_weight[q])) { set_error("non-finite pair weight"); return KK_ERR_INVALID_ARG; }
   if (d->compound < KK_COMPOUND_NONE || d->compound > KK_COMPOUND_INCOHERENT) { set_error("bad compound mode"); return KK_ERR_INVALID_ARG; }
   if (d->precision < KK_PREC_F32 || d->precision > KK_PREC_F8E4M3) { set_error("bad precision"); return KK_ERR_INVALID_ARG; }
   for (int o = 0; o < d->n_rx; ++o)
@@ -303,6 +306,12 @@ kk_status make_kk(kk_plan &p, const kk_plan_desc *d) {
   }
   const size_t off_row = blob.add(row), off_A = blob.add(A), off_B = blob.add(Bv), off_C = blob.add(C);
   const size_t off_Af = blob.add(Af), off_Bf = blob.add(Bf);
+  size_t off_W = 0;
+  if (d->pair_weight) {  // caller's pair order: rows of rf_theta
+    std::vector<float> wv(P);
+    for (int q = 0; q < P; ++q) wv[q] = (float)d->pair_weight[q];
+    off_W = blob.add(wv);
+  }
   std::vector<int32_t> gs(p.h_group_start.begin(), p.h_group_start.end());
   const size_t off_gs = blob.add(gs);
 
@@ -343,12 +352,19 @@ kk_status make_kk(kk_plan &p, const kk_plan_desc *d) {
   p.t.bf_C = at<long long>(b, off_C);
   p.t.bf_Af = at<float>(b, off_Af);
   p.t.bf_Bf = at<float>(b, off_Bf);
+  p.t.pair_w = d->pair_weight ? at<float>(b, off_W) : nullptr;
   p.t.group_start = at<int32_t>(b, off_gs);
   p.t.status = at<int>(b, p.status_off);
   return KK_OK;
 }
 
 kk_status make_das(kk_plan &p, const kk_plan_desc *d) {
+  if (!std::isfinite(d->f_number) || (d->aperture != KK_APERTURE_BOXCAR && d->aperture != KK_APERTURE_HANN)) {
+    set_error("bad receive aperture (finite f_number, KK_APERTURE_BOXCAR or KK_APERTURE_HANN)");
+    return KK_ERR_INVALID_ARG;
+  }
+  p.das_two_f = d->f_number > 0 ? (float)(2.0 * d->f_number) : 0.f;
+  p.das_window = d->aperture;
   p.is_das = true;
   p.J = 1;
   p.P = p.N * p.L;
@@ -496,7 +512,7 @@ kk_status enqueue_decompose(const kk_plan *p, const void *rf, void *rf_theta, vo
   e = (p->precision == KK_PREC_F32) ? launch_shear_f32(*p, (const float2 *)X, Y, s)
                                      : launch_shear_tc(*p, X, Y, s);
   if (e != cudaSuccess) return cuda_fail(e, "shear launch");
-  e = launch_inverse(*p, Y, p->Nu * p->Mu, p->t.pair_q, p->P, (float2 *)rf_theta, s);
+  e = launch_inverse(*p, Y, p->Nu * p->Mu, p->t.pair_q, p->P, (float2 *)rf_theta, s, p->t.pair_w);
   if (e != cudaSuccess) return cuda_fail(e, "inverse launch");
   return KK_OK;
 }
@@ -639,7 +655,7 @@ kk_status kk_inverse(const kk_plan *p, const void *d_Y, void *d_rf_theta, void *
   if (!aligned(d_rf_theta, 16)) { set_error("rf_theta must be 16-byte aligned"); return KK_ERR_INVALID_ARG; }
   DeviceGuard guard(p->device);
   cudaError_t e = launch_inverse(*p, (const float2 *)d_Y, p->Nu * p->Mu, p->t.pair_q, p->P,
-                                 (float2 *)d_rf_theta, (cudaStream_t)stream);
+                                 (float2 *)d_rf_theta, (cudaStream_t)stream, p->t.pair_w);
   return e == cudaSuccess ? KK_OK : cuda_fail(e, "inverse launch");
 }
 
