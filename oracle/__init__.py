@@ -18,9 +18,12 @@ compressive ultrasound beamforming", that it follows):
   (Eq. (compression) via the Fourier shift theorem, Section II-F), KK image
   formation (Eq. (KK)), DAS (Eq. (DAS)), compounding.
 * ``kk_oracle.c`` -- the pixel x pair loops in plain FP64 C.
+* ``quality``  -- image-quality measures the paper judges images by: gCNR of
+  an inclusion against a background region and half-amplitude widths of
+  point targets (Section III, Figs. 4 and 5).
 
 Every function here is pinned by ``tests/test_oracle_*.py`` against closed
 forms, invariants, brute force or the paper's stated properties; see the test
 docstrings for which mistake each pin would catch.
 """
-from . import schemes, kk  # noqa: F401
+from . import schemes, kk, quality  # noqa: F401
