@@ -18,4 +18,6 @@ from .phantom import (  # noqa: F401
     simulate_rf, add_noise_and_quantise,
     workload_small, workload_large, workload_tiny, workload_custom,
     point_phantom,
+    LARGE_WIRES_MM, LARGE_CYSTS_MM,
 )
+from .images import speckle_images  # noqa: F401

@@ -25,6 +25,8 @@ KK_PREC_F32, KK_PREC_BF16, KK_PREC_F16, KK_PREC_F8E4M3 = 0, 1, 2, 3
 KK_COMPOUND_NONE, KK_COMPOUND_COHERENT, KK_COMPOUND_INCOHERENT = 0, 1, 2
 KK_SCHEME_SAME, KK_SCHEME_VERNIER, KK_SCHEME_SHIFTED, KK_SCHEME_CONFOCAL = 0, 1, 2, 3
 KK_APERTURE_BOXCAR, KK_APERTURE_HANN = 0, 1
+KK_REGION_DISK, KK_REGION_ANNULUS, KK_REGION_RECT = 0, 1, 2
+KK_IMAGE_COMPLEX, KK_IMAGE_INTENSITY = 0, 1
 
 _STATUS = {0: "KK_OK", 1: "KK_ERR_INVALID_ARG", 2: "KK_ERR_UNSUPPORTED", 3: "KK_ERR_CUDA",
            4: "KK_ERR_OOM", 5: "KK_ERR_TIMEOUT"}
@@ -40,7 +42,9 @@ EXPORTS = ["kk_plan_create", "das_plan_create", "kk_plan_destroy", "kk_plan_get_
            "kk_net_create", "kk_net_destroy", "kk_net_info", "kk_net_status", "kk_nn_status", "kk_net_get_params", "kk_net_set_params",
            "kk_net_forward", "kk_net_loss_grad", "kk_net_adam", "kk_net_save", "kk_net_load",
            "kk_net_judge_filter", "kk_net_judge", "kk_net_image_scale",
-           "kk_nn_conv3x3", "kk_nn_conv3x3_dgrad", "kk_nn_conv3x3_wgrad_workspace", "kk_nn_conv3x3_wgrad"]
+           "kk_nn_conv3x3", "kk_nn_conv3x3_dgrad", "kk_nn_conv3x3_wgrad_workspace", "kk_nn_conv3x3_wgrad",
+           # include/kkquality.h
+           "kk_quality_create", "kk_quality_destroy", "kk_quality_gcnr", "kk_quality_fwhm"]
 
 
 class KKError(RuntimeError):
@@ -100,6 +104,27 @@ class kk_net_desc(ctypes.Structure):
     _fields_ = [("max_batch", ctypes.c_int32), ("height", ctypes.c_int32), ("width", ctypes.c_int32),
                 ("base_channels", ctypes.c_int32), ("seed", ctypes.c_uint64)]
 
+
+class kk_region(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("a", ctypes.c_double), ("b", ctypes.c_double),
+                ("c", ctypes.c_double), ("d", ctypes.c_double)]
+
+
+class kk_target(ctypes.Structure):
+    _fields_ = [("ix", ctypes.c_int32), ("iz", ctypes.c_int32), ("wx", ctypes.c_int32),
+                ("wz", ctypes.c_int32)]
+
+
+class kk_quality_desc(ctypes.Structure):
+    _fields_ = [("grid", kk_grid), ("image_kind", ctypes.c_int32), ("n_contrast", ctypes.c_int32),
+                ("inside", ctypes.POINTER(kk_region)), ("outside", ctypes.POINTER(kk_region)),
+                ("n_bins", ctypes.c_int32), ("n_targets", ctypes.c_int32),
+                ("targets", ctypes.POINTER(kk_target)), ("device", ctypes.c_int32)]
+
+
+# layout of kk_fwhm_result (32 bytes)
+FWHM_DTYPE = np.dtype([("ix", "<i4"), ("iz", "<i4"), ("peak", "<f4"), ("reserved", "<i4"),
+                       ("lateral", "<f8"), ("axial", "<f8")])
 
 _lib = None
 
@@ -174,6 +199,10 @@ def load(build_if_missing: bool = False):
                                            ctypes.c_int32, ctypes.POINTER(ctypes.c_size_t)], st),
         "kk_nn_conv3x3_wgrad": ([vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, vp,
                                  ctypes.c_int32, vp, vp, vp, vp], st),
+        "kk_quality_create": ([pp, ctypes.POINTER(kk_quality_desc)], st),
+        "kk_quality_destroy": ([vp], None),
+        "kk_quality_gcnr": ([vp, vp, ctypes.c_int32, vp, vp], st),
+        "kk_quality_fwhm": ([vp, vp, ctypes.c_int32, vp, vp], st),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -617,3 +646,94 @@ class Net:
             stat = torch.empty((out.shape[0], 2), dtype=torch.float32, device=out.device)
         _check(load().kk_net_judge(self.handle, out.shape[0], _ptr(out), _ptr(xc), _ptr(stat), _stream(stream)))
         return stat
+
+
+def _region(r) -> kk_region:
+    kind, a, b, c, d = r
+    return kk_region(int(kind), float(a), float(b), float(c), float(d))
+
+
+def kk_quality_create(desc: kk_quality_desc) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    _check(load().kk_quality_create(ctypes.byref(h), ctypes.byref(desc)))
+    return h
+
+
+def kk_quality_destroy(h):
+    if h:
+        load().kk_quality_destroy(h)
+
+
+def kk_quality_gcnr(h, images, n_images, out, stream=None):
+    _check(load().kk_quality_gcnr(h, _ptr(images), int(n_images), _ptr(out), _stream(stream)))
+
+
+def kk_quality_fwhm(h, images, n_images, out, stream=None):
+    _check(load().kk_quality_fwhm(h, _ptr(images), int(n_images), _ptr(out), _stream(stream)))
+
+
+class Quality:
+    """Owner of a ``kk_quality`` handle: gCNR region pairs and FWHM targets on one grid.
+
+    ``inside`` / ``outside``: sequences of ``(kind, a, b, c, d)`` regions
+    (metres); ``targets``: sequences of ``(ix, iz, wx, wz)`` pixel windows.
+    """
+
+    def __init__(self, grid, inside=(), outside=(), targets=(), n_bins: int = 256,
+                 image_kind: int = KK_IMAGE_COMPLEX, device: int = 0):
+        if len(inside) != len(outside):
+            raise ValueError("inside and outside need the same number of regions")
+        nx, nz, x0, dx, z0, dz = grid
+        self.grid = tuple(grid)
+        self.n_contrast = len(inside)
+        self.n_targets = len(targets)
+        self.image_kind = int(image_kind)
+        rin = (kk_region * max(1, self.n_contrast))(*[_region(r) for r in inside])
+        rout = (kk_region * max(1, self.n_contrast))(*[_region(r) for r in outside])
+        tg = (kk_target * max(1, self.n_targets))(*[kk_target(*(int(v) for v in t)) for t in targets])
+        d = kk_quality_desc(kk_grid(int(nx), int(nz), float(x0), float(dx), float(z0), float(dz)),
+                            self.image_kind, self.n_contrast, rin, rout, int(n_bins), self.n_targets,
+                            tg, int(device))
+        self.h = None
+        self.h = kk_quality_create(d)
+
+    def __del__(self):
+        try:
+            if self.h:
+                kk_quality_destroy(self.h)
+                self.h = None
+        except Exception:
+            pass
+
+    def _n_images(self, images):
+        nx, nz = self.grid[0], self.grid[1]
+        per = nx * nz * (2 if self.image_kind == KK_IMAGE_COMPLEX else 1)
+        if images.dtype.itemsize != 4 or images.numel() % per:
+            raise ValueError("images must be float32 / complex64 [n][nz][nx] on the plan's grid")
+        return images.numel() // per
+
+    def gcnr(self, images, out=None, stream=None):
+        """float64 ``[n_images][n_contrast]`` gCNR (device tensor)."""
+        import torch
+        n = self._n_images(images)
+        if out is None:
+            out = torch.empty((n, self.n_contrast), dtype=torch.float64, device=images.device)
+        kk_quality_gcnr(self.h, images, n, out, stream)
+        return out
+
+    def fwhm(self, images, out=None, stream=None):
+        """Raw ``[n_images][n_targets][32]`` uint8 device tensor of kk_fwhm_result
+        records; ``decode_fwhm`` turns it into a numpy structured array."""
+        import torch
+        n = self._n_images(images)
+        if out is None:
+            out = torch.empty((n, self.n_targets, FWHM_DTYPE.itemsize), dtype=torch.uint8,
+                              device=images.device)
+        kk_quality_fwhm(self.h, images, n, out, stream)
+        return out
+
+
+def decode_fwhm(raw) -> np.ndarray:
+    """numpy structured array (``FWHM_DTYPE``) of a raw kk_fwhm_result tensor."""
+    a = raw.detach().cpu().contiguous().numpy()
+    return np.frombuffer(a.tobytes(), dtype=FWHM_DTYPE).reshape(a.shape[:-1])

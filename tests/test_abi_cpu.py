@@ -89,3 +89,57 @@ def test_plan_validation_is_host_side(lib):
         kb.kk_plan_create(d)
     assert e.value.status == kb.KK_ERR_INVALID_ARG
     assert kb.load().kk_last_error()
+
+
+def test_quality_struct_layouts_match_header(tmp_path):
+    """ctypes mirrors of kkquality.h have the C compiler's sizes and offsets."""
+    src = tmp_path / "layout.c"
+    src.write_text("""
+#include <stddef.h>
+#include <stdio.h>
+#include "kkquality.h"
+#define P(T, f) printf(#T "." #f " %zu\\n", offsetof(T, f))
+int main(void) {
+  printf("kk_region %zu\\nkk_target %zu\\nkk_fwhm_result %zu\\nkk_quality_desc %zu\\n",
+         sizeof(kk_region), sizeof(kk_target), sizeof(kk_fwhm_result), sizeof(kk_quality_desc));
+  P(kk_region, a); P(kk_region, d); P(kk_fwhm_result, peak); P(kk_fwhm_result, lateral);
+  P(kk_fwhm_result, axial); P(kk_quality_desc, image_kind); P(kk_quality_desc, inside);
+  P(kk_quality_desc, n_bins); P(kk_quality_desc, targets); P(kk_quality_desc, device);
+  return 0;
+}
+""")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", INCLUDE, str(src), "-o", str(exe)], check=True)
+    got = dict(line.split() for line in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                       check=True).stdout.splitlines())
+    import ctypes
+    want = {"kk_region": ctypes.sizeof(kb.kk_region), "kk_target": ctypes.sizeof(kb.kk_target),
+            "kk_fwhm_result": kb.FWHM_DTYPE.itemsize, "kk_quality_desc": ctypes.sizeof(kb.kk_quality_desc),
+            "kk_region.a": kb.kk_region.a.offset, "kk_region.d": kb.kk_region.d.offset,
+            "kk_fwhm_result.peak": kb.FWHM_DTYPE.fields["peak"][1],
+            "kk_fwhm_result.lateral": kb.FWHM_DTYPE.fields["lateral"][1],
+            "kk_fwhm_result.axial": kb.FWHM_DTYPE.fields["axial"][1],
+            "kk_quality_desc.image_kind": kb.kk_quality_desc.image_kind.offset,
+            "kk_quality_desc.inside": kb.kk_quality_desc.inside.offset,
+            "kk_quality_desc.n_bins": kb.kk_quality_desc.n_bins.offset,
+            "kk_quality_desc.targets": kb.kk_quality_desc.targets.offset,
+            "kk_quality_desc.device": kb.kk_quality_desc.device.offset}
+    assert {k: int(v) for k, v in got.items()} == want
+
+
+@pytest.mark.parametrize("kw", [
+    dict(n_bins=0), dict(n_bins=4097), dict(image_kind=2),
+    dict(inside=[(3, 0, 0, 1, 0)], outside=[(0, 0, 0, 1, 0)]),              # bad kind
+    dict(inside=[(0, 0, 0, -1, 0)], outside=[(0, 0, 0, 1, 0)]),             # negative radius
+    dict(inside=[(1, 0, 0, 2, 1)], outside=[(0, 0, 0, 1, 0)]),              # r1 > r2
+    dict(inside=[(0, float("nan"), 0, 1, 0)], outside=[(0, 0, 0, 1, 0)]),   # non-finite
+    dict(targets=[(1, 1, -1, 2)]),
+    dict(grid=(0, 8, 0.0, 1e-4, 0.0, 1e-4)), dict(grid=(8, 8, 0.0, -1e-4, 0.0, 1e-4)),
+])
+def test_quality_validation_is_host_side(lib, kw):
+    args = dict(grid=(8, 8, 0.0, 1e-4, 0.0, 1e-4), inside=(), outside=(), targets=(), n_bins=16,
+                image_kind=kb.KK_IMAGE_COMPLEX)
+    args.update(kw)
+    with pytest.raises(kb.KKError) as e:
+        kb.Quality(**args)
+    assert e.value.status == kb.KK_ERR_INVALID_ARG
