@@ -36,6 +36,7 @@ struct LabelBox {
 constexpr int kGcnrThreads = 256;
 constexpr int kFwhmWarps = 8;
 constexpr int kMaxBins = 4096;
+constexpr int kUnroll = 4;  // columns per lane per step of the gCNR passes
 
 __device__ __forceinline__ bool in_region(const kk_region &R, double x, double z) {
   if (R.kind == KK_REGION_RECT) return x >= R.a && x <= R.b && z >= R.c && z <= R.d;
@@ -84,19 +85,32 @@ __global__ void __launch_bounds__(kGcnrThreads)
   const LabelBox b = boxes[m];
   const long long base = (long long)n * img_elems + (long long)b.bz0 * nx + b.bx0;
 
+  // Both passes walk the label box row by row (one warp per row, lanes
+  // along the row) and take kUnroll columns per lane per step, issuing all
+  // of that step's loads before using them.
   float lo = INFINITY, hi = -INFINITY;
   int nin = 0, nout = 0;
   for (int r = warp; r < b.bh; r += nwarp) {
     const uint8_t *lrow = labels + b.off + (long long)r * b.bw;
     const long long prow = base + (long long)r * nx;
-    for (int c = lane; c < b.bw; c += 32) {
-      const int L = lrow[c];
-      if (!L) continue;
-      const float e = envelope<KIND>(img, prow + c);
-      lo = fminf(lo, e);
-      hi = fmaxf(hi, e);
-      nin += L & 1;
-      nout += L >> 1;
+    for (int c0 = lane; c0 < b.bw; c0 += 32 * kUnroll) {
+      int L[kUnroll];
+      float e[kUnroll];
+#pragma unroll
+      for (int u = 0; u < kUnroll; ++u) {
+        const int c = c0 + 32 * u;
+        L[u] = c < b.bw ? lrow[c] : 0;
+      }
+#pragma unroll
+      for (int u = 0; u < kUnroll; ++u) e[u] = L[u] ? envelope<KIND>(img, prow + c0 + 32 * u) : 0.f;
+#pragma unroll
+      for (int u = 0; u < kUnroll; ++u)
+        if (L[u]) {
+          lo = fminf(lo, e[u]);
+          hi = fmaxf(hi, e[u]);
+          nin += L[u] & 1;
+          nout += L[u] >> 1;
+        }
     }
   }
   for (int o = 16; o; o >>= 1) {
@@ -133,17 +147,28 @@ __global__ void __launch_bounds__(kGcnrThreads)
   for (int r = warp; r < b.bh; r += nwarp) {
     const uint8_t *lrow = labels + b.off + (long long)r * b.bw;
     const long long prow = base + (long long)r * nx;
-    for (int c = lane; c < b.bw; c += 32) {
-      const int L = lrow[c];
-      if (!L) continue;
-      int bin = 0;
-      if (!flat) {
-        const float e = envelope<KIND>(img, prow + c);
-        const float q = __fdiv_rn(__fmul_rn(__fsub_rn(e, lo), nb), w);
-        bin = min((int)q, n_bins - 1);
+    for (int c0 = lane; c0 < b.bw; c0 += 32 * kUnroll) {
+      int L[kUnroll];
+      float e[kUnroll];
+#pragma unroll
+      for (int u = 0; u < kUnroll; ++u) {
+        const int c = c0 + 32 * u;
+        L[u] = c < b.bw ? lrow[c] : 0;
       }
-      if (L & 1) atomicAdd(&hist[bin], 1);
-      if (L & 2) atomicAdd(&hist[n_bins + bin], 1);
+#pragma unroll
+      for (int u = 0; u < kUnroll; ++u)
+        e[u] = (L[u] && !flat) ? envelope<KIND>(img, prow + c0 + 32 * u) : 0.f;
+#pragma unroll
+      for (int u = 0; u < kUnroll; ++u) {
+        if (!L[u]) continue;
+        int bin = 0;
+        if (!flat) {
+          const float q = __fdiv_rn(__fmul_rn(__fsub_rn(e[u], lo), nb), w);
+          bin = min((int)q, n_bins - 1);
+        }
+        if (L[u] & 1) atomicAdd(&hist[bin], 1);
+        if (L[u] & 2) atomicAdd(&hist[n_bins + bin], 1);
+      }
     }
   }
   __syncthreads();
