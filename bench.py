@@ -362,6 +362,111 @@ FORMS = (("bf16", "KK_PREC_BF16"), ("f32", "KK_PREC_F32"), ("f16", "KK_PREC_F16"
 CHOSEN = "bf16"
 
 
+def _quality(kb, w, images, flush, peaks, peak_src, n_batch=256):
+    """gCNR of the frame's three cysts (disk 0.75 R against the annulus
+    1.25-1.75 R) and half-amplitude widths of its 20 wires for each image, then
+    the quality kernels' speed on a batch of n_batch copies of the first image.
+    Algorithmic bytes of the gCNR kernel: one float32 read of every pixel of
+    every region (the second, histogram pass re-reads from L2)."""
+    import numpy as np
+    import torch
+    import kksynth
+    nx, nz, x0, dx, z0, dz = w.grid
+    R = 2e-3
+    inside = [(kb.KK_REGION_DISK, cx * 1e-3, cz * 1e-3, 0.75 * R, 0.0) for cx, cz in kksynth.LARGE_CYSTS_MM]
+    outside = [(kb.KK_REGION_ANNULUS, cx * 1e-3, cz * 1e-3, 1.25 * R, 1.75 * R) for cx, cz in kksynth.LARGE_CYSTS_MM]
+    win = int(round(0.5e-3 / dx))
+    tg = [(int(round((x * 1e-3 - x0) / dx)), int(round((z * 1e-3 - z0) / dz)), win, win)
+          for x, z in kksynth.LARGE_WIRES_MM]
+    q = kb.Quality(w.grid, inside, outside, tg, n_bins=256, image_kind=kb.KK_IMAGE_INTENSITY)
+    res = {"regions": "cysts of the frame: disk 1.5 mm vs annulus 2.5-3.5 mm, 256 bins; wires: +-0.5 mm windows"}
+    for name, img in images.items():
+        g = q.gcnr(img)
+        f = kb.decode_fwhm(q.fwhm(img))
+        torch.cuda.synchronize()
+        res[name] = {"gcnr_cysts": [round(float(v), 3) for v in g.cpu().numpy().ravel()],
+                     "lateral_fwhm_mm": round(float(np.nanmean(f["lateral"])) * 1e3, 3),
+                     "axial_fwhm_mm": round(float(np.nanmean(f["axial"])) * 1e3, 3)}
+    xs = x0 + dx * np.arange(nx)
+    zs = z0 + dz * np.arange(nz)
+    d2 = lambda cx, cz: (xs[None, :] - cx) ** 2 + (zs[:, None] - cz) ** 2
+    labelled = sum(int((d2(r[1], r[2]) <= r[3] ** 2).sum()) for r in inside) + \
+        sum(int(((d2(r[1], r[2]) > r[3] ** 2) & (d2(r[1], r[2]) <= r[4] ** 2)).sum()) for r in outside)
+    first = next(iter(images.values()))
+    batch = first.reshape(1, nz, nx).repeat(n_batch, 1, 1).contiguous()
+    out_g = torch.empty((n_batch, len(inside)), dtype=torch.float64, device=batch.device)
+    out_f = torch.empty((n_batch, len(tg), kb.FWHM_DTYPE.itemsize), dtype=torch.uint8, device=batch.device)
+    ms_g = _time_loop(lambda: q.gcnr(batch, out_g), 10, flush)
+    ms_f = _time_loop(lambda: q.fwhm(batch, out_f), 10, flush)
+    gbytes = n_batch * labelled * 4
+    gbs = gbytes / (ms_g / 1e3) / 1e9
+    res["kernels"] = {"images": n_batch, "gcnr_us_per_image": round(ms_g * 1e3 / n_batch, 3),
+                      "fwhm_us_per_image": round(ms_f * 1e3 / n_batch, 3),
+                      "gcnr_algorithmic_bytes": gbytes, "gcnr_hbm_gbs": round(gbs, 1),
+                      "gcnr_hbm_frac_of_" + peak_src: round(gbs / float(peaks["hbm_gbs"]), 4)}
+    del batch
+    return res
+
+
+def _streaming(kb, w, plan, info, groups=(5, 15, 25, 75), frames=40, warm=3):
+    """Streaming decomposition of the benchmark frame: the 75 transmit events
+    are pushed from pinned host memory in acquisition order, decomposed in
+    groups of G transmits as the groups fill, and every frame is imaged on a
+    second CUDA stream while the next frame's groups are decomposed.  For each
+    G: wall-clock frames/s over `frames` frames pushed back to back in bursts
+    of G events (host-to-device copies included) and the latency from the last
+    event of a frame to its finished image; for G = 15 also frames/s with the
+    events pushed one by one."""
+    import torch
+    h_rf = torch.from_numpy(w.rf).pin_memory()
+    outs = [(plan.empty_image(), plan.empty_intensity()) for _ in range(2)]
+    N = h_rf.shape[0]
+    res = {"h2d_bytes_per_frame": int(info.rf_bytes), "frames": frames, "by_group": {}}
+    for G in groups:
+        st = kb.Stream(plan, G)
+
+        def frame(f, burst):
+            if burst:
+                for i in range(0, N, G):
+                    st.push_many(i, h_events=h_rf[i:i + G])
+            else:
+                for i in range(N):
+                    st.push(i, h_event=h_rf[i])
+            st.end_frame(*outs[f % 2])
+
+        modes = (True, False) if G == 15 else (True,)
+        rates = {}
+        for burst in modes:
+            for f in range(warm):
+                frame(f, burst)
+            st.sync()
+            t0 = time.perf_counter()
+            for f in range(frames):
+                frame(f, burst)
+            st.sync()
+            rates[burst] = frames / (time.perf_counter() - t0)
+        lat = []
+        for f in range(5):
+            if N > 1:
+                st.push_many(0, h_events=h_rf[0:N - 1])
+            st.sync()
+            t1 = time.perf_counter()
+            st.push(N - 1, h_event=h_rf[N - 1])
+            st.end_frame(*outs[f % 2])
+            st.sync()
+            lat.append(time.perf_counter() - t1)
+        si = st.info
+        r = {"frames_per_s": round(rates[True], 1), "groups_per_frame": si.n_groups,
+             "ring_groups": si.ring_groups, "last_event_to_image_ms": round(1e3 * sorted(lat)[len(lat) // 2], 3),
+             "device_bytes": int(si.device_bytes)}
+        if False in rates:
+            r["frames_per_s_event_by_event"] = round(rates[False], 1)
+        res["by_group"][str(G)] = r
+        del st
+        torch.cuda.empty_cache()
+    return res
+
+
 def _form_plan(kb, w, rx, pairs, prec_name, local):
     return kb.Plan(w.elem_x, w.tx_angles, w.grid, w.c, w.fs, w.n_samples, kb.KK_RF_I16,
                    rx_angles=rx, pairs=pairs, compound=kb.KK_COMPOUND_COHERENT,
@@ -445,6 +550,28 @@ def run_ours(args):
            "gpu_launches": launches, "clocks": clk, "device_status": status}
 
     if rank == 0 and not args.quick:
+        # end to end through the C ABI from pinned host memory
+        h_rf = torch.from_numpy(w.rf).pin_memory()
+        h_B = torch.empty((1, info.nz, info.nx, 2), dtype=torch.float32).pin_memory()
+        h_I = torch.empty((info.nz, info.nx), dtype=torch.float32).pin_memory()
+        scratch = torch.empty(plan.scratch_bytes(), dtype=torch.uint8, device=dev)
+        for _ in range(3):
+            plan.run_host(h_rf, h_B, h_I, scratch)
+        torch.cuda.synchronize()
+        k_e2e = max(5, args.steps // 2)
+        t0 = time.perf_counter()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(k_e2e):
+            plan.run_host(h_rf, h_B, h_I, scratch)
+        b.record()
+        torch.cuda.synchronize()
+        ms_e2e = a.elapsed_time(b) / k_e2e
+        out["e2e"] = {"value": round(1e3 / ms_e2e, 3), "unit": UNIT,
+                      "h2d_bytes_per_step": int(info.rf_bytes),
+                      "d2h_bytes_per_step": int(info.image_bytes + info.intensity_bytes),
+                      "wall_ms_per_step": round((time.perf_counter() - t0) * 1e3 / k_e2e, 3)}
         side = {}
         reps = 10
         F = info.n_bins
@@ -517,6 +644,10 @@ def run_ours(args):
         ms_d = _time_loop(lambda: dplan.das(d_rf, dB, dI, dws), 5, flush)
         side["das_75x128"] = {"frames_per_s": round(1e3 / ms_d, 1),
                               "gpixel_pairs_per_s": round(75 * 128 * npix / (ms_d / 1e3) / 1e9, 2)}
+        side["image_quality"] = _quality(kb, w, {"kk_75x128": I, "kk_vernier_8x16": vI, "das_75x128": dI},
+                                         flush, peaks, peak_src)
+        side["streaming"] = _streaming(kb, w, plan, info)
+        torch.cuda.empty_cache()
         # batched form: 256 frames of uneven size, one CUDA graph
         if not args.no_batch:
             frames_b = _batch_frames(kb, args.batch_frames)
@@ -541,28 +672,6 @@ def run_ours(args):
             torch.cuda.empty_cache()
         out["breakdown"] = side
 
-        # end to end through the C ABI from pinned host memory
-        h_rf = torch.from_numpy(w.rf).pin_memory()
-        h_B = torch.empty((1, info.nz, info.nx, 2), dtype=torch.float32).pin_memory()
-        h_I = torch.empty((info.nz, info.nx), dtype=torch.float32).pin_memory()
-        scratch = torch.empty(plan.scratch_bytes(), dtype=torch.uint8, device=dev)
-        for _ in range(3):
-            plan.run_host(h_rf, h_B, h_I, scratch)
-        torch.cuda.synchronize()
-        k_e2e = max(5, args.steps // 2)
-        t0 = time.perf_counter()
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record()
-        for _ in range(k_e2e):
-            plan.run_host(h_rf, h_B, h_I, scratch)
-        b.record()
-        torch.cuda.synchronize()
-        ms_e2e = a.elapsed_time(b) / k_e2e
-        out["e2e"] = {"value": round(1e3 / ms_e2e, 3), "unit": UNIT,
-                      "h2d_bytes_per_step": int(info.rf_bytes),
-                      "d2h_bytes_per_step": int(info.image_bytes + info.intensity_bytes),
-                      "wall_ms_per_step": round((time.perf_counter() - t0) * 1e3 / k_e2e, 3)}
         if world == 1 and not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline(w, rx, pairs, plans)
     if rank == 0:

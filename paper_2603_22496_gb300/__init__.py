@@ -44,7 +44,10 @@ EXPORTS = ["kk_plan_create", "das_plan_create", "kk_plan_destroy", "kk_plan_get_
            "kk_net_judge_filter", "kk_net_judge", "kk_net_image_scale",
            "kk_nn_conv3x3", "kk_nn_conv3x3_dgrad", "kk_nn_conv3x3_wgrad_workspace", "kk_nn_conv3x3_wgrad",
            # include/kkquality.h
-           "kk_quality_create", "kk_quality_destroy", "kk_quality_gcnr", "kk_quality_fwhm"]
+           "kk_quality_create", "kk_quality_destroy", "kk_quality_gcnr", "kk_quality_fwhm",
+           # include/kkstream.h
+           "kk_stream_create", "kk_stream_push", "kk_stream_push_many", "kk_stream_end_frame", "kk_stream_wait", "kk_stream_sync",
+           "kk_stream_get_info", "kk_stream_destroy"]
 
 
 class KKError(RuntimeError):
@@ -120,6 +123,13 @@ class kk_quality_desc(ctypes.Structure):
                 ("inside", ctypes.POINTER(kk_region)), ("outside", ctypes.POINTER(kk_region)),
                 ("n_bins", ctypes.c_int32), ("n_targets", ctypes.c_int32),
                 ("targets", ctypes.POINTER(kk_target)), ("device", ctypes.c_int32)]
+
+
+class kk_stream_info(ctypes.Structure):
+    _fields_ = [("group", ctypes.c_int32), ("ring_groups", ctypes.c_int32), ("n_groups", ctypes.c_int32),
+                ("events_pushed", ctypes.c_int64),
+                ("events_dropped", ctypes.c_int64), ("groups_run", ctypes.c_int64),
+                ("frames_done", ctypes.c_int64), ("device_bytes", ctypes.c_size_t), ("copies", ctypes.c_int64)]
 
 
 # layout of kk_fwhm_result (32 bytes)
@@ -203,6 +213,14 @@ def load(build_if_missing: bool = False):
         "kk_quality_destroy": ([vp], None),
         "kk_quality_gcnr": ([vp, vp, ctypes.c_int32, vp, vp], st),
         "kk_quality_fwhm": ([vp, vp, ctypes.c_int32, vp, vp], st),
+        "kk_stream_create": ([pp, vp, ctypes.c_int32, ctypes.c_int32], st),
+        "kk_stream_push": ([vp, ctypes.c_int32, vp, vp], st),
+        "kk_stream_push_many": ([vp, ctypes.c_int32, ctypes.c_int32, vp, vp], st),
+        "kk_stream_end_frame": ([vp, vp, vp], st),
+        "kk_stream_wait": ([vp, vp], st),
+        "kk_stream_sync": ([vp], st),
+        "kk_stream_get_info": ([vp, ctypes.POINTER(kk_stream_info)], st),
+        "kk_stream_destroy": ([vp], None),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -737,3 +755,85 @@ def decode_fwhm(raw) -> np.ndarray:
     """numpy structured array (``FWHM_DTYPE``) of a raw kk_fwhm_result tensor."""
     a = raw.detach().cpu().contiguous().numpy()
     return np.frombuffer(a.tobytes(), dtype=FWHM_DTYPE).reshape(a.shape[:-1])
+
+
+# --------------------------------------------------------------------------
+# streaming decomposition (include/kkstream.h)
+# --------------------------------------------------------------------------
+def kk_stream_create(plan_handle, group: int, ring_groups: int = 2) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    _check(load().kk_stream_create(ctypes.byref(h), plan_handle, int(group), int(ring_groups)))
+    return h
+
+
+def kk_stream_push(h, tx_row: int, h_event=None, d_event=None):
+    """h_event: pinned host tensor (or None); d_event: CUDA tensor (or None)."""
+    _check(load().kk_stream_push(h, int(tx_row), _host_ptr(h_event), _ptr(d_event)))
+
+
+def kk_stream_push_many(h, first_row: int, h_events=None, d_events=None):
+    """Rows first_row.. from a [n][L][T] block (pinned host or CUDA tensor)."""
+    n = (h_events if h_events is not None else d_events).shape[0]
+    _check(load().kk_stream_push_many(h, int(first_row), int(n), _host_ptr(h_events), _ptr(d_events)))
+
+
+def kk_stream_end_frame(h, B, I=None):
+    _check(load().kk_stream_end_frame(h, _ptr(B), _ptr(I)))
+
+
+def kk_stream_wait(h, stream=None):
+    _check(load().kk_stream_wait(h, _stream(stream)))
+
+
+def kk_stream_sync(h):
+    _check(load().kk_stream_sync(h))
+
+
+def kk_stream_get_info(h) -> kk_stream_info:
+    info = kk_stream_info()
+    _check(load().kk_stream_get_info(h, ctypes.byref(info)))
+    return info
+
+
+def kk_stream_destroy(h):
+    if h:
+        load().kk_stream_destroy(h)
+
+
+class Stream:
+    """Owner of a ``kk_stream`` handle on a KK ``Plan`` (kept alive by this object)."""
+
+    def __init__(self, plan: "Plan", group: int, ring_groups: int | None = None):
+        """ring_groups defaults to a frame's groups plus one."""
+        self.plan = plan
+        self.h = None
+        if ring_groups is None:   # invalid group sizes are left to the library to reject
+            ring_groups = min(64, max(2, -(-plan.info.n_tx_used // int(group)) + 1)) if group >= 1 else 2
+        self.h = kk_stream_create(plan.handle, group, ring_groups)
+
+    def __del__(self):
+        try:
+            if self.h:
+                kk_stream_destroy(self.h)
+                self.h = None
+        except Exception:
+            pass
+
+    def push(self, tx_row: int, h_event=None, d_event=None):
+        kk_stream_push(self.h, tx_row, h_event, d_event)
+
+    def push_many(self, first_row: int, h_events=None, d_events=None):
+        kk_stream_push_many(self.h, first_row, h_events, d_events)
+
+    def end_frame(self, B, I=None):
+        kk_stream_end_frame(self.h, B, I)
+
+    def wait(self, stream=None):
+        kk_stream_wait(self.h, stream)
+
+    def sync(self):
+        kk_stream_sync(self.h)
+
+    @property
+    def info(self) -> kk_stream_info:
+        return kk_stream_get_info(self.h)

@@ -303,7 +303,8 @@ __global__ void __launch_bounds__(NT) k_inverse(const float2 *__restrict__ Y, in
                                                 const float2 *__restrict__ tw,
                                                 const float2 *__restrict__ rw,
                                                 float2 *__restrict__ out, float scale,
-                                                const float *__restrict__ row_w) {
+                                                const float *__restrict__ row_w,
+                                                const int32_t *__restrict__ out_row) {
   constexpr int FS = fft_row(F);
   constexpr int T = 2 * F;
   extern __shared__ float2 sm[];
@@ -339,7 +340,8 @@ __global__ void __launch_bounds__(NT) k_inverse(const float2 *__restrict__ Y, in
     const float2 od = sm[(2 * rr + 1) * FS + fft_pad(m)];
     const float sc = row_w ? scale * __ldg(row_w + row) : scale;
     const float4 o = make_float4(ev.x * sc, -ev.y * sc, od.x * sc, -od.y * sc);
-    *reinterpret_cast<float4 *>(out + (size_t)row * T + 2 * m) = o;
+    const size_t orow = out_row ? (size_t)__ldg(out_row + row) : (size_t)row;
+    *reinterpret_cast<float4 *>(out + orow * T + 2 * m) = o;
   }
 }
 
@@ -386,14 +388,15 @@ static cudaError_t spectrum_f(const kk_plan &p, const void *rf, void *X, int n_r
 
 template <int F>
 static cudaError_t inverse_f(const kk_plan &p, const float2 *Y, int ncol, const int32_t *col,
-                             int nrow, float2 *out, cudaStream_t s, const float *row_w) {
+                             int nrow, float2 *out, cudaStream_t s, const float *row_w,
+                             const int32_t *out_row) {
   using Cfg = FftCfg<F>;
   const size_t smem = sizeof(float2) * (2 * Cfg::CI * fft_row(F) + fft_twoff(F, fft_npass(F)));
   auto k = k_inverse<F, Cfg::CI, Cfg::NT>;
   cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   const dim3 grid((nrow + Cfg::CI - 1) / Cfg::CI);
   k<<<grid, Cfg::NT, smem, s>>>(Y, ncol, col, nrow, p.t.fft_tw, p.t.rfft_w, out,
-                                (float)(1.0 / (double)(2 * F)), row_w);
+                                (float)(1.0 / (double)(2 * F)), row_w, out_row);
   return cudaGetLastError();
 }
 
@@ -412,15 +415,16 @@ cudaError_t launch_spectrum(const kk_plan &p, const void *rf, void *X, int n_row
 }
 
 cudaError_t launch_inverse(const kk_plan &p, const float2 *Y, int ncol, const int32_t *col,
-                           int nrow, float2 *out, cudaStream_t s, const float *row_w) {
+                           int nrow, float2 *out, cudaStream_t s, const float *row_w,
+                           const int32_t *out_row) {
   switch (p.F) {
-    case 128: return inverse_f<128>(p, Y, ncol, col, nrow, out, s, row_w);
-    case 256: return inverse_f<256>(p, Y, ncol, col, nrow, out, s, row_w);
-    case 512: return inverse_f<512>(p, Y, ncol, col, nrow, out, s, row_w);
-    case 768: return inverse_f<768>(p, Y, ncol, col, nrow, out, s, row_w);
-    case 1024: return inverse_f<1024>(p, Y, ncol, col, nrow, out, s, row_w);
-    case 1536: return inverse_f<1536>(p, Y, ncol, col, nrow, out, s, row_w);
-    case 2048: return inverse_f<2048>(p, Y, ncol, col, nrow, out, s, row_w);
+    case 128: return inverse_f<128>(p, Y, ncol, col, nrow, out, s, row_w, out_row);
+    case 256: return inverse_f<256>(p, Y, ncol, col, nrow, out, s, row_w, out_row);
+    case 512: return inverse_f<512>(p, Y, ncol, col, nrow, out, s, row_w, out_row);
+    case 768: return inverse_f<768>(p, Y, ncol, col, nrow, out, s, row_w, out_row);
+    case 1024: return inverse_f<1024>(p, Y, ncol, col, nrow, out, s, row_w, out_row);
+    case 1536: return inverse_f<1536>(p, Y, ncol, col, nrow, out, s, row_w, out_row);
+    case 2048: return inverse_f<2048>(p, Y, ncol, col, nrow, out, s, row_w, out_row);
     default: return cudaErrorInvalidValue;
   }
 }

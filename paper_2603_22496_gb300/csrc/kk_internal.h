@@ -80,6 +80,11 @@ struct kk_plan {
   void *dev_block = nullptr;     // the one allocation holding DevTables
   size_t status_off = 0;
   std::vector<int32_t> h_group_start;
+  // host copies of the pair tables (caller's pair order), for the streaming
+  // decomposition: transmit position (0..Nu-1), receive position (0..Mu-1),
+  // pair weight (empty without weights); used transmit rows (ascending)
+  std::vector<int32_t> h_pair_tu, h_pair_ou, h_tx_used;
+  std::vector<float> h_pair_w;
   // gather kernel configuration
   int bf_rows = 8;     // z rows per thread: tile = 32 x (4 * bf_rows) pixels
   int bf_win = 0;      // window entries staged per pair / channel
@@ -133,6 +138,10 @@ struct DeviceGuard {
 
 // spectrum -> contraction -> inverse of one frame on stream s (no checks)
 kk_status enqueue_decompose(const kk_plan *p, const void *rf, void *rf_theta, void *ws, cudaStream_t s);
+// KK image formation of one frame on stream s (no checks)
+kk_status enqueue_beamform(const kk_plan *p, const void *rf_theta, void *B, float *I, void *ws, cudaStream_t s);
+// the contraction of the plan's precision form: X [F][p.Nu][L] -> Y [F][p.Nu][Mu]
+cudaError_t launch_shear(const kk_plan &p, const void *X, float2 *Y, cudaStream_t s);
 
 // thread-local error message
 void set_error(const std::string &msg);
@@ -142,9 +151,11 @@ kk_status cuda_fail(cudaError_t e, const char *what);
 // X is complex FP32, BF16 or FP16 per the plan's precision (spectrum_bytes)
 cudaError_t launch_spectrum(const kk_plan &p, const void *rf, void *X, int n_tx_rows,
                             const int32_t *tx_rows, cudaStream_t s);
-// row r of out is scaled by row_w[r] (nullable: 1)
+// row r goes to row out_row[r] of out (nullable: r) scaled by row_w[r]
+// (nullable: 1)
 cudaError_t launch_inverse(const kk_plan &p, const float2 *Y, int ncol, const int32_t *col_of_row,
-                           int nrow, float2 *out, cudaStream_t s, const float *row_w = nullptr);
+                           int nrow, float2 *out, cudaStream_t s, const float *row_w = nullptr,
+                           const int32_t *out_row = nullptr);
 cudaError_t launch_shear_f32(const kk_plan &p, const float2 *X, float2 *Y, cudaStream_t s);
 cudaError_t launch_shear_tc(const kk_plan &p, const void *X, float2 *Y, cudaStream_t s);
 size_t tc_shear_smem_bytes(int precision, int NP);

@@ -268,8 +268,14 @@ kk_status make_kk(kk_plan &p, const kk_plan_desc *d) {
   const size_t off_phase32 = blob.add(phase32);
 
   std::vector<int32_t> pair_q(P);
-  for (int q = 0; q < P; ++q)
-    pair_q[q] = tx_pos[d->pairs[2 * q]] * p.Mu + rx_pos[d->pairs[2 * q + 1]];
+  p.h_pair_tu.resize(P);
+  p.h_pair_ou.resize(P);
+  for (int q = 0; q < P; ++q) {
+    p.h_pair_tu[q] = tx_pos[d->pairs[2 * q]];
+    p.h_pair_ou[q] = rx_pos[d->pairs[2 * q + 1]];
+    pair_q[q] = p.h_pair_tu[q] * p.Mu + p.h_pair_ou[q];
+  }
+  p.h_tx_used = txu;
   const size_t off_pq = blob.add(pair_q);
 
   // gather tables, pairs stably sorted by group
@@ -311,6 +317,7 @@ kk_status make_kk(kk_plan &p, const kk_plan_desc *d) {
     std::vector<float> wv(P);
     for (int q = 0; q < P; ++q) wv[q] = (float)d->pair_weight[q];
     off_W = blob.add(wv);
+    p.h_pair_w = wv;
   }
   std::vector<int32_t> gs(p.h_group_start.begin(), p.h_group_start.end());
   const size_t off_gs = blob.add(gs);
@@ -509,15 +516,17 @@ kk_status enqueue_decompose(const kk_plan *p, const void *rf, void *rf_theta, vo
   float2 *Y = at<float2>(ws, p->ws_Y);
   cudaError_t e = launch_spectrum(*p, rf, X, p->Nu, p->t.tx_used, s);
   if (e != cudaSuccess) return cuda_fail(e, "spectrum launch");
-  e = (p->precision == KK_PREC_F32) ? launch_shear_f32(*p, (const float2 *)X, Y, s)
-                                     : launch_shear_tc(*p, X, Y, s);
+  e = launch_shear(*p, X, Y, s);
   if (e != cudaSuccess) return cuda_fail(e, "shear launch");
   e = launch_inverse(*p, Y, p->Nu * p->Mu, p->t.pair_q, p->P, (float2 *)rf_theta, s, p->t.pair_w);
   if (e != cudaSuccess) return cuda_fail(e, "inverse launch");
   return KK_OK;
 }
 
-namespace {
+cudaError_t launch_shear(const kk_plan &p, const void *X, float2 *Y, cudaStream_t s) {
+  return (p.precision == KK_PREC_F32) ? launch_shear_f32(p, (const float2 *)X, Y, s)
+                                      : launch_shear_tc(p, X, Y, s);
+}
 
 kk_status enqueue_beamform(const kk_plan *p, const void *rf_theta, void *B, float *I, void *ws, cudaStream_t s) {
   float2 *part = (p->bf_split > 1) ? at<float2>(ws, p->ws_part) : nullptr;
@@ -525,6 +534,8 @@ kk_status enqueue_beamform(const kk_plan *p, const void *rf_theta, void *B, floa
   if (e != cudaSuccess) return cuda_fail(e, "kk gather launch");
   return KK_OK;
 }
+
+namespace {
 
 kk_status enqueue_das(const kk_plan *p, const void *rf, void *B, float *I, void *ws, cudaStream_t s) {
   float2 *X = at<float2>(ws, p->ws_X);

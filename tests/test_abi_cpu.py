@@ -92,12 +92,13 @@ def test_plan_validation_is_host_side(lib):
 
 
 def test_quality_struct_layouts_match_header(tmp_path):
-    """ctypes mirrors of kkquality.h have the C compiler's sizes and offsets."""
+    """ctypes mirrors of kkquality.h and kkstream.h have the C compiler's sizes and offsets."""
     src = tmp_path / "layout.c"
     src.write_text("""
 #include <stddef.h>
 #include <stdio.h>
 #include "kkquality.h"
+#include "kkstream.h"
 #define P(T, f) printf(#T "." #f " %zu\\n", offsetof(T, f))
 int main(void) {
   printf("kk_region %zu\\nkk_target %zu\\nkk_fwhm_result %zu\\nkk_quality_desc %zu\\n",
@@ -105,6 +106,8 @@ int main(void) {
   P(kk_region, a); P(kk_region, d); P(kk_fwhm_result, peak); P(kk_fwhm_result, lateral);
   P(kk_fwhm_result, axial); P(kk_quality_desc, image_kind); P(kk_quality_desc, inside);
   P(kk_quality_desc, n_bins); P(kk_quality_desc, targets); P(kk_quality_desc, device);
+  printf("kk_stream_info %zu\\n", sizeof(kk_stream_info));
+  P(kk_stream_info, n_groups); P(kk_stream_info, events_pushed); P(kk_stream_info, device_bytes);
   return 0;
 }
 """)
@@ -123,7 +126,11 @@ int main(void) {
             "kk_quality_desc.inside": kb.kk_quality_desc.inside.offset,
             "kk_quality_desc.n_bins": kb.kk_quality_desc.n_bins.offset,
             "kk_quality_desc.targets": kb.kk_quality_desc.targets.offset,
-            "kk_quality_desc.device": kb.kk_quality_desc.device.offset}
+            "kk_quality_desc.device": kb.kk_quality_desc.device.offset,
+            "kk_stream_info": ctypes.sizeof(kb.kk_stream_info),
+            "kk_stream_info.n_groups": kb.kk_stream_info.n_groups.offset,
+            "kk_stream_info.events_pushed": kb.kk_stream_info.events_pushed.offset,
+            "kk_stream_info.device_bytes": kb.kk_stream_info.device_bytes.offset}
     assert {k: int(v) for k, v in got.items()} == want
 
 
