@@ -21,3 +21,5 @@ from .phantom import (  # noqa: F401
     LARGE_WIRES_MM, LARGE_CYSTS_MM,
 )
 from .images import speckle_images  # noqa: F401
+from .volume import (Volume, matrix_elements, tilt_grid, simulate_rf3,  # noqa: F401
+                     volume_workload)

@@ -58,6 +58,11 @@ def _load():
                 ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                 ctypes.c_int, dp, dp, dp, dp]
             lib.kks_simulate.restype = ctypes.c_int
+            lib.kks_simulate3.argtypes = [
+                ctypes.c_int, dp, dp, ctypes.c_int, dp, dp, ctypes.c_int, ctypes.c_double,
+                ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                ctypes.c_int, dp, dp, dp, dp, dp]
+            lib.kks_simulate3.restype = ctypes.c_int
             _lib = lib
     return _lib
 

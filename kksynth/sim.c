@@ -79,3 +79,65 @@ int kks_simulate(int n_tx, const double *tx_angles, int n_elem,
   free(tout);
   return 0;
 }
+
+/*
+ * Volumetric forward model for a 2D array (elements at (u_l, v_l, 0)):
+ *   tau_in  = (x_s sx_i + y_s sy_i + z_s sz_i) / c,
+ *             (sx, sy, sz) = (sin ax_i, sin ay_i, sqrt(1 - sin^2 ax_i - sin^2 ay_i))
+ *   tau_out = |r_s - (u_l, v_l, 0)| / c
+ * with the same pulse and recurrences as kks_simulate.
+ */
+int kks_simulate3(int n_tx, const double *tx_ax, const double *tx_ay, int n_elem,
+                  const double *elem_x, const double *elem_y, int T, double fs, double c,
+                  double f0, double alpha, double half_window, int n_scat, const double *px,
+                  const double *py, const double *pz, const double *amp,
+                  double *rf /* [n_tx][n_elem][T], overwritten */) {
+  if (n_tx <= 0 || n_elem <= 0 || T <= 0 || n_scat < 0) return 1;
+  for (int i = 0; i < n_tx; ++i) {
+    const double a = sin(tx_ax[i]), b = sin(tx_ay[i]);
+    if (a * a + b * b >= 1.0) return 3;
+  }
+  const double h = 1.0 / fs;
+  const double qq = exp(-2.0 * alpha * h * h);
+  const double rot_c = cos(2.0 * M_PI * f0 * h);
+  const double rot_s = sin(2.0 * M_PI * f0 * h);
+  double *tout = (double *)malloc(sizeof(double) * (size_t)n_elem * (size_t)(n_scat > 0 ? n_scat : 1));
+  if (!tout) return 2;
+#pragma omp parallel for schedule(static)
+  for (int l = 0; l < n_elem; ++l)
+    for (int s = 0; s < n_scat; ++s) {
+      const double dx = px[s] - elem_x[l], dy = py[s] - elem_y[l];
+      tout[(size_t)l * n_scat + s] = sqrt(dx * dx + dy * dy + pz[s] * pz[s]) / c;
+    }
+#pragma omp parallel for schedule(dynamic, 4)
+  for (int ch = 0; ch < n_tx * n_elem; ++ch) {
+    const int i = ch / n_elem, l = ch % n_elem;
+    const double sx = sin(tx_ax[i]), sy = sin(tx_ay[i]);
+    const double sz = sqrt(1.0 - sx * sx - sy * sy);
+    double *out = rf + (size_t)ch * T;
+    for (int n = 0; n < T; ++n) out[n] = 0.0;
+    const double *to = tout + (size_t)l * n_scat;
+    for (int s = 0; s < n_scat; ++s) {
+      const double tau = (px[s] * sx + py[s] * sy + pz[s] * sz) / c + to[s];
+      long n0 = (long)ceil((tau - half_window) * fs);
+      long n1 = (long)floor((tau + half_window) * fs);
+      if (n0 < 0) n0 = 0;
+      if (n1 > T - 1) n1 = T - 1;
+      if (n0 > n1) continue;
+      const double dt0 = (double)n0 * h - tau;
+      double g = amp[s] * exp(-alpha * dt0 * dt0);
+      double q = exp(-alpha * (2.0 * dt0 * h + h * h));
+      double er = cos(2.0 * M_PI * f0 * dt0), ei = sin(2.0 * M_PI * f0 * dt0);
+      for (long n = n0; n <= n1; ++n) {
+        out[n] += g * er;
+        g *= q;
+        q *= qq;
+        const double nr = er * rot_c - ei * rot_s;
+        ei = er * rot_s + ei * rot_c;
+        er = nr;
+      }
+    }
+  }
+  free(tout);
+  return 0;
+}

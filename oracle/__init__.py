@@ -18,6 +18,8 @@ compressive ultrasound beamforming", that it follows):
   (Eq. (compression) via the Fourier shift theorem, Section II-F), KK image
   formation (Eq. (KK)), DAS (Eq. (DAS)), compounding.
 * ``kk_oracle.c`` -- the pixel x pair loops in plain FP64 C.
+* ``volume``   -- volumetric KK and DAS with a 2D (matrix) array: plane
+  waves in three dimensions, the extension Section IV names.
 * ``quality``  -- image-quality measures the paper judges images by: gCNR of
   an inclusion against a background region and half-amplitude widths of
   point targets (Section III, Figs. 4 and 5).
@@ -26,4 +28,4 @@ Every function here is pinned by ``tests/test_oracle_*.py`` against closed
 forms, invariants, brute force or the paper's stated properties; see the test
 docstrings for which mistake each pin would catch.
 """
-from . import schemes, kk, quality  # noqa: F401
+from . import schemes, kk, quality, volume  # noqa: F401

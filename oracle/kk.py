@@ -64,6 +64,12 @@ def _load():
             lib.orc_kk_beamform.restype = ci
             lib.orc_das_beamform.argtypes = [ci, ci, ci, dp, dp, dp, dp, ci, dp, dp, cd, cd, cd, ci, dp]
             lib.orc_das_beamform.restype = ci
+            lib.orc_kk_beamform_vol.argtypes = [ci, ci, dp, dp, dp, dp, dp, dp, dp, dp, dp, ip, ci, ci,
+                                                dp, dp, dp, cd, cd, dp]
+            lib.orc_kk_beamform_vol.restype = ci
+            lib.orc_das_beamform_vol.argtypes = [ci, ci, ci, dp, dp, dp, dp, dp, dp, ci, dp, dp, dp,
+                                                 cd, cd, dp]
+            lib.orc_das_beamform_vol.restype = ci
             _lib = lib
     return _lib
 

@@ -126,3 +126,77 @@ int orc_das_beamform(int N, int L, int T, const double *y, const double *sin_i,
   }
   return 0;
 }
+
+/*
+ * Volumetric KK image formation with a 2D array: Eq. (KK) with plane waves
+ * in three dimensions (the extension to 2D arrays and volumes the paper
+ * names in Section IV):
+ *   tau_in  = (x sx_i + y sy_i + z sz_i) / c
+ *   tau_out = ((x - xref_o) sx_o + (y - yref_o) sy_o + z sz_o) / c
+ * (sx, sy, sz) is the unit propagation direction of each plane wave; xref_o,
+ * yref_o the corner of the array that keeps the receive shear a
+ * non-negative advance in each direction.
+ * y [P][T] complex; direction cosines and references [P]; group [P];
+ * pix_x, pix_y, pix_z [n_pix]; B [J][n_pix] complex (overwritten).
+ */
+int orc_kk_beamform_vol(int P, int T, const double *y, const double *sx_i, const double *sy_i,
+                        const double *sz_i, const double *sx_o, const double *sy_o,
+                        const double *sz_o, const double *xref_o, const double *yref_o,
+                        const int32_t *group, int J, int n_pix, const double *pix_x,
+                        const double *pix_y, const double *pix_z, double fs, double c,
+                        double *B) {
+  if (P < 0 || T < 2 || J < 1 || n_pix < 0) return 1;
+  for (int p = 0; p < P; ++p)
+    if (group[p] < 0 || group[p] >= J) return 2;
+#pragma omp parallel for schedule(static)
+  for (int q = 0; q < n_pix; ++q) {
+    const double x = pix_x[q], yy = pix_y[q], z = pix_z[q];
+    for (int j = 0; j < J; ++j) {
+      B[2 * ((long)j * n_pix + q)] = 0.0;
+      B[2 * ((long)j * n_pix + q) + 1] = 0.0;
+    }
+    for (int p = 0; p < P; ++p) {
+      const double tau_in = (x * sx_i[p] + yy * sy_i[p] + z * sz_i[p]) / c;
+      const double tau_out =
+          ((x - xref_o[p]) * sx_o[p] + (yy - yref_o[p]) * sy_o[p] + z * sz_o[p]) / c;
+      double re, im;
+      lerp(y + 2L * p * T, T, fs * (tau_in + tau_out), &re, &im);
+      B[2 * ((long)group[p] * n_pix + q)] += re;
+      B[2 * ((long)group[p] * n_pix + q) + 1] += im;
+    }
+  }
+  return 0;
+}
+
+/*
+ * Volumetric CPWC delay-and-sum, Eq. (DAS) with a 2D array:
+ *   B(r) = sum_{i,l} y_il( tau_in(r, i) + |r - (u_l, v_l, 0)| / c )
+ * y [N][L][T] complex analytic channel data; sx_i, sy_i, sz_i [N];
+ * elem_x, elem_y [L]; B [n_pix] complex (overwritten).
+ */
+int orc_das_beamform_vol(int N, int L, int T, const double *y, const double *sx_i,
+                         const double *sy_i, const double *sz_i, const double *elem_x,
+                         const double *elem_y, int n_pix, const double *pix_x,
+                         const double *pix_y, const double *pix_z, double fs, double c,
+                         double *B) {
+  if (N < 0 || L < 0 || T < 2 || n_pix < 0) return 1;
+#pragma omp parallel for schedule(static)
+  for (int q = 0; q < n_pix; ++q) {
+    const double x = pix_x[q], yy = pix_y[q], z = pix_z[q];
+    double accr = 0.0, acci = 0.0;
+    for (int i = 0; i < N; ++i) {
+      const double tau_in = (x * sx_i[i] + yy * sy_i[i] + z * sz_i[i]) / c;
+      for (int l = 0; l < L; ++l) {
+        const double dx = x - elem_x[l], dy = yy - elem_y[l];
+        const double tau_out = sqrt(dx * dx + dy * dy + z * z) / c;
+        double re, im;
+        lerp(y + 2L * ((long)i * L + l) * T, T, fs * (tau_in + tau_out), &re, &im);
+        accr += re;
+        acci += im;
+      }
+    }
+    B[2 * q] = accr;
+    B[2 * q + 1] = acci;
+  }
+  return 0;
+}
