@@ -467,6 +467,50 @@ def _streaming(kb, w, plan, info, groups=(5, 15, 25, 75), frames=40, warm=3):
     return res
 
 
+def _volume(kb, flush, n_sm, peaks, peak_src, reps=10):
+    """Volumetric KK with a 32 x 32 matrix array (1024 elements, 0.3 mm pitch):
+    5 x 5 transmit tilts over +-10 deg, int16 records of 2048 samples (30 dB),
+    7 x 7 receive waves evenly over +-14 deg (1225 pairs), a 128 x 128 x 160
+    voxel grid at 0.15 mm from 5 mm depth.  FP32 decomposition (1024
+    elements: beyond the tensor-core forms), volumes/s and voxel-pairs/s of
+    the image formation against the same shared-memory gather roofline as
+    the 2D frame."""
+    import numpy as np
+    import kksynth
+    w = kksynth.volume_workload(seed=3500, lx=32, ly=32, pitch=0.3e-3, ntx=5, nty=5, theta_max_deg=10.0,
+                                n_samples=2048, nx=128, ny=128, nz=160, dxyz=0.15e-3, z0=5e-3,
+                                points=((0.0, 0.0, 12e-3), (-4e-3, 3e-3, 18e-3), (5e-3, -2e-3, 24e-3)),
+                                speckle=3000, rf_dtype="i16")
+    rx1 = np.deg2rad(np.linspace(-14.0, 14.0, 7))
+    rxx, rxy = np.tile(rx1, 7), np.repeat(rx1, 7)
+    pairs = np.array([(i, o) for i in range(w.n_tx) for o in range(49)], dtype=np.int32)
+    plan = kb.Plan(w.elem_x, w.tx_ax, w.grid, w.c, w.fs, w.n_samples, kb.KK_RF_I16, rx_angles=rxx, pairs=pairs,
+                   compound=kb.KK_COMPOUND_COHERENT, elem_y=w.elem_y, tx_angles_y=w.tx_ay, rx_angles_y=rxy,
+                   grid_y=w.grid_y)
+    info = plan.info
+    import torch
+    d_rf = torch.from_numpy(w.rf).cuda()
+    ws, rt, B, I = plan.empty_workspace(), plan.empty_rf_theta(), plan.empty_image(), plan.empty_intensity()
+    for _ in range(3):
+        plan.decompose(d_rf, rt, ws)
+        plan.beamform(rt, B, I, ws)
+    torch.cuda.synchronize()
+    ms_dec = _time_loop(lambda: plan.decompose(d_rf, rt, ws), reps, flush)
+    ms_bf = _time_loop(lambda: plan.beamform(rt, B, I, ws), reps, flush)
+    vp = float(info.n_pairs) * info.nx * info.nz * info.ny
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    peak_pp = 8.0 * n_sm * sm_max * 1e6 / 1e9
+    ach = vp / (ms_bf / 1e3) / 1e9
+    res = {"array": "32x32", "transmits": int(info.n_tx), "receive_waves": int(info.n_rx_used),
+           "pairs": int(info.n_pairs), "voxels": [int(info.nx), int(info.ny), int(info.nz)], "samples": int(info.n_samples),
+           "volumes_per_s": round(1e3 / (ms_dec + ms_bf), 2), "decompose_ms": round(ms_dec, 4),
+           "kk_image_ms": round(ms_bf, 4), "gvoxel_pairs_per_s": round(ach, 1),
+           "gather_frac_of_8pp_per_clk_sm": round(ach / peak_pp, 4),
+           "compression": round(info.compression_factor, 2), "status": plan.status()}
+    del plan, d_rf, ws, rt, B, I
+    return res
+
+
 def _form_plan(kb, w, rx, pairs, prec_name, local):
     return kb.Plan(w.elem_x, w.tx_angles, w.grid, w.c, w.fs, w.n_samples, kb.KK_RF_I16,
                    rx_angles=rx, pairs=pairs, compound=kb.KK_COMPOUND_COHERENT,
@@ -647,6 +691,8 @@ def run_ours(args):
         side["image_quality"] = _quality(kb, w, {"kk_75x128": I, "kk_vernier_8x16": vI, "das_75x128": dI},
                                          flush, peaks, peak_src)
         side["streaming"] = _streaming(kb, w, plan, info)
+        torch.cuda.empty_cache()
+        side["volume"] = _volume(kb, flush, n_sm, peaks, peak_src)
         torch.cuda.empty_cache()
         # batched form: 256 frames of uneven size, one CUDA graph
         if not args.no_batch:

@@ -122,6 +122,22 @@ typedef struct kk_plan_desc {
                                  (x, z) when |x - u_l| <= z / (2 f_number),
                                  weighted by `aperture`; <= 0 = full aperture */
   int32_t aperture;           /* kk_aperture window over that half-width */
+  /* Volumetric imaging with a 2D (matrix) array, the extension Section IV
+   * names (KK only; all NULL / 0 = a linear array and a 2D grid).  Element l
+   * sits at (elem_x[l], elem_y[l], 0).  A plane wave with tilts (ax, ay)
+   * travels along (sin ax, sin ay, sqrt(1 - sin^2 ax - sin^2 ay)) and passes
+   * the origin at t = 0 (ax is tx_angles / rx_angles, ay the arrays below);
+   * every used angle needs sin^2 ax + sin^2 ay < sin^2(80 deg).  The receive
+   * shear of Eq. (compression) is ((xr - u_l) sx + (yr - v_l) sy) / c with
+   * xr, yr the array edges that keep each term a non-negative advance.
+   * Voxel (ix, iy, iz) sits at (x0 + ix dx, y0 + iy dy, z0 + iz dz); B is
+   * [J][ny][nz][nx] and I [ny][nz][nx].  Set any of these to make a plan
+   * volumetric. */
+  const double *elem_y;       /* [L] element y positions (NULL = 0) */
+  const double *tx_angles_y;  /* [N] transmit tilts ay (NULL = 0) */
+  const double *rx_angles_y;  /* [n_rx] receive tilts ay (NULL = 0) */
+  int32_t ny;                 /* y slices (<= 1: one slice at y0) */
+  double y0, dy;              /* dy > 0 when ny > 1 */
 } kk_plan_desc;
 
 typedef struct kk_plan kk_plan;
@@ -136,11 +152,13 @@ typedef struct kk_plan_info {
   size_t workspace_bytes;                  /* for kk_decompose/kk_beamform/das_beamform */
   size_t rf_bytes;                         /* N*L*T*sizeof(sample) */
   size_t rf_theta_bytes;                   /* P*T*8 */
-  size_t image_bytes;                      /* J*nz*nx*8 (B) */
-  size_t intensity_bytes;                  /* nz*nx*4 (I) */
+  size_t image_bytes;                      /* J*ny*nz*nx*8 (B) */
+  size_t intensity_bytes;                  /* ny*nz*nx*4 (I) */
   double compression_factor;               /* L / (number of receive angles in use) */
   int32_t launches_decompose;              /* kernels one kk_decompose enqueues */
   int32_t launches_beamform;               /* kernels one kk_beamform / das_beamform enqueues */
+  int32_t ny;                              /* y slices (1 for a 2D grid) */
+  int32_t is_volume;                       /* a volumetric plan (2D array or y slices) */
 } kk_plan_info;
 
 /*
@@ -278,7 +296,8 @@ kk_status das_beamform(const kk_plan *p, const void *d_rf, void *d_B,
  * {2, 4, 8}, stage in {4, 8, 16}) sets it.  Results match the per-frame calls
  * up to FP32 summation order.  The buffers given here are baked into the
  * graph: refill them in place between runs.  Each frame needs its own
- * workspace (frames run concurrently).
+ * workspace (frames run concurrently).  Volumetric plans are not accepted
+ * (KK_ERR_UNSUPPORTED).
  *
  * kk_batch_run enqueues the graph on `stream`.  A batch must not run twice
  * concurrently (it owns one work counter).

@@ -75,7 +75,9 @@ class kk_plan_desc(ctypes.Structure):
                 ("c", ctypes.c_double), ("fs", ctypes.c_double),
                 ("n_samples", ctypes.c_int32), ("rf_dtype", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("device", ctypes.c_int32),
-                ("pair_weight", _dp), ("f_number", ctypes.c_double), ("aperture", ctypes.c_int32)]
+                ("pair_weight", _dp), ("f_number", ctypes.c_double), ("aperture", ctypes.c_int32),
+                ("elem_y", _dp), ("tx_angles_y", _dp), ("rx_angles_y", _dp), ("ny", ctypes.c_int32),
+                ("y0", ctypes.c_double), ("dy", ctypes.c_double)]
 
 
 class kk_plan_info(ctypes.Structure):
@@ -87,7 +89,8 @@ class kk_plan_info(ctypes.Structure):
                 ("workspace_bytes", ctypes.c_size_t), ("rf_bytes", ctypes.c_size_t),
                 ("rf_theta_bytes", ctypes.c_size_t), ("image_bytes", ctypes.c_size_t),
                 ("intensity_bytes", ctypes.c_size_t), ("compression_factor", ctypes.c_double),
-                ("launches_decompose", ctypes.c_int32), ("launches_beamform", ctypes.c_int32)]
+                ("launches_decompose", ctypes.c_int32), ("launches_beamform", ctypes.c_int32),
+                ("ny", ctypes.c_int32), ("is_volume", ctypes.c_int32)]
 
 
 class kk_batch_frame(ctypes.Structure):
@@ -281,7 +284,8 @@ def kk_scheme_angles(kind: int, n_tx: int, dtheta: float, M: int, j: float = 0.0
 
 def _desc(elem_x, tx_angles, grid, c, fs, n_samples, rf_dtype, rx_angles=None, pairs=None,
           group_of_pair=None, n_groups=1, compound=KK_COMPOUND_NONE, precision=KK_PREC_F32,
-          device=0, pair_weight=None, f_number=0.0, aperture=KK_APERTURE_BOXCAR):
+          device=0, pair_weight=None, f_number=0.0, aperture=KK_APERTURE_BOXCAR, elem_y=None,
+          tx_angles_y=None, rx_angles_y=None, grid_y=None):
     keep = []
     ex = _f64(elem_x); keep.append(ex)
     tx = _f64(tx_angles); keep.append(tx)
@@ -315,6 +319,12 @@ def _desc(elem_x, tx_angles, grid, c, fs, n_samples, rf_dtype, rx_angles=None, p
         d.pair_weight = pw.ctypes.data_as(_dp)
     d.f_number = float(f_number)
     d.aperture = int(aperture)
+    for name, arr in (("elem_y", elem_y), ("tx_angles_y", tx_angles_y), ("rx_angles_y", rx_angles_y)):
+        if arr is not None:
+            a = _f64(arr); keep.append(a)
+            setattr(d, name, a.ctypes.data_as(_dp))
+    if grid_y is not None:
+        d.ny, d.y0, d.dy = int(grid_y[0]), float(grid_y[1]), float(grid_y[2])
     return d, keep
 
 
@@ -401,10 +411,15 @@ class Plan:
     def __init__(self, elem_x, tx_angles, grid, c, fs, n_samples, rf_dtype=KK_RF_F32,
                  rx_angles=None, pairs=None, group_of_pair=None, n_groups=1,
                  compound=KK_COMPOUND_NONE, precision=KK_PREC_F32, device=0, das=False,
-                 pair_weight=None, f_number=0.0, aperture=KK_APERTURE_BOXCAR):
+                 pair_weight=None, f_number=0.0, aperture=KK_APERTURE_BOXCAR, elem_y=None,
+                 tx_angles_y=None, rx_angles_y=None, grid_y=None):
+        """Volumetric plans (2D array, tilts about both axes, y slices): give
+        elem_y, tx_angles_y, rx_angles_y and grid_y = (ny, y0, dy); images are
+        then [J][ny][nz][nx] and intensities [ny][nz][nx]."""
         self.desc, self._keep = _desc(elem_x, tx_angles, grid, c, fs, n_samples, rf_dtype,
                                       rx_angles, pairs, group_of_pair, n_groups, compound,
-                                      precision, device, pair_weight, f_number, aperture)
+                                      precision, device, pair_weight, f_number, aperture, elem_y,
+                                      tx_angles_y, rx_angles_y, grid_y)
         self.handle = das_plan_create(self.desc) if das else kk_plan_create(self.desc)
         self.info = kk_plan_get_info(self.handle)
         self.is_das = das
@@ -433,13 +448,15 @@ class Plan:
     def empty_image(self):
         import torch
         J = 1 if self.is_das else self.info.n_groups
-        return torch.empty((J, self.info.nz, self.info.nx, 2), dtype=torch.float32,
-                           device=f"cuda:{self.device}")
+        shape = ((J, self.info.ny, self.info.nz, self.info.nx, 2) if self.info.is_volume
+                 else (J, self.info.nz, self.info.nx, 2))
+        return torch.empty(shape, dtype=torch.float32, device=f"cuda:{self.device}")
 
     def empty_intensity(self):
         import torch
-        return torch.empty((self.info.nz, self.info.nx), dtype=torch.float32,
-                           device=f"cuda:{self.device}")
+        shape = ((self.info.ny, self.info.nz, self.info.nx) if self.info.is_volume
+                 else (self.info.nz, self.info.nx))
+        return torch.empty(shape, dtype=torch.float32, device=f"cuda:{self.device}")
 
     def set_gather(self, rows: int, stage: int):
         kk_plan_set_gather(self.handle, rows, stage)

@@ -240,6 +240,7 @@ kk_status kk_batch_create(kk_batch **out, const kk_batch_frame *frames, int32_t 
   for (int f = 0; f < n_frames; ++f) {
     const kk_batch_frame &fr = frames[f];
     if (!fr.plan || fr.plan->is_das) { set_error("every frame needs a KK plan"); return KK_ERR_INVALID_ARG; }
+    if (fr.plan->vol) { set_error("volumetric plans are not supported in the batched form"); return KK_ERR_UNSUPPORTED; }
     if (fr.plan->device != device) { set_error("all plans must live on one device"); return KK_ERR_INVALID_ARG; }
     if (!fr.d_rf || !fr.d_rf_theta || !fr.d_B || !fr.d_workspace) { set_error("null frame buffer"); return KK_ERR_INVALID_ARG; }
     if (fr.plan->compound != KK_COMPOUND_NONE && !fr.d_I) { set_error("compound mode set but I is null"); return KK_ERR_INVALID_ARG; }

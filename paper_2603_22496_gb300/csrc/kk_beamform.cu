@@ -28,6 +28,8 @@
 // Index bound: with W0 = floor(min_tile s) - 1 and a staged window of
 // win >= span + 4 entries (span = |A| 31 + B (TZ - 1)), every read index lies
 // in [0, win).
+#include <type_traits>
+
 #include "kk_internal.h"
 
 namespace kk {
@@ -54,6 +56,11 @@ struct __align__(8) PairIn {
   int pad;
 };
 
+// volumetric plans: also the 32.32 delay per y slice
+struct __align__(8) PairInVol : PairIn {
+  long long Y;
+};
+
 __device__ __forceinline__ void cp_async4(void *smem_dst, const void *gsrc) {
   const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gsrc) : "memory");
@@ -68,18 +75,22 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 __device__ __forceinline__ float2 f2add(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 
 // Per-pair state of the delay tables, double-buffered by stage.
-template <int STAGE>
+template <int STAGE, bool VOL = false>
 struct GatherSmem {
   WarpPair wp[2][4][STAGE];
   PairSrc src[2][STAGE];
-  PairIn in[2][STAGE];
+  typename std::conditional<VOL, PairInVol, PairIn>::type in[2][STAGE];
 };
 
 // One tile (and pair slice) of KK image formation; shared by the per-plan
-// kernel and the batched persistent kernel.
-template <int ROWS, int STAGE, int NPT, bool MULTI>
+// kernel and the batched persistent kernel.  VOL: the tile index also runs
+// over y slices (slice = tile / tiles_xz); every delay gains the pair's
+// per-slice term Y * slice, and the slice is one [nz][nx] plane of the
+// [J][ny][nz][nx] output (of the [ny][nz][nx] intensity).
+template <int ROWS, int STAGE, int NPT, bool MULTI, bool VOL = false>
 __device__ __forceinline__ void gather_tile(const GatherArgs &a, int tile, int sidx, float4 *sw,
-                                            GatherSmem<STAGE> &sm) {
+                                            GatherSmem<STAGE, VOL> &sm,
+                                            const GatherVolArgs *va = nullptr) {
   const float2 *__restrict__ rf_theta = a.rf_theta;
   const int T = a.T;
   const int32_t *__restrict__ bf_row = a.bf_row;
@@ -93,6 +104,15 @@ __device__ __forceinline__ void gather_tile(const GatherArgs &a, int tile, int s
   float2 *__restrict__ out = a.out;
   float *__restrict__ I = a.I;
   const int compound = a.compound;
+  // volumetric plans: slice of this tile and its per-pair delay term
+  [[maybe_unused]] long long vol_slice = 0;
+  if constexpr (VOL) {
+    const int sl = tile / va->tiles_xz;
+    tile -= sl * va->tiles_xz;
+    vol_slice = sl;
+    out += (size_t)sl * nx * nz;          // plane `sl` of each [ny][nz][nx] image
+    if (I != nullptr) I += (size_t)sl * nx * nz;
+  }
   auto &s_wp = sm.wp;
   auto &s_src = sm.src;
   auto &s_in = sm.in;
@@ -147,10 +167,11 @@ __device__ __forceinline__ void gather_tile(const GatherArgs &a, int tile, int s
 #define KK_FETCH(P0, NS, B_)                           \
   if (tw == 0 && tj < (NS)) {                          \
     const int p_ = (P0) + tj;                          \
-    PairIn *d_ = &s_in[B_][tj];                        \
+    auto *d_ = &s_in[B_][tj];                          \
     cp_async8(&d_->A, bfA + p_);                       \
     cp_async8(&d_->B, bfB + p_);                       \
     cp_async8(&d_->C, bfC + p_);                       \
+    if constexpr (VOL) cp_async8(&d_->Y, va->bfY + p_); \
     cp_async4(&d_->af, bfAf + p_);                     \
     cp_async4(&d_->bf, bfBf + p_);                     \
     cp_async4(&d_->row, bf_row + p_);                  \
@@ -159,7 +180,8 @@ __device__ __forceinline__ void gather_tile(const GatherArgs &a, int tile, int s
   // tables of a stage (NS pairs, inputs in s_in[B_]) into buffer B_
 #define KK_TABLES(NS, B_)                                                                        \
   if (tj < (NS)) {                                                                               \
-    const PairIn in = s_in[B_][tj];                                                              \
+    auto in = s_in[B_][tj];                                                                      \
+    if constexpr (VOL) in.C += in.Y * vol_slice;                                                 \
     const long long smin = in.C + in.B * (long long)iz0 +                                        \
                            in.A * (long long)(in.A >= 0 ? ix0 : ix0 + kTileX - 1);               \
     const int w0 = (int)(smin >> 32) - 1;                                                        \
@@ -240,7 +262,7 @@ __device__ __forceinline__ void gather_tile(const GatherArgs &a, int tile, int s
     if (nxt_g < J) { KK_LOAD_RAW(nxt_n, buf ^ 1); }  // in flight during the gathers
 
     while (gw < cur_g) {
-      float2 *dst = out + ((size_t)sidx * J + gw) * (size_t)nx * nz;
+      float2 *dst = out + ((size_t)sidx * J + gw) * (size_t)nx * nz * (VOL ? va->ny : 1);
 #pragma unroll
       for (int r = 0; r < ROWS; ++r) {
         const int iz = izb + r;
@@ -286,7 +308,7 @@ __device__ __forceinline__ void gather_tile(const GatherArgs &a, int tile, int s
 #undef KK_TABLES
 #undef KK_LOAD_RAW
   while (gw < J) {
-    float2 *dst = out + ((size_t)sidx * J + gw) * (size_t)nx * nz;
+    float2 *dst = out + ((size_t)sidx * J + gw) * (size_t)nx * nz * (VOL ? va->ny : 1);
 #pragma unroll
     for (int r = 0; r < ROWS; ++r) {
       const int iz = izb + r;
@@ -322,6 +344,15 @@ __global__ void __launch_bounds__(kGatherThreads, MINB) k_kk_gather(const Gather
   extern __shared__ float4 sw[];  // [STAGE][win] staged entries
   __shared__ GatherSmem<STAGE> sm;
   gather_tile<ROWS, STAGE, NPT, MULTI>(a, blockIdx.x, blockIdx.y, sw, sm);
+}
+
+// Volumetric plans: tiles of every y slice in one grid.
+template <int ROWS, int STAGE, int NPT, int MINB, bool MULTI>
+__global__ void __launch_bounds__(kGatherThreads, MINB)
+    k_kk_gather_vol(const GatherArgs a, const GatherVolArgs v) {
+  extern __shared__ float4 sw[];
+  __shared__ GatherSmem<STAGE, true> sm;
+  gather_tile<ROWS, STAGE, NPT, MULTI, true>(a, blockIdx.x, blockIdx.y, sw, sm, &v);
 }
 
 // Batched form: a persistent grid pulls (frame, tile) work items, largest
@@ -368,13 +399,21 @@ cudaError_t launch_cfg(const kk_plan &p, const float2 *rf_theta, float2 *dst, fl
                        cudaStream_t s) {
   // registers held to 64 for ROWS <= 4 (8 CTAs of 128 threads per SM) and
   // to 102 for ROWS = 8 (5 CTAs)
-  auto k = (p.J > 1) ? k_kk_gather<ROWS, STAGE, NPT, (ROWS <= 4 ? 7 : 5), true>
-                     : k_kk_gather<ROWS, STAGE, NPT, (ROWS <= 4 ? 7 : 5), false>;
+  constexpr int MB = ROWS <= 4 ? 7 : 5;
   const size_t smem = sizeof(float4) * (size_t)STAGE * p.bf_win;
-  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  const dim3 grid(p.tiles_x * p.tiles_z, p.bf_split);
-  k<<<grid, kGatherThreads, smem, s>>>(gather_args(p, rf_theta, dst, I));
+  const dim3 grid(p.tiles_x * p.tiles_z * p.ny, p.bf_split);
+  cudaError_t e;
+  if (p.vol) {
+    auto k = (p.J > 1) ? k_kk_gather_vol<ROWS, STAGE, NPT, MB, true> : k_kk_gather_vol<ROWS, STAGE, NPT, MB, false>;
+    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k<<<grid, kGatherThreads, smem, s>>>(gather_args(p, rf_theta, dst, I), gather_vol_args(p));
+  } else {
+    auto k = (p.J > 1) ? k_kk_gather<ROWS, STAGE, NPT, MB, true> : k_kk_gather<ROWS, STAGE, NPT, MB, false>;
+    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k<<<grid, kGatherThreads, smem, s>>>(gather_args(p, rf_theta, dst, I));
+  }
   return cudaGetLastError();
 }
 
@@ -423,6 +462,14 @@ GatherArgs gather_args(const kk_plan &p, const float2 *rf_theta, float2 *dst, fl
   a.I = I;
   a.compound = p.compound;
   return a;
+}
+
+GatherVolArgs gather_vol_args(const kk_plan &p) {
+  GatherVolArgs v;
+  v.bfY = p.t.bf_Y;
+  v.ny = p.ny;
+  v.tiles_xz = p.tiles_x * p.tiles_z;
+  return v;
 }
 
 template <int ROWS, int STAGE, int NPT>
@@ -502,7 +549,7 @@ cudaError_t launch_kk_gather(const kk_plan &p, const float2 *rf_theta, float2 *B
     default: return cudaErrorInvalidConfiguration;
   }
   if (e != cudaSuccess || p.bf_split == 1) return e;
-  const int npix = p.grid.nx * p.grid.nz;
+  const int npix = p.grid.nx * p.grid.nz * p.ny;
   k_kk_reduce<<<(npix + 255) / 256, 256, 0, s>>>(partial, p.bf_split, p.J, npix, B, I, p.compound);
   return cudaGetLastError();
 }

@@ -52,6 +52,7 @@ struct DevTables {
   // KK gather (pairs in group-sorted order)
   int32_t *bf_row = nullptr;           // [P] row of rf_theta
   long long *bf_A = nullptr, *bf_B = nullptr, *bf_C = nullptr; // 32.32 samples
+  long long *bf_Y = nullptr;           // [P] 32.32 samples per y slice (volumetric)
   float *bf_Af = nullptr, *bf_Bf = nullptr;                    // samples per pixel
   float *pair_w = nullptr;             // [P] pair weights, caller's order (null: all 1)
   int32_t *group_start = nullptr;      // [J+1]
@@ -102,6 +103,11 @@ struct kk_plan {
   // DAS receive aperture: 2 F (0 = full aperture) and window (kk_aperture)
   float das_two_f = 0.f;
   int das_window = KK_APERTURE_BOXCAR;
+  // volumetric plan: ny y-slices at y0 + iy dy, per-pair y slope of the
+  // delay in bf_Y (32.32 samples per slice)
+  bool vol = false;
+  int ny = 1;
+  double y0 = 0, dy = 0;
 };
 
 namespace kk {
@@ -126,6 +132,13 @@ struct GatherArgs {
   float2 *out;
   float *I;
   int compound;
+};
+
+// Extra arguments of the volumetric gather (a second kernel parameter, so the
+// linear-array kernel's argument block stays as it is).
+struct GatherVolArgs {
+  const long long *bfY;  // per-pair delay per y slice (32.32 samples)
+  int ny, tiles_xz;      // y slices and tiles per slice
 };
 
 // Keeps the caller's current device and restores it on exit.
@@ -165,6 +178,7 @@ inline int spectrum_bytes(int precision) { return precision == KK_PREC_F32 ? 8 :
 cudaError_t launch_kk_gather(const kk_plan &p, const float2 *rf_theta, float2 *B, float *I,
                              float2 *partial, cudaStream_t s);
 GatherArgs gather_args(const kk_plan &p, const float2 *rf_theta, float2 *dst, float *I);
+GatherVolArgs gather_vol_args(const kk_plan &p);
 // persistent gather over n_items (frame, tile) items; *counter must be 0
 cudaError_t launch_kk_gather_batch(int rows, int stage, const GatherArgs *frames, const int2 *items,
                                    int n_items, int *counter, int max_win, int grid,

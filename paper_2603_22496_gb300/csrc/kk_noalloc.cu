@@ -60,7 +60,7 @@ extern "C" kk_status kk_beamform_noalloc(const kk_plan *p, const void *d_rf_thet
   if (p->compound != KK_COMPOUND_NONE && !d_I) { set_error("compound mode set but I is null"); return KK_ERR_INVALID_ARG; }
   if ((uintptr_t)d_rf_theta % 16) { set_error("rf_theta must be 16-byte aligned"); return KK_ERR_INVALID_ARG; }
   const size_t need = (p->bf_split > 1)
-                          ? sizeof(float2) * (size_t)p->bf_split * p->J * p->grid.nx * p->grid.nz
+                          ? sizeof(float2) * (size_t)p->bf_split * p->J * p->grid.nx * p->grid.nz * p->ny
                           : 0;
   if (need > kNoAllocScratchBytes) {
     set_error("plan needs " + std::to_string(need) + " bytes of partial images; the no-allocation "

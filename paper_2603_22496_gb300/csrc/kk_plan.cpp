@@ -78,6 +78,31 @@ T *at(void *base, size_t off) {
   return reinterpret_cast<T *>(static_cast<unsigned char *>(base) + off);
 }
 
+bool is_volume(const kk_plan_desc *d) {
+  return d->elem_y || d->tx_angles_y || d->rx_angles_y || d->ny > 1 || d->y0 != 0.0;
+}
+
+// a plane wave (ax, ay) must propagate: sin^2 ax + sin^2 ay below sin^2(80 deg)
+bool tilt_ok(double ax, double ay) {
+  if (!std::isfinite(ax) || !std::isfinite(ay)) return false;
+  const double sx = std::sin(ax), sy = std::sin(ay), m = std::sin(kMaxAngle);
+  return sx * sx + sy * sy < m * m;
+}
+
+// unit propagation vector of a plane wave; a linear-array plan keeps
+// (sin ax, 0, cos ax)
+void direction(bool vol, double ax, double ay, double &sx, double &sy, double &sz) {
+  if (!vol) {
+    sx = std::sin(ax);
+    sy = 0.0;
+    sz = std::cos(ax);
+    return;
+  }
+  sx = std::sin(ax);
+  sy = std::sin(ay);
+  sz = std::sqrt(1.0 - sx * sx - sy * sy);
+}
+
 kk_status validate_common(const kk_plan_desc *d) {
   if (!d) { set_error("null plan description"); return KK_ERR_INVALID_ARG; }
   if (d->n_elem < 1 || !d->elem_x) { set_error("n_elem < 1 or elem_x null"); return KK_ERR_INVALID_ARG; }
@@ -100,6 +125,32 @@ kk_status validate_common(const kk_plan_desc *d) {
   for (int l = 0; l < d->n_elem; ++l) umax = std::max(umax, std::fabs(d->elem_x[l]));
   const double smax = d->fs / d->c * (2 * (xmax + umax) + 2 * zmax);
   if (smax > 1e6) { set_error("geometry gives delays beyond 1e6 samples"); return KK_ERR_INVALID_ARG; }
+  if (is_volume(d)) {
+    if (d->ny > 8192 || (long long)std::max(d->ny, 1) * g.nx * g.nz > (1ll << 31)) {
+      set_error("volume size out of range (ny <= 8192, at most 2^31 voxels)");
+      return KK_ERR_INVALID_ARG;
+    }
+    if (!std::isfinite(d->y0) || (d->ny > 1 && !(d->dy > 0 && std::isfinite(d->dy)))) {
+      set_error("volume needs a finite y0 and dy > 0 when ny > 1");
+      return KK_ERR_INVALID_ARG;
+    }
+    double vmax = 0;
+    if (d->elem_y)
+      for (int l = 0; l < d->n_elem; ++l) {
+        if (!std::isfinite(d->elem_y[l])) { set_error("non-finite element y position"); return KK_ERR_INVALID_ARG; }
+        vmax = std::max(vmax, std::fabs(d->elem_y[l]));
+      }
+    for (int i = 0; i < d->n_tx; ++i)
+      if (!tilt_ok(d->tx_angles[i], d->tx_angles_y ? d->tx_angles_y[i] : 0.0)) {
+        set_error("transmit tilts beyond sin^2 ax + sin^2 ay < sin^2(80 deg)");
+        return KK_ERR_INVALID_ARG;
+      }
+    const double ymax = std::fabs(d->y0) + (d->ny > 1 ? d->dy * (d->ny + 64) : 0.0);
+    if (d->fs / d->c * (2 * (xmax + umax) + 2 * (ymax + vmax) + 2 * zmax) > 1e6) {
+      set_error("geometry gives delays beyond 1e6 samples");
+      return KK_ERR_INVALID_ARG;
+    }
+  }
   int dev_count = 0;
   if (cudaGetDeviceCount(&dev_count) != cudaSuccess || d->device < 0 || d->device >= dev_count) {
     set_error("device ordinal not available");
@@ -154,7 +205,7 @@ int gather_split(const kk_plan &p, int rows, int stage) {
   const int tz = 4 * rows;
   int sms = 148;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p.device);
-  const int tiles = ((p.grid.nx + kTileX - 1) / kTileX) * ((p.grid.nz + tz - 1) / tz);
+  const int tiles = ((p.grid.nx + kTileX - 1) / kTileX) * ((p.grid.nz + tz - 1) / tz) * p.ny;
   const int split = (4 * sms + tiles - 1) / tiles;
   const int max_by_pairs = std::max(1, (p.P / p.J) / (2 * stage));
   return std::max(1, std::min(split, max_by_pairs));
@@ -202,6 +253,12 @@ kk_status make_kk(kk_plan &p, const kk_plan_desc *d) {
   if (d->precision < KK_PREC_F32 || d->precision > KK_PREC_F8E4M3) { set_error("bad precision"); return KK_ERR_INVALID_ARG; }
   for (int o = 0; o < d->n_rx; ++o)
     if (!(std::fabs(d->rx_angles[o]) < kMaxAngle)) { set_error("receive angle out of range (|theta| < 80 deg)"); return KK_ERR_INVALID_ARG; }
+  if (p.vol)
+    for (int o = 0; o < d->n_rx; ++o)
+      if (!tilt_ok(d->rx_angles[o], d->rx_angles_y ? d->rx_angles_y[o] : 0.0)) {
+        set_error("receive tilts beyond sin^2 ax + sin^2 ay < sin^2(80 deg)");
+        return KK_ERR_INVALID_ARG;
+      }
   const int P = d->n_pairs, J = d->n_groups;
   std::vector<int> gp(P, 0);
   for (int q = 0; q < P; ++q) {
@@ -252,11 +309,25 @@ kk_status make_kk(kk_plan &p, const kk_plan_desc *d) {
 
   // shear phases: frac(fs delta_l(theta_o) / T), delta = (x_ref - u_l) sin(theta_o) / c
   std::vector<unsigned long long> phase((size_t)p.Mu * p.L);
+  std::vector<double> v(p.L, 0.0);
+  if (d->elem_y) v.assign(d->elem_y, d->elem_y + p.L);
+  auto rx_y = [&](int o) { return d->rx_angles_y ? d->rx_angles_y[o] : 0.0; };
+  auto tx_y = [&](int i) { return d->tx_angles_y ? d->tx_angles_y[i] : 0.0; };
   for (int a = 0; a < p.Mu; ++a) {
     const double th = d->rx_angles[rx_used[a]];
     const double xr = shear_reference(u, th);
+    if (!p.vol) {
+      for (int l = 0; l < p.L; ++l) {
+        const double D = d->fs * (xr - u[l]) * std::sin(th) / d->c;  // samples
+        phase[(size_t)a * p.L + l] = frac64(D / (double)p.T);
+      }
+      continue;
+    }
+    double sx, sy, sz;
+    direction(true, th, rx_y(rx_used[a]), sx, sy, sz);
+    const double yr = shear_reference(v, sy);
     for (int l = 0; l < p.L; ++l) {
-      const double D = d->fs * (xr - u[l]) * std::sin(th) / d->c;  // samples
+      const double D = d->fs * ((xr - u[l]) * sx + (yr - v[l]) * sy) / d->c;  // samples
       phase[(size_t)a * p.L + l] = frac64(D / (double)p.T);
     }
   }
@@ -286,7 +357,7 @@ kk_status make_kk(kk_plan &p, const kk_plan_desc *d) {
   for (int q = 0; q < P; ++q) p.h_group_start[gp[q] + 1]++;
   for (int g = 0; g < J; ++g) p.h_group_start[g + 1] += p.h_group_start[g];
   std::vector<int32_t> row(P);
-  std::vector<long long> A(P), Bv(P), C(P);
+  std::vector<long long> A(P), Bv(P), C(P), Yv(p.vol ? P : 0);
   std::vector<float> Af(P), Bf(P);
   const kk_grid &g = p.grid;
   const double k_s = d->fs / d->c;
@@ -296,11 +367,23 @@ kk_status make_kk(kk_plan &p, const kk_plan_desc *d) {
     const double ti = d->tx_angles[d->pairs[2 * q]];
     const double to = d->rx_angles[d->pairs[2 * q + 1]];
     const double xr = shear_reference(u, to);
-    const double sx = std::sin(ti) + std::sin(to);
-    const double cz = std::cos(ti) + std::cos(to);
-    const double a = k_s * g.dx * sx;
-    const double b = k_s * g.dz * cz;
-    const double c0 = k_s * (g.x0 * sx + g.z0 * cz - xr * std::sin(to));
+    double a, b, c0;
+    if (!p.vol) {
+      const double sx = std::sin(ti) + std::sin(to);
+      const double cz = std::cos(ti) + std::cos(to);
+      a = k_s * g.dx * sx;
+      b = k_s * g.dz * cz;
+      c0 = k_s * (g.x0 * sx + g.z0 * cz - xr * std::sin(to));
+    } else {
+      double ix, iy, iz, ox, oy, oz;
+      direction(true, ti, tx_y(d->pairs[2 * q]), ix, iy, iz);
+      direction(true, to, rx_y(d->pairs[2 * q + 1]), ox, oy, oz);
+      const double yr = shear_reference(v, oy);
+      a = k_s * g.dx * (ix + ox);
+      b = k_s * g.dz * (iz + oz);
+      c0 = k_s * (g.x0 * (ix + ox) + p.y0 * (iy + oy) + g.z0 * (iz + oz) - xr * ox - yr * oy);
+      Yv[s] = to_fixed32(k_s * p.dy * (iy + oy));
+    }
     row[s] = q;
     p.h_bfA.push_back(a);
     p.h_bfB.push_back(b);
@@ -312,6 +395,7 @@ kk_status make_kk(kk_plan &p, const kk_plan_desc *d) {
   }
   const size_t off_row = blob.add(row), off_A = blob.add(A), off_B = blob.add(Bv), off_C = blob.add(C);
   const size_t off_Af = blob.add(Af), off_Bf = blob.add(Bf);
+  const size_t off_Y = p.vol ? blob.add(Yv) : 0;
   size_t off_W = 0;
   if (d->pair_weight) {  // caller's pair order: rows of rf_theta
     std::vector<float> wv(P);
@@ -342,7 +426,9 @@ kk_status make_kk(kk_plan &p, const kk_plan_desc *d) {
   int max_split = 1;
   for (int rows : {2, 4, 8})
     for (int stage : {4, 8, 16}) max_split = std::max(max_split, gather_split(p, rows, stage));
-  p.ws_total = max_split > 1 ? align_up(off + sizeof(float2) * (size_t)max_split * p.J * p.grid.nx * p.grid.nz) : off;
+  p.ws_total = max_split > 1 ? align_up(off + sizeof(float2) * (size_t)max_split * p.J * p.grid.nx * p.grid.nz *
+                                             (size_t)p.ny)
+                             : off;
 
   kk_status st = upload(p, blob);
   if (st != KK_OK) return st;
@@ -357,6 +443,7 @@ kk_status make_kk(kk_plan &p, const kk_plan_desc *d) {
   p.t.bf_A = at<long long>(b, off_A);
   p.t.bf_B = at<long long>(b, off_B);
   p.t.bf_C = at<long long>(b, off_C);
+  p.t.bf_Y = p.vol ? at<long long>(b, off_Y) : nullptr;
   p.t.bf_Af = at<float>(b, off_Af);
   p.t.bf_Bf = at<float>(b, off_Bf);
   p.t.pair_w = d->pair_weight ? at<float>(b, off_W) : nullptr;
@@ -366,6 +453,10 @@ kk_status make_kk(kk_plan &p, const kk_plan_desc *d) {
 }
 
 kk_status make_das(kk_plan &p, const kk_plan_desc *d) {
+  if (p.vol) {
+    set_error("volumetric DAS is not implemented (the volumetric path is KK only)");
+    return KK_ERR_UNSUPPORTED;
+  }
   if (!std::isfinite(d->f_number) || (d->aperture != KK_APERTURE_BOXCAR && d->aperture != KK_APERTURE_HANN)) {
     set_error("bad receive aperture (finite f_number, KK_APERTURE_BOXCAR or KK_APERTURE_HANN)");
     return KK_ERR_INVALID_ARG;
@@ -483,6 +574,10 @@ kk_status create(kk_plan **out, const kk_plan_desc *d, bool das) {
   p->c = d->c;
   p->fs = d->fs;
   p->rf_dtype = d->rf_dtype;
+  p->vol = is_volume(d);
+  p->ny = std::max(d->ny, 1);
+  p->y0 = d->y0;
+  p->dy = d->ny > 1 ? d->dy : 0.0;
   try {
     st = das ? make_das(*p, d) : make_kk(*p, d);
   } catch (const std::bad_alloc &) {
@@ -622,8 +717,10 @@ kk_status kk_plan_get_info(const kk_plan *p, kk_plan_info *info) {
   info->workspace_bytes = p->ws_total;
   info->rf_bytes = (size_t)p->N * p->L * p->T * (p->rf_dtype == KK_RF_I16 ? 2 : 4);
   info->rf_theta_bytes = p->is_das ? 0 : (size_t)p->P * p->T * 8;
-  info->image_bytes = (size_t)p->J * p->grid.nx * p->grid.nz * 8;
-  info->intensity_bytes = (size_t)p->grid.nx * p->grid.nz * 4;
+  info->image_bytes = (size_t)p->J * p->grid.nx * p->grid.nz * p->ny * 8;
+  info->intensity_bytes = (size_t)p->grid.nx * p->grid.nz * p->ny * 4;
+  info->ny = p->ny;
+  info->is_volume = p->vol ? 1 : 0;
   info->compression_factor = p->compression;
   info->launches_decompose = p->is_das ? 0 : 3;
   info->launches_beamform = (p->is_das ? 2 : 0) + (p->bf_split > 1 ? 2 : 1);

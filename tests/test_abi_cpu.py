@@ -92,7 +92,8 @@ def test_plan_validation_is_host_side(lib):
 
 
 def test_quality_struct_layouts_match_header(tmp_path):
-    """ctypes mirrors of kkquality.h and kkstream.h have the C compiler's sizes and offsets."""
+    """ctypes mirrors of the plan description / info and of kkquality.h and kkstream.h have the C
+    compiler's sizes and offsets."""
     src = tmp_path / "layout.c"
     src.write_text("""
 #include <stddef.h>
@@ -107,6 +108,9 @@ int main(void) {
   P(kk_fwhm_result, axial); P(kk_quality_desc, image_kind); P(kk_quality_desc, inside);
   P(kk_quality_desc, n_bins); P(kk_quality_desc, targets); P(kk_quality_desc, device);
   printf("kk_stream_info %zu\\n", sizeof(kk_stream_info));
+  printf("kk_plan_desc %zu\\nkk_plan_info %zu\\n", sizeof(kk_plan_desc), sizeof(kk_plan_info));
+  P(kk_plan_desc, aperture); P(kk_plan_desc, elem_y); P(kk_plan_desc, rx_angles_y); P(kk_plan_desc, ny);
+  P(kk_plan_desc, dy); P(kk_plan_info, ny); P(kk_plan_info, is_volume);
   P(kk_stream_info, n_groups); P(kk_stream_info, events_pushed); P(kk_stream_info, device_bytes);
   return 0;
 }
@@ -130,7 +134,13 @@ int main(void) {
             "kk_stream_info": ctypes.sizeof(kb.kk_stream_info),
             "kk_stream_info.n_groups": kb.kk_stream_info.n_groups.offset,
             "kk_stream_info.events_pushed": kb.kk_stream_info.events_pushed.offset,
-            "kk_stream_info.device_bytes": kb.kk_stream_info.device_bytes.offset}
+            "kk_stream_info.device_bytes": kb.kk_stream_info.device_bytes.offset,
+            "kk_plan_desc": ctypes.sizeof(kb.kk_plan_desc), "kk_plan_info": ctypes.sizeof(kb.kk_plan_info),
+            "kk_plan_desc.aperture": kb.kk_plan_desc.aperture.offset,
+            "kk_plan_desc.elem_y": kb.kk_plan_desc.elem_y.offset,
+            "kk_plan_desc.rx_angles_y": kb.kk_plan_desc.rx_angles_y.offset,
+            "kk_plan_desc.ny": kb.kk_plan_desc.ny.offset, "kk_plan_desc.dy": kb.kk_plan_desc.dy.offset,
+            "kk_plan_info.ny": kb.kk_plan_info.ny.offset, "kk_plan_info.is_volume": kb.kk_plan_info.is_volume.offset}
     assert {k: int(v) for k, v in got.items()} == want
 
 

@@ -1,0 +1,159 @@
+"""Volumetric KK with a 2D array on the GPU against the FP64 oracle
+(oracle.volume).  FP32 forms at the plain path's bound, rel-L2 <= 1e-5 over
+the whole complex volume; a linear array described as a volume reproduces the
+linear-array plan; groups, compounding, pair-range splits, the BF16 form and
+the streaming decomposition run on volumes; the calls that do not support
+volumes refuse them."""
+import numpy as np
+import pytest
+
+import kksynth
+import paper_2603_22496_gb300 as kb
+from oracle import kk, schemes, volume as V
+from tests import kkcases as kc
+
+pytestmark = pytest.mark.gpu
+FS, C = kksynth.FS, kksynth.C_SOUND
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_2603_22496_gb300 import build
+    build.build()
+    kb.load()
+
+
+def _plan(w, ps, compound=kb.KK_COMPOUND_COHERENT, precision=kb.KK_PREC_F32):
+    pairs = np.stack([ps.tx_index, ps.rx_index], 1).astype(np.int32)
+    return kb.Plan(w.elem_x, w.tx_ax, w.grid, w.c, w.fs, w.n_samples, kc.rf_dtype_of(w), rx_angles=ps.rx_ax,
+                   pairs=pairs, group_of_pair=ps.group.astype(np.int32), n_groups=ps.n_groups,
+                   compound=compound, precision=precision, elem_y=w.elem_y, tx_angles_y=w.tx_ay,
+                   rx_angles_y=ps.rx_ay, grid_y=w.grid_y)
+
+
+def _run(plan, rf):
+    import torch
+    ws, rt, B, I = plan.empty_workspace(), plan.empty_rf_theta(), plan.empty_image(), plan.empty_intensity()
+    plan.decompose(kc.to_dev(rf), rt, ws)
+    plan.beamform(rt, B, I, ws)
+    torch.cuda.synchronize()
+    return kc.cplx(B), I.cpu().numpy().astype(np.float64), kc.cplx(rt)
+
+
+def _rx_product(theta_deg, m):
+    rx1 = schemes.even_receive_set(np.deg2rad(theta_deg), m)
+    return np.tile(rx1, m), np.repeat(rx1, m)
+
+
+@pytest.fixture(scope="module")
+def small():
+    return kksynth.volume_workload(speckle=400)
+
+
+def test_volume_full_matches_oracle(small):
+    w = small
+    ps = V.product_set(w.tx_ax, w.tx_ay, [_rx_product(12.0, 7)])
+    plan = _plan(w, ps)
+    info = plan.info
+    assert info.is_volume == 1 and info.ny == 48 and info.n_pairs == 9 * 49
+    B, I, rt = _run(plan, w.rf)
+    assert B.shape == (1, 48, 64, 48)
+    y = V.decompose3(w.rf, w.elem_x, w.elem_y, ps, FS, C)
+    assert kc.rel_l2(rt, y) <= 3e-6
+    ref = V.kk_beamform3(y, w.elem_x, w.elem_y, ps, w.grid, w.grid_y, FS, C)
+    assert kc.rel_l2(B, ref) <= TOL
+    assert kc.rel_l2(I, np.abs(ref[0]) ** 2) <= 2 * TOL
+
+
+def test_volume_hybrid_groups_incoherent(small):
+    """Three groups (x schemes shifted by j = 0, 1, 2) compounded incoherently:
+    the multi-group kernel on volumes, with a pair-range split."""
+    w = small
+    tx1 = np.deg2rad(np.linspace(-8, 8, 3))
+    groups = [V.separable_scheme("shifted", tx1, tx1, 5, 5, jx=j, jy=j) for j in (0, 1, 2)]
+    ps = V.product_set(w.tx_ax, w.tx_ay, groups)
+    plan = _plan(w, ps, compound=kb.KK_COMPOUND_INCOHERENT)
+    B, I, _ = _run(plan, w.rf)
+    ref = V.kk_volume(w.rf, w.elem_x, w.elem_y, ps, w.grid, w.grid_y, FS, C)
+    assert kc.rel_l2(B, ref) <= TOL
+    assert kc.rel_l2(I, np.sum(np.abs(ref) ** 2, axis=0)) <= 2 * TOL
+
+
+def test_linear_array_as_a_volume():
+    """A linear array, zero y tilts and one slice at y = 0 described as a volume
+    gives the linear-array plan's image (the coefficients differ only by the
+    rounding of sqrt(1 - sin^2) against cos)."""
+    w = kksynth.workload_small()
+    ops, (rx, pairs, grp, J) = kc.scheme_both("confocal", w.tx_angles, 11)
+    B2, I2, _, _ = kc.run_kk(w, rx, pairs, grp, J, compound=kb.KK_COMPOUND_COHERENT)
+    plan = kb.Plan(w.elem_x, w.tx_angles, w.grid, w.c, w.fs, w.n_samples, kc.rf_dtype_of(w), rx_angles=rx,
+                   pairs=pairs, group_of_pair=grp, n_groups=J, compound=kb.KK_COMPOUND_COHERENT,
+                   elem_y=np.zeros_like(w.elem_x), tx_angles_y=np.zeros_like(w.tx_angles),
+                   rx_angles_y=np.zeros_like(rx), grid_y=(1, 0.0, 0.0))
+    assert plan.info.is_volume == 1
+    B3, I3, _ = _run(plan, w.rf)
+    assert kc.rel_l2(B3[:, 0], B2) <= 1e-6
+    assert kc.rel_l2(I3[0], I2) <= 2e-6
+
+
+def test_volume_bf16_form_and_sampled_oracle():
+    """8 x 16 array (128 elements: the tensor-core forms), int16 at 30 dB,
+    5 x 3 tilts, 9 x 5 receive waves, 96 x 64 x 128 voxels; the oracle on
+    sampled voxels."""
+    w = kksynth.volume_workload(seed=3100, lx=16, ly=8, ntx=5, nty=3, theta_max_deg=10.0, n_samples=2048,
+                                nx=96, ny=64, nz=128, dxyz=0.1e-3, z0=5e-3, speckle=3000, rf_dtype="i16")
+    rx1x = schemes.even_receive_set(np.deg2rad(14.0), 9)
+    rx1y = schemes.even_receive_set(np.deg2rad(10.0), 5)
+    ps = V.product_set(w.tx_ax, w.tx_ay, [(np.tile(rx1x, 5), np.repeat(rx1y, 9))])
+    rng = np.random.default_rng(7)
+    vox = np.stack([rng.integers(0, 96, 1500), rng.integers(0, 64, 1500), rng.integers(0, 128, 1500)], 1)
+    ref = V.kk_volume(w.rf, w.elem_x, w.elem_y, ps, w.grid, w.grid_y, FS, C, voxels=vox)[0]
+    for prec, tol in ((kb.KK_PREC_F32, TOL), (kb.KK_PREC_BF16, 1e-2)):
+        plan = _plan(w, ps, precision=prec)
+        B, _, _ = _run(plan, w.rf)
+        got = B[0][vox[:, 1], vox[:, 2], vox[:, 0]]
+        assert kc.rel_l2(got, ref) <= tol, prec
+
+
+def test_volume_streaming_equals_whole_frame(small):
+    import torch
+    w = small
+    ps = V.product_set(w.tx_ax, w.tx_ay, [_rx_product(12.0, 5)])
+    plan = _plan(w, ps)
+    B0, I0, _ = _run(plan, w.rf)
+    st = kb.Stream(plan, 4)
+    h = torch.from_numpy(np.ascontiguousarray(w.rf)).pin_memory()
+    B, I = plan.empty_image(), plan.empty_intensity()
+    st.push_many(0, h_events=h)
+    st.end_frame(B, I)
+    st.sync()
+    assert np.array_equal(kc.cplx(B), B0) and np.array_equal(I.cpu().numpy().astype(np.float64), I0)
+
+
+def test_volume_rejections(small):
+    import torch
+    w = small
+    with pytest.raises(kb.KKError) as e:       # volumetric DAS is not implemented
+        kb.Plan(w.elem_x, w.tx_ax, w.grid, w.c, w.fs, w.n_samples, kb.KK_RF_F32, das=True, elem_y=w.elem_y,
+                tx_angles_y=w.tx_ay, grid_y=w.grid_y)
+    assert e.value.status == kb.KK_ERR_UNSUPPORTED
+    ps = V.product_set(w.tx_ax, w.tx_ay, [_rx_product(12.0, 3)])
+    pairs = np.stack([ps.tx_index, ps.rx_index], 1).astype(np.int32)
+    bad = [dict(rx_angles_y=np.full(ps.rx_ay.shape, np.deg2rad(75.0))),        # tilts do not propagate
+           dict(rx_angles_y=ps.rx_ay, grid_y=(4, 0.0, 0.0)),                     # ny > 1 needs dy > 0
+           dict(rx_angles_y=ps.rx_ay, grid_y=(4, np.nan, 1e-4))]
+    for kw in bad:
+        args = dict(elem_y=w.elem_y, tx_angles_y=w.tx_ay, grid_y=w.grid_y)
+        args.update(kw)
+        with pytest.raises(kb.KKError) as e:
+            kb.Plan(w.elem_x, w.tx_ax, w.grid, w.c, w.fs, w.n_samples, kb.KK_RF_F32, rx_angles=ps.rx_ax,
+                    pairs=pairs, **args)
+        assert e.value.status == kb.KK_ERR_INVALID_ARG
+    plan = _plan(w, ps)
+    fr = [{"plan": plan, "rf": kc.to_dev(w.rf), "rf_theta": plan.empty_rf_theta(), "B": plan.empty_image(),
+           "I": plan.empty_intensity(), "workspace": plan.empty_workspace()}]
+    with pytest.raises(kb.KKError) as e:
+        kb.Batch(fr, shape=404)
+    assert e.value.status == kb.KK_ERR_UNSUPPORTED
+    torch.cuda.synchronize()
