@@ -33,6 +33,7 @@
 #include "kk_internal.h"
 #include "kk_nn.h"
 #include "kk_tc.h"
+#include "kk_tma.h"
 
 namespace kk {
 namespace nn {
@@ -49,25 +50,8 @@ constexpr int kWgK = 64;
 
 __device__ int g_tma_status;
 
-using EncodeFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
-                              const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
-                              CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-EncodeFn encoder() {
-  static EncodeFn fn = nullptr;
-  static std::once_flag once;
-  std::call_once(once, [] {
-    void *p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
-            cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<EncodeFn>(p);
-    else
-      cudaGetLastError();
-  });
-  return fn;
-}
+using kk::tma::encoder;
+using kk::tma::EncodeFn;
 
 // swizzle of a row of `ch` bf16 channels (32 / 64 / 128 bytes) and the
 // matching descriptor layout code
@@ -113,20 +97,12 @@ __device__ __forceinline__ void tma_4d(uint32_t dst, const CUtensorMap *m, int c
       "l"(reinterpret_cast<uint64_t>(m)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
       : "memory");
 }
-__device__ __forceinline__ void tma_2d(uint32_t dst, const CUtensorMap *m, int c0, int c1, uint64_t *bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
-      "[%4];" ::"r"(dst),
-      "l"(reinterpret_cast<uint64_t>(m)), "r"(c0), "r"(c1), "r"(smem_u32(bar))
-      : "memory");
-}
+using kk::tma::tma_2d;
 // shared-memory descriptor with a layout (swizzle) code
 __device__ __forceinline__ uint64_t smem_desc_sw(uint32_t saddr, uint32_t lbo, uint32_t sbo, uint32_t layout) {
   return smem_desc(saddr, lbo, sbo) | ((uint64_t)layout << 61);
 }
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
-}
+using kk::tma::mbar_expect_tx;
 __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
                                          uint32_t accumulate) {
   asm volatile(

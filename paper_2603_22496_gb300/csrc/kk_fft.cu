@@ -24,6 +24,7 @@
 #include <cuda_fp16.h>
 
 #include "kk_internal.h"
+#include "kk_tma.h"
 
 namespace kk {
 
@@ -345,6 +346,88 @@ __global__ void __launch_bounds__(NT) k_inverse(const float2 *__restrict__ Y, in
   }
 }
 
+// ---- inverse with TMA prefetch (persistent) ---------------------------------
+// The same transform as k_inverse for the common case where row r reads
+// column r of Y (col_of_row is the identity) and ncol is even: each CTA loops
+// over groups of C consecutive rows; the group's Y tile [F][C] arrives by 2D
+// bulk copies (boxes of up to 256 bins x C columns) in a staging buffer while
+// the previous group is transformed and stored, so the strided 8C-byte runs
+// of the bin-major Y never stall the transform.  Every wait is bounded; a CTA
+// that gives up sets *status to KK_ERR_TIMEOUT, waits (bounded) for the copy
+// it issued and returns.
+template <int F, int C, int NT>
+__global__ void __launch_bounds__(NT, (F == 1024 || F == 2048) ? 2 : 1) k_inverse_tma(const __grid_constant__ CUtensorMap ymap, int nrow,
+                                                    const float2 *__restrict__ tw,
+                                                    const float2 *__restrict__ rw,
+                                                    float2 *__restrict__ out, float scale,
+                                                    const float *__restrict__ row_w,
+                                                    const int32_t *__restrict__ out_row, int *status) {
+  constexpr int FS = fft_row(F);
+  constexpr int T = 2 * F;
+  constexpr int BK = F < 256 ? F : 256;  // bins per box
+  constexpr unsigned kTx = (unsigned)(C * F * sizeof(float2));
+  extern __shared__ __align__(128) float2 sm[];
+  float2 *stg = sm;                     // [F][C] tile of Y (bin-major, as in global memory)
+  float2 *buf = sm + C * F;             // [2C][FS] transforms
+  float2 *s_tw = buf + 2 * C * FS;      // twiddles of every pass
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ int s_bad;
+  const int tid = threadIdx.x;
+  const int n_groups = (nrow + C - 1) / C;
+  for (int i = tid; i < fft_twoff(F, fft_npass(F)); i += NT) s_tw[i] = __ldg(tw + i);
+  if (tid == 0) {
+    tc::mbar_init(&bar, 1);
+    s_bad = 0;
+  }
+  tc::mbar_init_fence();
+  __syncthreads();
+  auto issue = [&](int g) {
+    tma::mbar_expect_tx(&bar, kTx);
+#pragma unroll
+    for (int b = 0; b < F / BK; ++b)
+      tma::tma_2d(tc::smem_u32(stg + b * BK * C), &ymap, g * C, b * BK, &bar);
+  };
+  int g = blockIdx.x;
+  if (tid == 0 && g < n_groups) issue(g);
+  uint32_t phase = 0;
+  for (; g < n_groups; g += gridDim.x) {
+    const bool ok = tc::mbar_wait(&bar, phase);
+    if (__syncthreads_or(!ok)) {
+      if (tid == 0) {
+        atomicExch(status, (int)KK_ERR_TIMEOUT);
+        tc::mbar_wait(&bar, phase);  // bounded: let the copy in flight land before exiting
+      }
+      return;
+    }
+    phase ^= 1u;
+    const int r0 = g * C;
+    // spread: conj(Y) to the even transform, conj(Y) e^{-2 pi i k / T} to the odd one
+#pragma unroll 4
+    for (int idx = tid; idx < C * F; idx += NT) {
+      const int k = idx / C, rr = idx - k * C;
+      const float2 y = stg[idx];
+      const float2 a = make_float2(y.x, -y.y);
+      buf[(2 * rr) * FS + fft_pad(k)] = a;
+      buf[(2 * rr + 1) * FS + fft_pad(k)] = cmul(a, __ldg(rw + k));
+    }
+    __syncthreads();  // staging consumed: prefetch the next group while transforming this one
+    if (tid == 0 && g + (int)gridDim.x < n_groups) issue(g + gridDim.x);
+    run_passes<F, FS, 2 * C, NT, 0>(buf, s_tw, tid);
+    for (int idx = tid; idx < C * F; idx += NT) {
+      const int rr = idx / F, m = idx - rr * F;
+      const int row = r0 + rr;
+      if (row >= nrow) continue;
+      const float2 ev = buf[(2 * rr) * FS + fft_pad(m)];
+      const float2 od = buf[(2 * rr + 1) * FS + fft_pad(m)];
+      const float sc = row_w ? scale * __ldg(row_w + row) : scale;
+      const float4 o = make_float4(ev.x * sc, -ev.y * sc, od.x * sc, -od.y * sc);
+      const size_t orow = out_row ? (size_t)__ldg(out_row + row) : (size_t)row;
+      *reinterpret_cast<float4 *>(out + orow * T + 2 * m) = o;
+    }
+    __syncthreads();  // transforms stored: the buffers are free for the next group
+  }
+}
+
 // ---- dispatch ----------------------------------------------------------------
 template <int F>
 struct FftCfg {
@@ -386,11 +469,44 @@ static cudaError_t spectrum_f(const kk_plan &p, const void *rf, void *X, int n_r
   return spectrum_fi<F, float>(p, rf, X, n_ch, rows, s);
 }
 
+// Y [F][ncol] complex as (ncol, F) 8-byte elements, box {C, min(F, 256)}
+static bool map_y(CUtensorMap *m, const float2 *Y, int ncol, int F, int C) {
+  tma::EncodeFn enc = tma::encoder();
+  if (!enc) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)ncol, (cuuint64_t)F};
+  const cuuint64_t strides[1] = {(cuuint64_t)ncol * sizeof(float2)};
+  const cuuint32_t box[2] = {(cuuint32_t)C, (cuuint32_t)(F < 256 ? F : 256)};
+  const cuuint32_t es[2] = {1, 1};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, const_cast<float2 *>(Y), dims, strides, box, es,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 template <int F>
 static cudaError_t inverse_f(const kk_plan &p, const float2 *Y, int ncol, const int32_t *col,
                              int nrow, float2 *out, cudaStream_t s, const float *row_w,
                              const int32_t *out_row) {
   using Cfg = FftCfg<F>;
+  // TMA path: identity column map (col null, or rows reading columns 0..nrow-1
+  // in order, flagged by the plan), even ncol, 16-byte aligned Y
+  if (col == nullptr && ncol % 2 == 0 && nrow <= ncol && ((uintptr_t)Y % 16) == 0 && p.t.status) {
+    CUtensorMap m;
+    if (map_y(&m, Y, ncol, F, Cfg::CI)) {
+      const size_t smem = sizeof(float2) * ((size_t)Cfg::CI * F + 2 * Cfg::CI * fft_row(F) +
+                                            fft_twoff(F, fft_npass(F)));
+      auto k = k_inverse_tma<F, Cfg::CI, Cfg::NT>;
+      cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      int sms = 148, per_sm = 1;
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p.device);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, Cfg::NT, smem);
+      const int groups = (nrow + Cfg::CI - 1) / Cfg::CI;
+      const int grid = std::max(1, std::min(groups, sms * std::max(per_sm, 1)));
+      k<<<grid, Cfg::NT, smem, s>>>(m, nrow, p.t.fft_tw, p.t.rfft_w, out, (float)(1.0 / (double)(2 * F)),
+                                    row_w, out_row, p.t.status);
+      return cudaGetLastError();
+    }
+  }
   const size_t smem = sizeof(float2) * (2 * Cfg::CI * fft_row(F) + fft_twoff(F, fft_npass(F)));
   auto k = k_inverse<F, Cfg::CI, Cfg::NT>;
   cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -107,6 +107,10 @@ struct kk_plan {
   // delay in bf_Y (32.32 samples per slice)
   bool vol = false;
   int ny = 1;
+  // pair q's record comes from column q of Y (pairs listed transmit-major
+  // over every used (transmit, receive) combination): the inverse needs no
+  // column table and can stream Y tiles by TMA
+  bool pair_q_identity = false;
   double y0 = 0, dy = 0;
 };
 

@@ -347,6 +347,8 @@ kk_status make_kk(kk_plan &p, const kk_plan_desc *d) {
     pair_q[q] = p.h_pair_tu[q] * p.Mu + p.h_pair_ou[q];
   }
   p.h_tx_used = txu;
+  p.pair_q_identity = (P == p.Nu * p.Mu);
+  for (int q = 0; q < P && p.pair_q_identity; ++q) p.pair_q_identity = pair_q[q] == q;
   const size_t off_pq = blob.add(pair_q);
 
   // gather tables, pairs stably sorted by group
@@ -613,7 +615,8 @@ kk_status enqueue_decompose(const kk_plan *p, const void *rf, void *rf_theta, vo
   if (e != cudaSuccess) return cuda_fail(e, "spectrum launch");
   e = launch_shear(*p, X, Y, s);
   if (e != cudaSuccess) return cuda_fail(e, "shear launch");
-  e = launch_inverse(*p, Y, p->Nu * p->Mu, p->t.pair_q, p->P, (float2 *)rf_theta, s, p->t.pair_w);
+  e = launch_inverse(*p, Y, p->Nu * p->Mu, p->pair_q_identity ? nullptr : p->t.pair_q, p->P, (float2 *)rf_theta, s,
+                     p->t.pair_w);
   if (e != cudaSuccess) return cuda_fail(e, "inverse launch");
   return KK_OK;
 }
@@ -762,7 +765,7 @@ kk_status kk_inverse(const kk_plan *p, const void *d_Y, void *d_rf_theta, void *
   if (!d_Y || !d_rf_theta) { set_error("null buffer"); return KK_ERR_INVALID_ARG; }
   if (!aligned(d_rf_theta, 16)) { set_error("rf_theta must be 16-byte aligned"); return KK_ERR_INVALID_ARG; }
   DeviceGuard guard(p->device);
-  cudaError_t e = launch_inverse(*p, (const float2 *)d_Y, p->Nu * p->Mu, p->t.pair_q, p->P,
+  cudaError_t e = launch_inverse(*p, (const float2 *)d_Y, p->Nu * p->Mu, p->pair_q_identity ? nullptr : p->t.pair_q, p->P,
                                  (float2 *)d_rf_theta, (cudaStream_t)stream, p->t.pair_w);
   return e == cudaSuccess ? KK_OK : cuda_fail(e, "inverse launch");
 }

@@ -41,6 +41,7 @@ struct Group {
   kk_plan sub;             // plan copy with Nu = this group's transmits
   int first_tu = 0, n_tx = 0, n_pairs = 0;
   int32_t *d_col = nullptr;    // Y column of each pair: (tu - first_tu) * Mu + ou
+  bool col_identity = false;   // d_col[j] == j
   int32_t *d_orow = nullptr;   // rf_theta row (caller's pair order)
   float *d_w = nullptr;        // pair weight (null without weights)
 };
@@ -151,7 +152,8 @@ kk_status run_group(kk_stream *s, int g) {
   if (e != cudaSuccess) return cuda_fail(e, "kk_stream: spectrum launch");
   e = launch_shear(gr.sub, s->X, s->Y, s->s_dec);
   if (e != cudaSuccess) return cuda_fail(e, "kk_stream: shear launch");
-  e = launch_inverse(gr.sub, s->Y, gr.n_tx * gr.sub.Mu, gr.d_col, gr.n_pairs, s->rt[s->frame % 2], s->s_dec,
+  e = launch_inverse(gr.sub, s->Y, gr.n_tx * gr.sub.Mu, gr.col_identity ? nullptr : gr.d_col, gr.n_pairs,
+                     s->rt[s->frame % 2], s->s_dec,
                      gr.d_w, gr.d_orow);
   if (e != cudaSuccess) return cuda_fail(e, "kk_stream: inverse launch");
   e = cudaEventRecord(s->ev_dec[b], s->s_dec);
@@ -271,6 +273,8 @@ kk_status kk_stream_create(kk_stream **out, const kk_plan *plan, int32_t group, 
     unsigned char *base = s->block + o_tab[g];
     const size_t nb = up(col[g].size() * sizeof(int32_t));
     gr.d_col = reinterpret_cast<int32_t *>(base);
+    gr.col_identity = true;  // the group's pair j reads column j of its Y (TMA-fed inverse)
+    for (size_t j = 0; j < col[g].size() && gr.col_identity; ++j) gr.col_identity = col[g][j] == (int32_t)j;
     gr.d_orow = reinterpret_cast<int32_t *>(base + nb);
     gr.d_w = w[g].empty() ? nullptr : reinterpret_cast<float *>(base + 2 * nb);
     if (gr.n_pairs) {
