@@ -296,6 +296,94 @@ __global__ void __launch_bounds__(NT) k_spectrum(const TIn *__restrict__ rf,
   }
 }
 
+// Persistent form of k_spectrum: each CTA loops over groups of C channels;
+// the group's records (contiguous T samples each) arrive by 1D bulk copies in
+// a staging buffer while the previous group is transformed and stored.
+// Records must be 16-byte aligned (T * sizeof(TIn) is a multiple of 16 for
+// every supported T).  Bounded waits as in k_inverse_tma.
+template <int F, int C, int NT, typename TIn, typename TOut>
+__global__ void __launch_bounds__(NT, (F == 1024 || F == 2048) ? 2 : 1) k_spectrum_tma(const TIn *__restrict__ rf,
+                                                        const int32_t *__restrict__ tx_rows, int L, int n_ch,
+                                                        const float2 *__restrict__ tw,
+                                                        const float2 *__restrict__ rw,
+                                                        TOut *__restrict__ X, float xscale, int *status) {
+  constexpr int FS = fft_row(F);
+  constexpr int T = 2 * F;
+  constexpr int VE = 16 / (int)sizeof(TIn);  // samples per 16-byte vector
+  constexpr int NV = T / VE;                 // vectors per record
+  constexpr unsigned kRec = (unsigned)(T * sizeof(TIn));
+  extern __shared__ __align__(128) float2 sm[];
+  float2 *buf = sm;                                                       // [C][FS]
+  float2 *s_tw = buf + C * FS;                                            // twiddles
+  uint4 *stg = reinterpret_cast<uint4 *>(s_tw + ((fft_twoff(F, fft_npass(F)) + 1) & ~1));  // [C][NV]
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ long long s_row[C];
+  const int tid = threadIdx.x;
+  const int n_groups = (n_ch + C - 1) / C;
+  for (int i = tid; i < fft_twoff(F, fft_npass(F)); i += NT) s_tw[i] = __ldg(tw + i);
+  if (tid == 0) tc::mbar_init(&bar, 1);
+  tc::mbar_init_fence();
+  __syncthreads();
+  auto issue = [&](int g) {  // one thread
+    const int c0 = g * C;
+    const int nc = min(C, n_ch - c0);
+    tma::mbar_expect_tx(&bar, kRec * (unsigned)nc);
+    for (int cc = 0; cc < nc; ++cc) {
+      const int c = c0 + cc;
+      const int iu = c / L, l = c - iu * L;
+      const long long r = ((long long)__ldg(tx_rows + iu) * L + l) * T;
+      tma::bulk_1d(tc::smem_u32(stg + cc * NV), rf + r, kRec, &bar);
+    }
+  };
+  int g = blockIdx.x;
+  if (tid == 0 && g < n_groups) issue(g);
+  uint32_t phase = 0;
+  for (; g < n_groups; g += gridDim.x) {
+    const bool ok = tc::mbar_wait(&bar, phase);
+    if (__syncthreads_or(!ok)) {
+      if (tid == 0) {
+        atomicExch(status, (int)KK_ERR_TIMEOUT);
+        tc::mbar_wait(&bar, phase);
+      }
+      return;
+    }
+    phase ^= 1u;
+    const int c0 = g * C;
+    const int nc = min(C, n_ch - c0);
+#pragma unroll 4
+    for (int idx = tid; idx < C * NV; idx += NT) {
+      const int cc = idx / NV, v = idx - cc * NV;
+      float2 z[VE / 2];
+      if (cc < nc) {
+        unpack16(stg[idx], rf, z);
+      } else {
+#pragma unroll
+        for (int q = 0; q < VE / 2; ++q) z[q] = make_float2(0.f, 0.f);
+      }
+#pragma unroll
+      for (int q = 0; q < VE / 2; ++q) buf[cc * FS + fft_pad(v * (VE / 2) + q)] = z[q];
+    }
+    __syncthreads();  // staging consumed: prefetch the next group
+    if (tid == 0 && g + (int)gridDim.x < n_groups) issue(g + gridDim.x);
+    run_passes<F, FS, C, NT, 0>(buf, s_tw, tid);
+    for (int idx = tid; idx < C * F; idx += NT) {
+      const int k = idx / C, cc = idx - k * C;
+      if (cc >= nc) continue;
+      const float2 zk = buf[cc * FS + fft_pad(k)];
+      const float2 zm = buf[cc * FS + fft_pad(k == 0 ? 0 : F - k)];
+      const float2 e = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
+      const float2 o = make_float2(0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
+      float2 x = cadd(e, cmul(__ldg(rw + k), o));
+      const float h = (k == 0) ? xscale : 2.f * xscale;
+      x.x *= h;
+      x.y *= h;
+      store_x(X, (size_t)k * n_ch + c0 + cc, x);
+    }
+    __syncthreads();  // buffers free for the next group
+  }
+  (void)s_row;
+}
+
 // ---- inverse of a half spectrum -------------------------------------------
 // out[row][t], row < nrow, from Y[k][col(row)] (col = identity if null).
 template <int F, int C, int NT>
@@ -440,6 +528,22 @@ template <int F, typename TIn, typename TOut>
 static cudaError_t spectrum_ft(const kk_plan &p, const void *rf, void *X, int n_ch,
                                const int32_t *rows, cudaStream_t s) {
   using Cfg = FftCfg<F>;
+  if (((uintptr_t)rf % 16) == 0 && p.t.status && n_ch > 0) {
+    constexpr int NV = 2 * F * (int)sizeof(TIn) / 16;
+    const size_t tw_n = (size_t)((fft_twoff(F, fft_npass(F)) + 1) & ~1);
+    const size_t smem = sizeof(float2) * ((size_t)Cfg::CS * fft_row(F) + tw_n) + sizeof(uint4) * Cfg::CS * NV;
+    auto k = k_spectrum_tma<F, Cfg::CS, Cfg::NT, TIn, TOut>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int sms = 148, per_sm = 1;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p.device);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, Cfg::NT, smem);
+    const int groups = (n_ch + Cfg::CS - 1) / Cfg::CS;
+    const int grid = std::max(1, std::min(groups, sms * std::max(per_sm, 1)));
+    k<<<grid, Cfg::NT, smem, s>>>((const TIn *)rf, rows, p.L, n_ch, p.t.fft_tw, p.t.rfft_w, (TOut *)X, p.x_scale,
+                                  p.t.status);
+    return cudaGetLastError();
+  }
   const size_t smem = sizeof(float2) * (Cfg::CS * fft_row(F) + fft_twoff(F, fft_npass(F)));
   const dim3 grid((n_ch + Cfg::CS - 1) / Cfg::CS);
   const bool vec = ((uintptr_t)rf % 16) == 0;

@@ -43,6 +43,14 @@ __device__ __forceinline__ void tma_2d(uint32_t dst, const CUtensorMap *m, int c
       : "memory");
 }
 
+// 1D bulk copy of `bytes` (multiple of 16, both addresses 16-byte aligned)
+__device__ __forceinline__ void bulk_1d(uint32_t dst, const void *src, uint32_t bytes, uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+      "l"(src), "r"(bytes), "r"(kk::tc::smem_u32(bar))
+      : "memory");
+}
+
 __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(kk::tc::smem_u32(bar)), "r"(bytes)
                : "memory");
