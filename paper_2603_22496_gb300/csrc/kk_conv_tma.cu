@@ -152,7 +152,19 @@ constexpr int kPersThreads = 192;
 constexpr int kPersMaxStages = 16;
 constexpr int kPersBudget = 200 * 1024;
 
-template <int KC>
+// HALO (one-row tiles of 128 pixels): a stage is one channel chunk -- one
+// copy of the tile's 3 input rows x 130 pixels (box {KC, 130, 3, 1} at
+// (c0, w0 - 1, h0 - 1)) plus the nine taps' weight tiles -- and tap (kh, kw)
+// reads A from row kh * 130 + kw of that halo tile (rows are packed densely,
+// so a tap is a whole-row shift of the descriptor start within the swizzled
+// tile).  Each input pixel then crosses L2 about 3 times per layer, not 9.
+constexpr int kHaloW = kTileM + 2;
+constexpr int kHaloRows = 3 * kHaloW;
+__host__ __device__ constexpr uint32_t halo_bytes(int KC) {
+  return (uint32_t)((kHaloRows * KC * 2 + 1023) / 1024 * 1024);
+}
+
+template <int KC, bool HALO>
 __global__ void __launch_bounds__(kPersThreads)
     k_conv3x3_tma_pers(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmW,
                        const TmaConvArgs a, const int N, const int S, const int n_items, const int n_ntiles) {
@@ -162,14 +174,15 @@ __global__ void __launch_bounds__(kPersThreads)
   __shared__ uint32_t tmem_slot;
   __shared__ int s_abort;
 
-  constexpr uint32_t A_BYTES = kTileM * KC * 2;
+  constexpr uint32_t A_BYTES = HALO ? halo_bytes(KC) : kTileM * KC * 2;
   constexpr uint32_t ROW = KC * 2;
   constexpr uint32_t LAYOUT = layout_code(KC);
   const uint32_t B_BYTES = (uint32_t)N * KC * 2;
-  const uint32_t STAGE = A_BYTES + B_BYTES;
+  const uint32_t STAGE = A_BYTES + (HALO ? 9u : 1u) * B_BYTES;
+  const uint32_t STAGE_TX = (HALO ? (uint32_t)kHaloRows * ROW : A_BYTES) + (HALO ? 9u : 1u) * B_BYTES;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int cpt = a.cin / KC;
-  const int nK = 9 * cpt;
+  const int nK = HALO ? cpt : 9 * cpt;
   int *status = a.status ? a.status : &g_tma_status;
 
   uint32_t ncols = 32;
@@ -211,12 +224,19 @@ __global__ void __launch_bounds__(kPersThreads)
         if (lane == 0) {
           if (g >= S && !mbar_wait(&empty_bar[s], (uint32_t)((g / S) - 1) & 1u)) go = 0;
           if (go) {
-            mbar_expect_tx(&full_bar[s], STAGE);
-            const int tap = k / cpt, c0 = (k - tap * cpt) * KC;
-            const int kh = tap / 3, kw = tap - kh * 3;
+            mbar_expect_tx(&full_bar[s], STAGE_TX);
             const uint32_t sA = sbase + (uint32_t)s * STAGE;
-            tma_4d(sA, &tmX, c0, w0 + kw - 1, h0 + kh - 1, img, &full_bar[s]);
-            tma_2d(sA + A_BYTES, &tmW, tap * a.cin + c0, n0, &full_bar[s]);
+            if constexpr (HALO) {
+              const int c0 = k * KC;
+              tma_4d(sA, &tmX, c0, w0 - 1, h0 - 1, img, &full_bar[s]);
+              for (int tap = 0; tap < 9; ++tap)
+                tma_2d(sA + A_BYTES + (uint32_t)tap * B_BYTES, &tmW, tap * a.cin + c0, n0, &full_bar[s]);
+            } else {
+              const int tap = k / cpt, c0 = (k - tap * cpt) * KC;
+              const int kh = tap / 3, kw = tap - kh * 3;
+              tma_4d(sA, &tmX, c0, w0 + kw - 1, h0 + kh - 1, img, &full_bar[s]);
+              tma_2d(sA + A_BYTES, &tmW, tap * a.cin + c0, n0, &full_bar[s]);
+            }
           }
         }
         go = __shfl_sync(0xffffffffu, go, 0);
@@ -254,11 +274,25 @@ __global__ void __launch_bounds__(kPersThreads)
           }
           tc_fence_after();
           const uint32_t sA = sbase + (uint32_t)s * STAGE, sB = sA + A_BYTES;
+          if constexpr (HALO) {
+            for (int tap = 0; tap < 9; ++tap) {
+              const int kh = tap / 3, kw = tap - kh * 3;
+              const uint32_t sAt = sA + (uint32_t)(kh * kHaloW + kw) * ROW;
+              const uint32_t sBt = sB + (uint32_t)tap * B_BYTES;
 #pragma unroll
-          for (int kk = 0; kk < KC / 16; ++kk) {
-            const uint64_t ad = smem_desc_sw(sA + (uint32_t)kk * 32, 16, 8 * ROW, LAYOUT);
-            const uint64_t bd = smem_desc_sw(sB + (uint32_t)kk * 32, 16, 8 * ROW, LAYOUT);
-            mma_bf16(acc, ad, bd, idesc, (k | kk) != 0 ? 1u : 0u);
+              for (int kk = 0; kk < KC / 16; ++kk) {
+                const uint64_t ad = smem_desc_sw(sAt + (uint32_t)kk * 32, 16, 8 * ROW, LAYOUT);
+                const uint64_t bd = smem_desc_sw(sBt + (uint32_t)kk * 32, 16, 8 * ROW, LAYOUT);
+                mma_bf16(acc, ad, bd, idesc, (k | tap | kk) != 0 ? 1u : 0u);
+              }
+            }
+          } else {
+#pragma unroll
+            for (int kk = 0; kk < KC / 16; ++kk) {
+              const uint64_t ad = smem_desc_sw(sA + (uint32_t)kk * 32, 16, 8 * ROW, LAYOUT);
+              const uint64_t bd = smem_desc_sw(sB + (uint32_t)kk * 32, 16, 8 * ROW, LAYOUT);
+              mma_bf16(acc, ad, bd, idesc, (k | kk) != 0 ? 1u : 0u);
+            }
           }
           mma_commit(&empty_bar[s]);
         }
@@ -492,23 +526,25 @@ int sm_count() {
   return n;
 }
 
-template <int KC>
+template <int KC, bool HALO>
 cudaError_t launch_fwd(const CUtensorMap &mx, const CUtensorMap &mw, const TmaConvArgs &a, int N, int tiles,
                        cudaStream_t s) {
-  // persistent CTAs per SM: as many as TMEM holds (2 accumulators each), at most 4
+  // persistent CTAs per SM: as many as TMEM holds (2 accumulators each), at
+  // most 4; halo stages are larger, so at most 2 CTAs with 2+ stages each
   uint32_t ncols = 32;
   while ((int)ncols < N) ncols <<= 1;
-  const int cps = std::max(1, std::min(4, (int)(512 / (2 * ncols))));
-  const size_t stage = (size_t)kTileM * KC * 2 + (size_t)N * KC * 2;
-  const int S = (int)std::max<size_t>(3, std::min<size_t>(kPersMaxStages, kPersBudget / cps / stage));
+  const int cps = std::max(1, std::min(HALO ? 2 : 4, (int)(512 / (2 * ncols))));
+  const size_t stage = HALO ? (size_t)halo_bytes(KC) + 9 * (size_t)N * KC * 2
+                            : (size_t)kTileM * KC * 2 + (size_t)N * KC * 2;
+  const int S = (int)std::max<size_t>(HALO ? 2 : 3, std::min<size_t>(kPersMaxStages, kPersBudget / cps / stage));
   const size_t smem = (size_t)S * stage;
-  cudaError_t e =
-      cudaFuncSetAttribute(k_conv3x3_tma_pers<KC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  auto k = k_conv3x3_tma_pers<KC, HALO>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int n_ntiles = (a.cout + N - 1) / N;
   const int n_items = tiles * n_ntiles;
   const int grid = std::min(n_items, cps * sm_count());
-  k_conv3x3_tma_pers<KC><<<grid, kPersThreads, smem, s>>>(mx, mw, a, N, S, n_items, n_ntiles);
+  k<<<grid, kPersThreads, smem, s>>>(mx, mw, a, N, S, n_items, n_ntiles);
   return cudaGetLastError();
 }
 
@@ -523,14 +559,17 @@ bool conv3x3_tma(const Tensor4 &x, const __nv_bfloat16 *w, int cout, const float
   const long tiles = (long)x.n * x.h * x.w / kTileM;
   while (N > 32 && N % 32 == 0 && tiles * ((cout + N - 1) / N) < 304) N /= 2;
   CUtensorMap mx, mw;
-  if (!map_nhwc(&mx, x, KC, bw, bh) || !map_2d(&mw, w, cout, 9 * x.c, KC, N)) return false;
+  // one-row tiles with up to 32 channels per chunk read a halo tile per chunk
+  const bool halo = bh == 1 && KC <= 32;
+  if (!map_nhwc(&mx, x, KC, halo ? kHaloW : bw, halo ? 3 : bh) || !map_2d(&mw, w, cout, 9 * x.c, KC, N))
+    return false;
   TmaConvArgs a{x.n, x.h, x.w, x.c, cout, bw, bias, relu ? 1 : 0, y, yf, status};
   if (KC == 64)
-    *err = launch_fwd<64>(mx, mw, a, N, (int)tiles, s);
+    *err = launch_fwd<64, false>(mx, mw, a, N, (int)tiles, s);
   else if (KC == 32)
-    *err = launch_fwd<32>(mx, mw, a, N, (int)tiles, s);
+    *err = halo ? launch_fwd<32, true>(mx, mw, a, N, (int)tiles, s) : launch_fwd<32, false>(mx, mw, a, N, (int)tiles, s);
   else
-    *err = launch_fwd<16>(mx, mw, a, N, (int)tiles, s);
+    *err = halo ? launch_fwd<16, true>(mx, mw, a, N, (int)tiles, s) : launch_fwd<16, false>(mx, mw, a, N, (int)tiles, s);
   return true;
 }
 
