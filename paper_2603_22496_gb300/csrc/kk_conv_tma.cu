@@ -533,9 +533,11 @@ cudaError_t launch_fwd(const CUtensorMap &mx, const CUtensorMap &mw, const TmaCo
   // most 4; halo stages are larger, so at most 2 CTAs with 2+ stages each
   uint32_t ncols = 32;
   while ((int)ncols < N) ncols <<= 1;
-  const int cps = std::max(1, std::min(HALO ? 2 : 4, (int)(512 / (2 * ncols))));
   const size_t stage = HALO ? (size_t)halo_bytes(KC) + 9 * (size_t)N * KC * 2
                             : (size_t)kTileM * KC * 2 + (size_t)N * KC * 2;
+  int cps = std::max(1, std::min(4, (int)(512 / (2 * ncols))));
+  if (HALO)  // two stages per CTA at least: as many CTAs as fit in the shared-memory budget
+    cps = std::max(1, std::min(cps, (int)(kPersBudget / (2 * stage))));
   const int S = (int)std::max<size_t>(HALO ? 2 : 3, std::min<size_t>(kPersMaxStages, kPersBudget / cps / stage));
   const size_t smem = (size_t)S * stage;
   auto k = k_conv3x3_tma_pers<KC, HALO>;
@@ -554,13 +556,15 @@ bool conv3x3_tma(const Tensor4 &x, const __nv_bfloat16 *w, int cout, const float
                  __nv_bfloat16 *y, float *yf, int *status, cudaStream_t s, cudaError_t *err) {
   int bw, bh;
   if (!tile_shape(x.h, x.w, kTileM, bw, bh) || x.c % 16 || cout % 16) return false;
-  const int KC = atom_channels(x.c);
+  int KC = atom_channels(x.c);
   int N = std::min(cout, kMaxN);
   const long tiles = (long)x.n * x.h * x.w / kTileM;
   while (N > 32 && N % 32 == 0 && tiles * ((cout + N - 1) / N) < 304) N /= 2;
   CUtensorMap mx, mw;
-  // one-row tiles with up to 32 channels per chunk read a halo tile per chunk
-  const bool halo = bh == 1 && KC <= 32;
+  // one-row tiles read a halo tile per chunk of at most 32 channels (wider
+  // inputs in 32-channel chunks), while a stage of nine weight tiles fits
+  const bool halo = bh == 1 && (KC <= 32 || x.c % 32 == 0) && N <= 64;
+  if (halo && KC > 32) KC = 32;
   if (!map_nhwc(&mx, x, KC, halo ? kHaloW : bw, halo ? 3 : bh) || !map_2d(&mw, w, cout, 9 * x.c, KC, N))
     return false;
   TmaConvArgs a{x.n, x.h, x.w, x.c, cout, bw, bias, relu ? 1 : 0, y, yf, status};
