@@ -404,7 +404,9 @@ cudaError_t launch_cfg(const kk_plan &p, const float2 *rf_theta, float2 *dst, fl
   const dim3 grid(p.tiles_x * p.tiles_z * p.ny, p.bf_split);
   cudaError_t e;
   if (p.vol) {
-    auto k = (p.J > 1) ? k_kk_gather_vol<ROWS, STAGE, NPT, MB, true> : k_kk_gather_vol<ROWS, STAGE, NPT, MB, false>;
+    // the slice term costs registers: one CTA per SM fewer than the 2D kernel, without spills
+    constexpr int MBV = MB - 1;
+    auto k = (p.J > 1) ? k_kk_gather_vol<ROWS, STAGE, NPT, MBV, true> : k_kk_gather_vol<ROWS, STAGE, NPT, MBV, false>;
     e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k<<<grid, kGatherThreads, smem, s>>>(gather_args(p, rf_theta, dst, I), gather_vol_args(p));
