@@ -112,3 +112,33 @@ def test_gpu_simulator_matches_cpu_forward_model():
     noisy = kb.kk_simulate_rf(w.tx_angles, w.elem_x, w.n_samples, sc, w.fs, w.c, noise_sigma=0.5, seed=7)
     d = (noisy - rf).cpu().numpy()
     assert abs(d.std() - 0.5) < 0.01 and abs(d.mean()) < 0.01
+
+
+def test_batch_full_256_uneven_frames_match_per_frame():
+    """The benchmark's batched workload at full size (256 frames of 64-256
+    elements, 1024-4096 samples, 8-75 transmits, 32-512 pairs, 256^2-1024^2
+    grids, autotuned launch shape): every frame of the graph equals the
+    per-frame path.  Its inputs come from the GPU simulator, so the oracle
+    checks the per-frame path on CPU-simulated inputs in the tests above
+    instead."""
+    import os
+    import sys
+    import torch
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import bench
+    frames = bench._batch_frames(kb, 256)
+    batch = kb.Batch(frames, shape=0)
+    batch.run()
+    torch.cuda.synchronize()
+    assert batch.info.n_frames == 256
+    worst = 0.0
+    for f in frames:
+        plan = f["plan"]
+        assert plan.status() == kb.KK_OK
+        ws, rt, B1, I1 = plan.empty_workspace(), plan.empty_rf_theta(), plan.empty_image(), plan.empty_intensity()
+        plan.decompose(f["rf"], rt, ws)
+        plan.beamform(rt, B1, I1, ws)
+        torch.cuda.synchronize()
+        worst = max(worst, kc.rel_l2(kc.cplx(f["B"]), kc.cplx(B1)))
+        del ws, rt, B1, I1
+    assert worst <= 1e-6, worst

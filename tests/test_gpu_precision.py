@@ -123,3 +123,37 @@ def test_precision_plan_limits():
         kb.Plan(w.elem_x, w.tx_angles, w.grid, w.c, w.fs, w.n_samples, kb.KK_RF_F32,
                 rx_angles=np.zeros(1), pairs=np.array([[0, 0]], np.int32), precision=kb.KK_PREC_BF16)
     assert e.value.status == kb.KK_ERR_UNSUPPORTED
+
+
+@pytest.fixture(scope="module")
+def full_frame_oracle():
+    """The 75 x 128 frame the benchmark times: oracle records and 3000 sampled pixels."""
+    from oracle import schemes
+    w = kksynth.workload_large()
+    rxa = schemes.even_receive_set(np.deg2rad(16.0), 128)
+    rx, pairs, grp = kc.product_pairs(np.arange(75), [rxa])
+    ops = schemes.full_product(w.tx_angles, np.arange(75), [rxa])
+    y = kk.decompose(w.rf, w.elem_x, ops, FS, C)
+    rng = np.random.default_rng(11)
+    pix = np.stack([rng.integers(0, 512, 3000), rng.integers(0, 512, 3000)], 1)
+    ref = kk.kk_beamform(y, w.elem_x, ops, w.grid, FS, C, pixels=pix)[0]
+    return w, rx, pairs, grp, y, pix, ref
+
+
+@pytest.mark.parametrize("form", ["bf16", "f16", "f8e4m3"])
+def test_precision_forms_full_75x128_sampled(form, full_frame_oracle):
+    """The benchmark's frame and launch configuration (75 transmits x 128 receive
+    angles, int16, 512 x 512) in each reduced-precision form: decomposed
+    records and sampled pixels within the form's stated bound."""
+    import torch
+    w, rx, pairs, grp, y, pix, ref = full_frame_oracle
+    prec, bound = FORMS[form]
+    plan = _plan(w, rx, pairs, grp, 1, prec, compound=kb.KK_COMPOUND_COHERENT)
+    ws, rt, B, I = plan.empty_workspace(), plan.empty_rf_theta(), plan.empty_image(), plan.empty_intensity()
+    plan.decompose(kc.to_dev(w.rf), rt, ws)
+    plan.beamform(rt, B, I, ws)
+    torch.cuda.synchronize()
+    assert plan.status() == 0
+    assert kc.rel_l2(kc.cplx(rt), y) <= bound
+    got = kc.cplx(B)[0][pix[:, 1], pix[:, 0]]
+    assert kc.rel_l2(got, ref) <= bound
