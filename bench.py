@@ -594,7 +594,14 @@ def run_ours(args):
            "gpu_launches": launches, "clocks": clk, "device_status": status}
 
     if rank == 0 and not args.quick:
-        # end to end through the C ABI from pinned host memory
+        # end to end through the public API from pinned host memory.  Headline:
+        # the streaming API (kkstream.h) with one decomposition group per frame:
+        # every step pushes the frame's int16 RF from pinned host memory and
+        # reads its B and I back into pinned host memory; frame f+1's upload and
+        # decomposition overlap frame f's image formation and download (two
+        # device output buffers, each reused only after its download).  The
+        # one-call-per-frame path (kk_run_host, one stream, nothing overlapped)
+        # is reported beside it.
         h_rf = torch.from_numpy(w.rf).pin_memory()
         h_B = torch.empty((1, info.nz, info.nx, 2), dtype=torch.float32).pin_memory()
         h_I = torch.empty((info.nz, info.nx), dtype=torch.float32).pin_memory()
@@ -602,7 +609,7 @@ def run_ours(args):
         for _ in range(3):
             plan.run_host(h_rf, h_B, h_I, scratch)
         torch.cuda.synchronize()
-        k_e2e = max(5, args.steps // 2)
+        k_e2e = max(10, args.steps // 2)
         t0 = time.perf_counter()
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
@@ -611,11 +618,45 @@ def run_ours(args):
             plan.run_host(h_rf, h_B, h_I, scratch)
         b.record()
         torch.cuda.synchronize()
-        ms_e2e = a.elapsed_time(b) / k_e2e
-        out["e2e"] = {"value": round(1e3 / ms_e2e, 3), "unit": UNIT,
+        ms_seq = a.elapsed_time(b) / k_e2e
+        wall_seq = (time.perf_counter() - t0) * 1e3 / k_e2e
+        st = kb.Stream(plan, info.n_tx_used)
+        cs = torch.cuda.Stream(device=dev)
+        dB = [plan.empty_image() for _ in range(2)]
+        dI = [plan.empty_intensity() for _ in range(2)]
+        hB = [torch.empty((1, info.nz, info.nx, 2), dtype=torch.float32).pin_memory() for _ in range(2)]
+        hI = [torch.empty((info.nz, info.nx), dtype=torch.float32).pin_memory() for _ in range(2)]
+
+        def e2e_step(f):
+            st.after(cs)                       # frame f - 2's download freed buffer f % 2
+            st.push_many(0, h_events=h_rf)
+            st.end_frame(dB[f % 2], dI[f % 2])
+            st.wait(cs)
+            with torch.cuda.stream(cs):
+                hB[f % 2].copy_(dB[f % 2], non_blocking=True)
+                hI[f % 2].copy_(dI[f % 2], non_blocking=True)
+
+        for f in range(3):
+            e2e_step(f)
+        st.sync()
+        cs.synchronize()
+        t0 = time.perf_counter()
+        for f in range(k_e2e):
+            e2e_step(f)
+        st.sync()
+        cs.synchronize()
+        ms_pipe = (time.perf_counter() - t0) * 1e3 / k_e2e
+        same = bool(torch.equal(hB[(k_e2e - 1) % 2], h_B) and torch.equal(hI[(k_e2e - 1) % 2], h_I))
+        out["e2e"] = {"value": round(1e3 / ms_pipe, 3), "unit": UNIT,
                       "h2d_bytes_per_step": int(info.rf_bytes),
                       "d2h_bytes_per_step": int(info.image_bytes + info.intensity_bytes),
-                      "wall_ms_per_step": round((time.perf_counter() - t0) * 1e3 / k_e2e, 3)}
+                      "wall_ms_per_step": round(ms_pipe, 3),
+                      "api": "kkstream.h, one decomposition group per frame, uploads and downloads "
+                             "overlapped across frames (wall clock over all steps)",
+                      "matches_sequential_bitwise": same,
+                      "sequential": {"value": round(1e3 / ms_seq, 3), "api": "kk_run_host (one call per frame)",
+                                     "wall_ms_per_step": round(wall_seq, 3)}}
+        del st
         side = {}
         reps = 10
         F = info.n_bins

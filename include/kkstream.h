@@ -89,6 +89,12 @@ kk_status kk_stream_end_frame(kk_stream *s, void *d_B, float *d_I);
 /* Makes `stream` (a cudaStream_t) wait for the last ended frame's image. */
 kk_status kk_stream_wait(kk_stream *s, void *stream);
 
+/* Makes the image formations enqueued from now on wait for the work already
+ * enqueued on `stream` (a cudaStream_t): e.g. the download of an earlier
+ * frame's B and I before those buffers are passed to kk_stream_end_frame
+ * again. */
+kk_status kk_stream_after(kk_stream *s, void *stream);
+
 /* Waits for all enqueued work; returns the plan's device status
  * (KK_ERR_TIMEOUT if a bounded device wait gave up, else KK_OK). */
 kk_status kk_stream_sync(kk_stream *s);

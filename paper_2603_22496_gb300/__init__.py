@@ -46,7 +46,7 @@ EXPORTS = ["kk_plan_create", "das_plan_create", "kk_plan_destroy", "kk_plan_get_
            # include/kkquality.h
            "kk_quality_create", "kk_quality_destroy", "kk_quality_gcnr", "kk_quality_fwhm",
            # include/kkstream.h
-           "kk_stream_create", "kk_stream_push", "kk_stream_push_many", "kk_stream_end_frame", "kk_stream_wait", "kk_stream_sync",
+           "kk_stream_create", "kk_stream_push", "kk_stream_push_many", "kk_stream_end_frame", "kk_stream_wait", "kk_stream_after", "kk_stream_sync",
            "kk_stream_get_info", "kk_stream_destroy"]
 
 
@@ -221,6 +221,7 @@ def load(build_if_missing: bool = False):
         "kk_stream_push_many": ([vp, ctypes.c_int32, ctypes.c_int32, vp, vp], st),
         "kk_stream_end_frame": ([vp, vp, vp], st),
         "kk_stream_wait": ([vp, vp], st),
+        "kk_stream_after": ([vp, vp], st),
         "kk_stream_sync": ([vp], st),
         "kk_stream_get_info": ([vp, ctypes.POINTER(kk_stream_info)], st),
         "kk_stream_destroy": ([vp], None),
@@ -802,6 +803,10 @@ def kk_stream_wait(h, stream=None):
     _check(load().kk_stream_wait(h, _stream(stream)))
 
 
+def kk_stream_after(h, stream=None):
+    _check(load().kk_stream_after(h, _stream(stream)))
+
+
 def kk_stream_sync(h):
     _check(load().kk_stream_sync(h))
 
@@ -847,6 +852,9 @@ class Stream:
 
     def wait(self, stream=None):
         kk_stream_wait(self.h, stream)
+
+    def after(self, stream=None):
+        kk_stream_after(self.h, stream)
 
     def sync(self):
         kk_stream_sync(self.h)

@@ -68,6 +68,7 @@ struct kk_stream {
   std::vector<cudaEvent_t> ev_copied, ev_dec;   // per ring group
   std::vector<char> dec_pending;
   cudaEvent_t ev_frame_dec[2] = {}, ev_img[2] = {};
+  cudaEvent_t ev_ext = nullptr;  // caller-stream work the image stream waits for
   bool img_pending[2] = {false, false};
   // state of the frame being pushed
   long long frame = 0;       // frames ended so far
@@ -96,6 +97,7 @@ struct kk_stream {
       if (ev_frame_dec[b]) cudaEventDestroy(ev_frame_dec[b]);
       if (ev_img[b]) cudaEventDestroy(ev_img[b]);
     }
+    if (ev_ext) cudaEventDestroy(ev_ext);
     if (s_copy) cudaStreamDestroy(s_copy);
     if (s_dec) cudaStreamDestroy(s_dec);
     if (s_img) cudaStreamDestroy(s_img);
@@ -299,6 +301,7 @@ kk_status kk_stream_create(kk_stream **out, const kk_plan *plan, int32_t group, 
     e = cudaEventCreateWithFlags(&s->ev_frame_dec[b], cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_img[b], cudaEventDisableTiming);
   }
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_ext, cudaEventDisableTiming);
   if (e != cudaSuccess) return fail(e, "kk_stream_create: streams and events");
   *out = s;
   return KK_OK;
@@ -425,6 +428,17 @@ kk_status kk_stream_wait(kk_stream *s, void *stream) {
   DeviceGuard guard(s->device);
   const cudaError_t e = cudaStreamWaitEvent((cudaStream_t)stream, s->ev_img[(s->frame - 1) % 2], 0);
   return e == cudaSuccess ? KK_OK : cuda_fail(e, "kk_stream_wait");
+}
+
+kk_status kk_stream_after(kk_stream *s, void *stream) {
+  if (!s) {
+    set_error("kk_stream_after: null stream");
+    return KK_ERR_INVALID_ARG;
+  }
+  DeviceGuard guard(s->device);
+  cudaError_t e = cudaEventRecord(s->ev_ext, (cudaStream_t)stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(s->s_img, s->ev_ext, 0);
+  return e == cudaSuccess ? KK_OK : cuda_fail(e, "kk_stream_after");
 }
 
 kk_status kk_stream_sync(kk_stream *s) {

@@ -190,3 +190,35 @@ def test_stream_push_many_coalesces_copies():
     assert np.array_equal(B.cpu().numpy(), Bb) and np.array_equal(I.cpu().numpy(), Ib)
     # groups {0..3}, {4..7}, {8..10}: the second straddles the two blocks
     assert st.info.copies == 2 * 4
+
+
+def test_stream_after_protects_reused_output_buffers():
+    """Pipelined end to end: frames pushed from pinned memory, imaged into two
+    alternating device buffers, each downloaded on a caller stream; the image
+    formation of frame f waits (kk_stream_after) for frame f - 2's download.
+    Every downloaded frame equals the per-frame path."""
+    import torch
+    w = kksynth.workload_small()
+    ops, (rx, pairs, grp, J) = kc.scheme_both("confocal", w.tx_angles, 11)
+    plan = kc.kk_plan_for(w, rx, pairs, grp, J, compound=kb.KK_COMPOUND_COHERENT)
+    st = kb.Stream(plan, 11)
+    frames = _frames(w, 6)
+    hs = [torch.from_numpy(np.ascontiguousarray(rf)).pin_memory() for rf in frames]
+    dB = [plan.empty_image() for _ in range(2)]
+    dI = [plan.empty_intensity() for _ in range(2)]
+    hB = [torch.empty(dB[0].shape, dtype=torch.float32).pin_memory() for _ in frames]
+    hI = [torch.empty(dI[0].shape, dtype=torch.float32).pin_memory() for _ in frames]
+    cs = torch.cuda.Stream()
+    for f in range(len(frames)):
+        st.after(cs)
+        st.push_many(0, h_events=hs[f])
+        st.end_frame(dB[f % 2], dI[f % 2])
+        st.wait(cs)
+        with torch.cuda.stream(cs):
+            hB[f].copy_(dB[f % 2], non_blocking=True)
+            hI[f].copy_(dI[f % 2], non_blocking=True)
+    st.sync()
+    cs.synchronize()
+    for f, rf in enumerate(frames):
+        B, I = _batch(plan, kc.to_dev(rf))
+        assert np.array_equal(hB[f].numpy(), B) and np.array_equal(hI[f].numpy(), I), f
