@@ -497,6 +497,13 @@ def _volume(kb, flush, n_sm, peaks, peak_src, reps=10):
     torch.cuda.synchronize()
     ms_dec = _time_loop(lambda: plan.decompose(d_rf, rt, ws), reps, flush)
     ms_bf = _time_loop(lambda: plan.beamform(rt, B, I, ws), reps, flush)
+    F, Nu, L, Mu = info.n_bins, info.n_tx_used, info.n_elem, info.n_rx_used
+    X = torch.empty((F, Nu, L, 2), device="cuda")
+    Y = torch.empty((F, Nu, Mu, 2), device="cuda")
+    ms_spec = _time_loop(lambda: plan.spectrum(d_rf, X), reps, flush)
+    ms_shear = _time_loop(lambda: plan.shear(X, Y), reps, flush)
+    ms_inv = _time_loop(lambda: plan.inverse(Y, rt), reps, flush)
+    xy_bytes = float(X.numel() + Y.numel()) * 4
     vp = float(info.n_pairs) * info.nx * info.nz * info.ny
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     peak_pp = 8.0 * n_sm * sm_max * 1e6 / 1e9
@@ -504,10 +511,15 @@ def _volume(kb, flush, n_sm, peaks, peak_src, reps=10):
     res = {"array": "32x32", "transmits": int(info.n_tx), "receive_waves": int(info.n_rx_used),
            "pairs": int(info.n_pairs), "voxels": [int(info.nx), int(info.ny), int(info.nz)], "samples": int(info.n_samples),
            "volumes_per_s": round(1e3 / (ms_dec + ms_bf), 2), "decompose_ms": round(ms_dec, 4),
+           "stages_ms": {"spectrum": round(ms_spec, 4), "contraction": round(ms_shear, 4),
+                         "inverse": round(ms_inv, 4)},
+           "contraction": "separable %dx%d elements, %dx%d receive" % (info.sep_lx, info.sep_ly, info.sep_mx,
+                                                                         info.sep_my) if info.sep_lx else "full",
+           "contraction_hbm_gbs": round(xy_bytes / (ms_shear / 1e3) / 1e9, 1),
            "kk_image_ms": round(ms_bf, 4), "gvoxel_pairs_per_s": round(ach, 1),
            "gather_frac_of_8pp_per_clk_sm": round(ach / peak_pp, 4),
            "compression": round(info.compression_factor, 2), "status": plan.status()}
-    del plan, d_rf, ws, rt, B, I
+    del plan, d_rf, ws, rt, B, I, X, Y
     return res
 
 

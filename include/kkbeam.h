@@ -159,6 +159,11 @@ typedef struct kk_plan_info {
   int32_t launches_beamform;               /* kernels one kk_beamform / das_beamform enqueues */
   int32_t ny;                              /* y slices (1 for a 2D grid) */
   int32_t is_volume;                       /* a volumetric plan (2D array or y slices) */
+  /* FP32 volumetric plans whose elements fill an Lx x Ly grid and whose
+   * receive waves in use are every combination of Mx x-tilts and My y-tilts
+   * run the element sum as two per-axis contractions (the shear delay splits
+   * per axis); these are Lx, Ly, Mx, My then, all 0 for the full form */
+  int32_t sep_lx, sep_ly, sep_mx, sep_my;
 } kk_plan_info;
 
 /*

@@ -90,7 +90,9 @@ class kk_plan_info(ctypes.Structure):
                 ("rf_theta_bytes", ctypes.c_size_t), ("image_bytes", ctypes.c_size_t),
                 ("intensity_bytes", ctypes.c_size_t), ("compression_factor", ctypes.c_double),
                 ("launches_decompose", ctypes.c_int32), ("launches_beamform", ctypes.c_int32),
-                ("ny", ctypes.c_int32), ("is_volume", ctypes.c_int32)]
+                ("ny", ctypes.c_int32), ("is_volume", ctypes.c_int32),
+                ("sep_lx", ctypes.c_int32), ("sep_ly", ctypes.c_int32), ("sep_mx", ctypes.c_int32),
+                ("sep_my", ctypes.c_int32)]
 
 
 class kk_batch_frame(ctypes.Structure):

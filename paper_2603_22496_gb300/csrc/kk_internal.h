@@ -48,6 +48,12 @@ struct DevTables {
   // decomposition
   unsigned long long *phase = nullptr; // [Mu][L] frac(D/T) * 2^64
   uint32_t *phase32 = nullptr;         // [Mu][L] the same, rounded to 0.32 turns (tensor-core forms)
+  // separable volumetric contraction: per-bin phasors of the two axes
+  // ([F][Wf [Lf][Mf] padded to even, Ws [Ls][parts * osn] zero padded]),
+  // element slot in the staged grid, column of Y per receive combination
+  float2 *sep_w = nullptr;
+  int32_t *sep_slot = nullptr;         // [L] ls Lf + lf (f: the grid axis listed fastest)
+  int32_t *sep_col = nullptr;          // [Ms][Mf] receive position (0..Mu-1)
   int32_t *pair_q = nullptr;           // [P] (caller order) column of Y
   // KK gather (pairs in group-sorted order)
   int32_t *bf_row = nullptr;           // [P] row of rf_theta
@@ -112,6 +118,11 @@ struct kk_plan {
   // column table and can stream Y tiles by TMA
   bool pair_q_identity = false;
   double y0 = 0, dy = 0;
+  // separable FP32 contraction (0: the full form): element grid Lx x Ly,
+  // receive product Mx x My, transmits per item; the elements are listed
+  // y-fastest (else x-fastest, or in another order when not bulk)
+  int sep_Lx = 0, sep_Ly = 0, sep_Mx = 0, sep_My = 0, sep_tpc = 0;
+  bool sep_yfast = false, sep_bulk = false;
 };
 
 namespace kk {
@@ -174,6 +185,12 @@ cudaError_t launch_inverse(const kk_plan &p, const float2 *Y, int ncol, const in
                            int nrow, float2 *out, cudaStream_t s, const float *row_w = nullptr,
                            const int32_t *out_row = nullptr);
 cudaError_t launch_shear_f32(const kk_plan &p, const float2 *X, float2 *Y, cudaStream_t s);
+cudaError_t launch_shear_sep(const kk_plan &p, const float2 *X, float2 *Y, cudaStream_t s);
+size_t sep_shear_smem_bytes(int L, int Lf, int Ls, int Mf, int Ms, int msp, int tpc, bool bulk);
+// separable contraction's split of the slow-axis waves over thread parts:
+// parts, and waves per part (2, 4, 8 or 16); Ws rows hold parts * osn entries
+void sep_split(int Lf, int Ms, int tpc, int &parts, int &osn);
+constexpr int kSepMaxSlowWaves = 16;
 cudaError_t launch_shear_tc(const kk_plan &p, const void *X, float2 *Y, cudaStream_t s);
 size_t tc_shear_smem_bytes(int precision, int NP);
 // bytes of one complex spectrum value for the plan's precision: FP32 8,

@@ -103,6 +103,83 @@ void direction(bool vol, double ax, double ay, double &sx, double &sy, double &s
   sz = std::sqrt(1.0 - sx * sx - sy * sy);
 }
 
+// distinct values of v (ascending) and the rank of every entry among them
+void distinct_ranks(const std::vector<double> &v, std::vector<double> &vals, std::vector<int> &rank) {
+  vals = v;
+  std::sort(vals.begin(), vals.end());
+  vals.erase(std::unique(vals.begin(), vals.end()), vals.end());
+  rank.resize(v.size());
+  for (size_t q = 0; q < v.size(); ++q)
+    rank[q] = (int)(std::lower_bound(vals.begin(), vals.end(), v[q]) - vals.begin());
+}
+
+// Tables of the separable volumetric contraction (see k_shear_sep).
+struct SepTables {
+  int Lx = 0, Ly = 0, Mx = 0, My = 0;
+  bool yfast = false;     // elements listed y-fastest
+  bool row_major = false; // l = ls Lf + lf exactly (one bulk copy per chunk)
+  std::vector<unsigned long long> phx, phy;
+  std::vector<int32_t> slot, col;
+};
+
+// The element positions fill an Lx x Ly grid (each (x, y) once) and the
+// receive waves in use are every combination of Mx x-tilts with My y-tilts
+// (each once): then fs delta_l(o) / T = phx[ox][lx] + phy[oy][ly] with the
+// per-axis shear references of Eq. (compression).  False otherwise.
+bool separable_tables(const kk_plan_desc *d, int T, const std::vector<double> &u, const std::vector<double> &v,
+                      const std::vector<int> &rx_used, SepTables &st) {
+  const int L = (int)u.size(), Mu = (int)rx_used.size();
+  std::vector<double> ux, vy, ax, ay, tx, ty;
+  std::vector<int> lx, ly, ox, oy;
+  distinct_ranks(u, ux, lx);
+  distinct_ranks(v, vy, ly);
+  st.Lx = (int)ux.size();
+  st.Ly = (int)vy.size();
+  if ((long long)st.Lx * st.Ly != L) return false;
+  std::vector<char> seen((size_t)L, 0);
+  bool xf = true, yf = true;
+  for (int l = 0; l < L; ++l) {
+    const int g = ly[l] * st.Lx + lx[l];
+    if (seen[g]) return false;
+    seen[g] = 1;
+    xf = xf && g == l;
+    yf = yf && lx[l] * st.Ly + ly[l] == l;
+  }
+  st.yfast = yf && !xf;
+  st.row_major = xf || yf;
+  const int Lf = st.yfast ? st.Ly : st.Lx;
+  st.slot.resize(L);
+  for (int l = 0; l < L; ++l) st.slot[l] = st.yfast ? lx[l] * Lf + ly[l] : ly[l] * Lf + lx[l];
+  for (int a = 0; a < Mu; ++a) {
+    tx.push_back(d->rx_angles[rx_used[a]]);
+    ty.push_back(d->rx_angles_y ? d->rx_angles_y[rx_used[a]] : 0.0);
+  }
+  distinct_ranks(tx, ax, ox);
+  distinct_ranks(ty, ay, oy);
+  st.Mx = (int)ax.size();
+  st.My = (int)ay.size();
+  if ((long long)st.Mx * st.My != Mu) return false;
+  st.col.assign(Mu, -1);
+  for (int a = 0; a < Mu; ++a) {
+    int32_t &c = st.col[st.yfast ? ox[a] * st.My + oy[a] : oy[a] * st.Mx + ox[a]];
+    if (c >= 0) return false;
+    c = a;
+  }
+  st.phx.resize((size_t)st.Mx * st.Lx);
+  st.phy.resize((size_t)st.My * st.Ly);
+  for (int o = 0; o < st.Mx; ++o) {
+    const double sx = std::sin(ax[o]), xr = shear_reference(u, ax[o]);
+    for (int l = 0; l < st.Lx; ++l)
+      st.phx[(size_t)o * st.Lx + l] = frac64(d->fs * (xr - ux[l]) * sx / d->c / (double)T);
+  }
+  for (int o = 0; o < st.My; ++o) {
+    const double sy = std::sin(ay[o]), yr = shear_reference(v, sy);
+    for (int l = 0; l < st.Ly; ++l)
+      st.phy[(size_t)o * st.Ly + l] = frac64(d->fs * (yr - vy[l]) * sy / d->c / (double)T);
+  }
+  return true;
+}
+
 kk_status validate_common(const kk_plan_desc *d) {
   if (!d) { set_error("null plan description"); return KK_ERR_INVALID_ARG; }
   if (d->n_elem < 1 || !d->elem_x) { set_error("n_elem < 1 or elem_x null"); return KK_ERR_INVALID_ARG; }
@@ -332,6 +409,60 @@ kk_status make_kk(kk_plan &p, const kk_plan_desc *d) {
     }
   }
   const size_t off_phase = blob.add(phase);
+  // separable FP32 contraction when it takes at most half the products of
+  // the full one; a chunk of transmits (up to 8, at most 256 lanes along the
+  // fast axis, two buffers within 110 KB of shared memory) per item
+  SepTables sep;
+  size_t off_w = 0, off_slot = 0, off_col = 0;
+  if (p.vol && p.precision == KK_PREC_F32 && separable_tables(d, p.T, u, v, rx_used, sep)) {
+    const int Lf = sep.yfast ? sep.Ly : sep.Lx, Ls = sep.yfast ? sep.Lx : sep.Ly;
+    const int Mf = sep.yfast ? sep.My : sep.Mx, Ms = sep.yfast ? sep.Mx : sep.My;
+    const bool bulk = sep.row_major && p.L % 2 == 0;
+    const bool pays = 2LL * ((long long)Ms * Ls + (long long)Mf * Ms) * Lf <= (long long)p.L * p.Mu &&
+                      Ms <= kSepMaxSlowWaves;
+    int tpc = 0;
+    for (int t = 1; pays && t <= 8; t *= 2)
+      if (t * Lf <= 256) {
+        int parts = 0, osn = 0;
+        sep_split(Lf, Ms, t, parts, osn);
+        if (sep_shear_smem_bytes(p.L, Lf, Ls, Mf, Ms, parts * osn, t, bulk) <= 110 * 1024) tpc = t;
+      }
+    if (tpc > 0) {
+      p.sep_tpc = tpc;
+      p.sep_Lx = sep.Lx;
+      p.sep_Ly = sep.Ly;
+      p.sep_Mx = sep.Mx;
+      p.sep_My = sep.My;
+      p.sep_yfast = sep.yfast;
+      p.sep_bulk = bulk;
+      // per-bin phasors exp(2 pi i frac(k phi)) in FP64, k phi mod 1 exact in
+      // 0.64 fixed point, stored as FP32 pairs
+      const std::vector<unsigned long long> &phf = sep.yfast ? sep.phy : sep.phx;
+      const std::vector<unsigned long long> &phs = sep.yfast ? sep.phx : sep.phy;
+      int parts = 0, osn = 0;
+      sep_split(Lf, Ms, tpc, parts, osn);
+      const int msp = parts * osn;            // Ws row: the parts' waves, zeros past Ms
+      const size_t wf = (size_t)((Lf * Mf + 1) & ~1);
+      const size_t per_k = wf + (size_t)Ls * msp;
+      std::vector<float2> wtab((size_t)p.F * per_k, make_float2(0.f, 0.f));
+      auto phasor = [](unsigned long long ph) {
+        double turns = (double)ph * 0x1p-64;
+        if (turns >= 0.5) turns -= 1.0;
+        return make_float2((float)std::cos(2.0 * M_PI * turns), (float)std::sin(2.0 * M_PI * turns));
+      };
+      for (int k = 0; k < p.F; ++k) {
+        float2 *w = wtab.data() + (size_t)k * per_k;
+        const unsigned long long kk = (unsigned long long)k;
+        for (int lf = 0; lf < Lf; ++lf)
+          for (int of = 0; of < Mf; ++of) w[lf * Mf + of] = phasor(kk * phf[(size_t)of * Lf + lf]);
+        for (int ls = 0; ls < Ls; ++ls)
+          for (int os = 0; os < Ms; ++os) w[wf + (size_t)ls * msp + os] = phasor(kk * phs[(size_t)os * Ls + ls]);
+      }
+      off_w = blob.add(wtab);
+      off_slot = blob.add(sep.slot);
+      off_col = blob.add(sep.col);
+    }
+  }
   // 0.32 fixed-point copy for the reduced-precision contraction: k phi mod
   // 2^32 is then off by at most k 2^-33 turns (< 8e-7 rad for k < 1024)
   std::vector<uint32_t> phase32(phase.size());
@@ -440,6 +571,11 @@ kk_status make_kk(kk_plan &p, const kk_plan_desc *d) {
   p.t.tx_used = at<int32_t>(b, off_txu);
   p.t.phase = at<unsigned long long>(b, off_phase);
   p.t.phase32 = at<uint32_t>(b, off_phase32);
+  if (p.sep_Lx > 0) {
+    p.t.sep_w = at<float2>(b, off_w);
+    p.t.sep_slot = at<int32_t>(b, off_slot);
+    p.t.sep_col = at<int32_t>(b, off_col);
+  }
   p.t.pair_q = at<int32_t>(b, off_pq);
   p.t.bf_row = at<int32_t>(b, off_row);
   p.t.bf_A = at<long long>(b, off_A);
@@ -724,6 +860,10 @@ kk_status kk_plan_get_info(const kk_plan *p, kk_plan_info *info) {
   info->intensity_bytes = (size_t)p->grid.nx * p->grid.nz * p->ny * 4;
   info->ny = p->ny;
   info->is_volume = p->vol ? 1 : 0;
+  info->sep_lx = p->sep_Lx;
+  info->sep_ly = p->sep_Ly;
+  info->sep_mx = p->sep_Mx;
+  info->sep_my = p->sep_My;
   info->compression_factor = p->compression;
   info->launches_decompose = p->is_das ? 0 : 3;
   info->launches_beamform = (p->is_das ? 2 : 0) + (p->bf_split > 1 ? 2 : 1);

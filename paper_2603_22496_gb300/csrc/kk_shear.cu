@@ -12,6 +12,10 @@
 // fixed-point phases (k * phi mod 2^64 is exact integer arithmetic), so the
 // contraction reads only X from HBM and writes only Y.
 #include "kk_internal.h"
+#include "kk_tc.h"
+#include "kk_tma.h"
+
+#include <algorithm>
 
 namespace kk {
 
@@ -108,9 +112,232 @@ cudaError_t launch_ri(const kk_plan &p, const float2 *X, float2 *Y, cudaStream_t
   return cudaGetLastError();
 }
 
+// Separable form.  For a matrix array whose elements fill an Lx x Ly grid,
+// u_l = ux[lx], v_l = vy[ly], and receive waves on a product of Mx x-tilts
+// and My y-tilts, the volumetric shear delay splits per axis,
+//     fs delta_l(o) / T = phx[ox][lx] + phy[oy][ly]  (mod 1),
+// so W[o][l] = Wx[ox][lx] Wy[oy][ly] and the element sum of Eq. (compression)
+// becomes two short contractions per bin and transmit.  With the element
+// index l = ls Lf + lf (f the grid axis that varies fastest in the caller's
+// element order, s the other):
+//     Z[lf][os] = sum_ls X[ls][lf] Ws[os][ls],   Y[os][of] = sum_lf Z[lf][os] Wf[of][lf],
+// (Ms Ls + Mf Ms) Lf complex products instead of Lf Ls Mf Ms.
+//
+// The phasors of every bin, Wf[k][lf][of] and Ws[k][ls][os], are built by
+// the plan in FP64 (from the 0.64 fixed-point phases, k phi mod 1 exact) and
+// stored per bin as one contiguous run, so an item needs no sin/cos.
+//
+// Persistent CTAs walk the (bin, transmit chunk) items.  A chunk's spectra
+// X[k][i0 .. i0 + nt)[:] are one contiguous run: it and the bin's phasors
+// are fetched by bulk copies into the other of two shared-memory stages
+// while the current item is contracted (BULK; element orders that are not a
+// row-major grid use a plain gather through the slot table and one stage).
+// In the first contraction the lanes of a warp run along lf, so the
+// unpadded rows are read without bank conflicts and the weights Ws[ls][os]
+// are broadcasts; threads left over split the ls range.  Z goes to the
+// stage's X buffer once every thread has read its rows, and the second
+// contraction adds the parts.
+constexpr int kSepThreads = 256;
+
+struct SepArgs {
+  const float2 *X;
+  const float2 *W;       // [F][wf + ws]: Wf [Lf][Mf] (padded to even), Ws [Ls][msp] (zero pad)
+  const int32_t *slot;   // [L] ls Lf + lf (gather form)
+  const int32_t *col;    // [Ms][Mf] receive position
+  int L, Lf, Ls, Mf, Ms, msp, parts, Nu, Mu, tpc, chunks, n_items;
+  float2 *Y;
+  int *status;
+};
+
+__device__ __forceinline__ void cmac(float2 &acc, float2 a, float2 b) {
+  acc.x = fmaf(a.x, b.x, acc.x);
+  acc.x = fmaf(-a.y, b.y, acc.x);
+  acc.y = fmaf(a.x, b.y, acc.y);
+  acc.y = fmaf(a.y, b.x, acc.y);
+}
+
+// float2 counts of one stage: X / Z buffer, Wf, Ws (each a multiple of 2,
+// so every part starts on 16 bytes)
+struct SepLayout {
+  int buf, wf, ws;
+  __host__ __device__ SepLayout(int L, int Lf, int Ls, int Mf, int Ms, int msp, int tpc) {
+    const int x = tpc * L, z = tpc * Lf * Ms;
+    buf = ((x > z ? x : z) + 1) & ~1;
+    wf = (Lf * Mf + 1) & ~1;
+    ws = Ls * msp;
+  }
+  __host__ __device__ int stage() const { return buf + wf + ws; }
+};
+
+template <bool BULK, int OSN>
+__global__ void __launch_bounds__(kSepThreads) k_shear_sep(const SepArgs a) {
+  extern __shared__ __align__(16) float2 sep_smem[];
+  __shared__ __align__(8) uint64_t bar[2];
+  const SepLayout lay(a.L, a.Lf, a.Ls, a.Mf, a.Ms, a.msp, a.tpc);
+  const int tid = threadIdx.x;
+  if (BULK) {
+    if (tid == 0) {
+      tc::mbar_init(&bar[0], 1);
+      tc::mbar_init(&bar[1], 1);
+    }
+    tc::mbar_init_fence();
+  }
+  __syncthreads();
+  auto issue = [&](int item, int b) {  // one thread
+    const int k = item / a.chunks, i0 = (item - k * a.chunks) * a.tpc;
+    const unsigned xb = (unsigned)(min(a.tpc, a.Nu - i0) * a.L * (int)sizeof(float2));
+    const unsigned wb = (unsigned)((lay.wf + lay.ws) * (int)sizeof(float2));
+    float2 *st = sep_smem + (size_t)b * lay.stage();
+    tma::mbar_expect_tx(&bar[b], xb + wb);
+    tma::bulk_1d(tc::smem_u32(st), a.X + ((size_t)k * a.Nu + i0) * a.L, xb, &bar[b]);
+    tma::bulk_1d(tc::smem_u32(st + lay.buf), a.W + (size_t)k * (lay.wf + lay.ws), wb, &bar[b]);
+  };
+  int item = blockIdx.x;
+  if (BULK && tid == 0 && item < a.n_items) issue(item, 0);
+  for (int n = 0; item < a.n_items; item += gridDim.x, ++n) {
+    const int b = BULK ? (n & 1) : 0;
+    const int k = item / a.chunks, i0 = (item - k * a.chunks) * a.tpc;
+    const int nt = min(a.tpc, a.Nu - i0);
+    const bool next = item + (int)gridDim.x < a.n_items;
+    float2 *Xs = sep_smem + (size_t)b * lay.stage();
+    const float2 *Wf = Xs + lay.buf;   // [Lf][Mf]
+    const float2 *Ws = Wf + lay.wf;    // [Ls][msp]: part h's waves at h OSN
+    if (BULK) {
+      if (tid == 0 && next) issue(item + gridDim.x, b ^ 1);
+      const bool ok = tc::mbar_wait(&bar[b], (uint32_t)(n >> 1) & 1u);
+      if (__syncthreads_or(!ok)) {
+        if (tid == 0) {
+          atomicExch(a.status, (int)KK_ERR_TIMEOUT);
+          tc::mbar_wait(&bar[b], (uint32_t)(n >> 1) & 1u);
+          if (next) tc::mbar_wait(&bar[b ^ 1], (uint32_t)((n + 1) >> 1) & 1u);
+        }
+        return;
+      }
+    } else {
+      const float2 *Xk = a.X + ((size_t)k * a.Nu + i0) * a.L;
+      for (int e = tid; e < nt * a.L; e += kSepThreads) {
+        const int t = e / a.L, l = e - t * a.L;
+        Xs[(size_t)t * a.L + __ldg(a.slot + l)] = __ldg(Xk + e);
+      }
+      const float2 *Wk = a.W + (size_t)k * (lay.wf + lay.ws);
+      for (int e = tid; e < lay.wf + lay.ws; e += kSepThreads) Xs[lay.buf + e] = __ldg(Wk + e);
+      __syncthreads();
+    }
+
+    // first contraction: thread (part h, transmit t, lf) over every row ls
+    // for the OSN slow-axis waves of part h (zero weights past Ms), so each
+    // Z entry is one sum in a fixed order whatever the items hold
+    const int lanes = nt * a.Lf;
+    const bool worker = tid < a.parts * lanes;
+    const int h = tid / lanes, r = tid - h * lanes;
+    const int t = r / a.Lf, lf = r - t * a.Lf;
+    float2 acc[OSN];
+#pragma unroll
+    for (int j = 0; j < OSN; ++j) acc[j] = make_float2(0.f, 0.f);
+    if (worker) {
+      const float2 *xc = Xs + (size_t)t * a.L + lf;
+      const float4 *wc = reinterpret_cast<const float4 *>(Ws + h * OSN);
+      const int wstep = a.msp / 2;
+#pragma unroll 4
+      for (int ls = 0; ls < a.Ls; ++ls) {
+        const float2 x = xc[ls * a.Lf];
+        const float4 *w = wc + ls * wstep;
+#pragma unroll
+        for (int j = 0; j < OSN / 2; ++j) {
+          const float4 w2 = w[j];
+          cmac(acc[2 * j], make_float2(w2.x, w2.y), x);
+          cmac(acc[2 * j + 1], make_float2(w2.z, w2.w), x);
+        }
+      }
+    }
+    __syncthreads();  // every row of X read: Z may overwrite the buffer
+    if (worker) {
+      float2 *z = Xs + ((size_t)t * a.Lf + lf) * a.Ms;
+#pragma unroll
+      for (int j = 0; j < OSN; ++j)
+        if (h * OSN + j < a.Ms) z[h * OSN + j] = acc[j];
+    }
+    __syncthreads();
+
+    // second contraction: thread (t, os, of) over lf, four interleaved
+    // partial sums (short dependency chains)
+    float2 *Yk = a.Y + ((size_t)k * a.Nu + i0) * a.Mu;
+    const int per_t = a.Ms * a.Mf;
+    for (int e = tid; e < nt * per_t; e += kSepThreads) {
+      const int t2 = e / per_t, r2 = e - t2 * per_t;
+      const int os = r2 / a.Mf, of = r2 - os * a.Mf;
+      float2 s4[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) s4[j] = make_float2(0.f, 0.f);
+      const float2 *z = Xs + (size_t)t2 * a.Lf * a.Ms + os;
+      const float2 *wf = Wf + of;
+      int l2 = 0;
+      for (; l2 + 4 <= a.Lf; l2 += 4) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) cmac(s4[j], wf[(l2 + j) * a.Mf], z[(l2 + j) * a.Ms]);
+      }
+      for (; l2 < a.Lf; ++l2) cmac(s4[0], wf[l2 * a.Mf], z[l2 * a.Ms]);
+      Yk[(size_t)t2 * a.Mu + __ldg(a.col + r2)] =
+          make_float2((s4[0].x + s4[1].x) + (s4[2].x + s4[3].x), (s4[0].y + s4[1].y) + (s4[2].y + s4[3].y));
+    }
+    __syncthreads();  // stage free for the copy issued at the next item
+  }
+}
+
 }  // namespace
 
+size_t sep_shear_smem_bytes(int L, int Lf, int Ls, int Mf, int Ms, int msp, int tpc, bool bulk) {
+  return sizeof(float2) * (size_t)(bulk ? 2 : 1) * SepLayout(L, Lf, Ls, Mf, Ms, msp, tpc).stage();
+}
+
+void sep_split(int Lf, int Ms, int tpc, int &parts, int &osn) {
+  parts = std::max(1, std::min(Ms, kSepThreads / (tpc * Lf)));
+  const int need = (Ms + parts - 1) / parts;
+  osn = need <= 2 ? 2 : need <= 4 ? 4 : need <= 8 ? 8 : 16;
+}
+
+cudaError_t launch_shear_sep(const kk_plan &p, const float2 *X, float2 *Y, cudaStream_t s) {
+  SepArgs a;
+  a.X = X;
+  a.Y = Y;
+  a.W = p.t.sep_w;
+  a.status = p.t.status;
+  a.slot = p.t.sep_slot;
+  a.col = p.t.sep_col;
+  a.L = p.L;
+  a.Nu = p.Nu;
+  a.Mu = p.Mu;
+  a.Lf = p.sep_yfast ? p.sep_Ly : p.sep_Lx;
+  a.Ls = p.sep_yfast ? p.sep_Lx : p.sep_Ly;
+  a.Mf = p.sep_yfast ? p.sep_My : p.sep_Mx;
+  a.Ms = p.sep_yfast ? p.sep_Mx : p.sep_My;
+  a.tpc = p.sep_tpc;
+  int osn = 0;
+  sep_split(a.Lf, a.Ms, a.tpc, a.parts, osn);
+  a.msp = a.parts * osn;
+  a.chunks = (p.Nu + p.sep_tpc - 1) / p.sep_tpc;
+  a.n_items = p.F * a.chunks;
+  const bool bulk = p.sep_bulk && ((uintptr_t)X % 16) == 0;
+  const size_t smem = sep_shear_smem_bytes(p.L, a.Lf, a.Ls, a.Mf, a.Ms, a.msp, a.tpc, bulk);
+  void (*k)(SepArgs) = nullptr;
+  switch (osn) {
+    case 2: k = bulk ? k_shear_sep<true, 2> : k_shear_sep<false, 2>; break;
+    case 4: k = bulk ? k_shear_sep<true, 4> : k_shear_sep<false, 4>; break;
+    case 8: k = bulk ? k_shear_sep<true, 8> : k_shear_sep<false, 8>; break;
+    default: k = bulk ? k_shear_sep<true, 16> : k_shear_sep<false, 16>; break;
+  }
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int sms = 148, per_sm = 1;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p.device);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kSepThreads, smem);
+  const int grid = std::max(1, std::min(a.n_items, sms * std::max(per_sm, 1)));
+  k<<<grid, kSepThreads, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_shear_f32(const kk_plan &p, const float2 *X, float2 *Y, cudaStream_t s) {
+  if (p.sep_Lx > 0) return launch_shear_sep(p, X, Y, s);
   const int ri = (p.Nu + 15) / 16;
   switch (ri) {
     case 1: return launch_ri<1>(p, X, Y, s);

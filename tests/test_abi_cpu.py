@@ -110,7 +110,7 @@ int main(void) {
   printf("kk_stream_info %zu\\n", sizeof(kk_stream_info));
   printf("kk_plan_desc %zu\\nkk_plan_info %zu\\n", sizeof(kk_plan_desc), sizeof(kk_plan_info));
   P(kk_plan_desc, aperture); P(kk_plan_desc, elem_y); P(kk_plan_desc, rx_angles_y); P(kk_plan_desc, ny);
-  P(kk_plan_desc, dy); P(kk_plan_info, ny); P(kk_plan_info, is_volume);
+  P(kk_plan_desc, dy); P(kk_plan_info, ny); P(kk_plan_info, is_volume); P(kk_plan_info, sep_my);
   P(kk_stream_info, n_groups); P(kk_stream_info, events_pushed); P(kk_stream_info, device_bytes);
   return 0;
 }
@@ -140,7 +140,8 @@ int main(void) {
             "kk_plan_desc.elem_y": kb.kk_plan_desc.elem_y.offset,
             "kk_plan_desc.rx_angles_y": kb.kk_plan_desc.rx_angles_y.offset,
             "kk_plan_desc.ny": kb.kk_plan_desc.ny.offset, "kk_plan_desc.dy": kb.kk_plan_desc.dy.offset,
-            "kk_plan_info.ny": kb.kk_plan_info.ny.offset, "kk_plan_info.is_volume": kb.kk_plan_info.is_volume.offset}
+            "kk_plan_info.ny": kb.kk_plan_info.ny.offset, "kk_plan_info.is_volume": kb.kk_plan_info.is_volume.offset,
+            "kk_plan_info.sep_my": kb.kk_plan_info.sep_my.offset}
     assert {k: int(v) for k, v in got.items()} == want
 
 

@@ -57,6 +57,7 @@ def test_volume_full_matches_oracle(small):
     plan = _plan(w, ps)
     info = plan.info
     assert info.is_volume == 1 and info.ny == 48 and info.n_pairs == 9 * 49
+    assert (info.sep_lx, info.sep_ly, info.sep_mx, info.sep_my) == (16, 16, 7, 7)
     B, I, rt = _run(plan, w.rf)
     assert B.shape == (1, 48, 64, 48)
     y = V.decompose3(w.rf, w.elem_x, w.elem_y, ps, FS, C)
@@ -64,6 +65,61 @@ def test_volume_full_matches_oracle(small):
     ref = V.kk_beamform3(y, w.elem_x, w.elem_y, ps, w.grid, w.grid_y, FS, C)
     assert kc.rel_l2(B, ref) <= TOL
     assert kc.rel_l2(I, np.abs(ref[0]) ** 2) <= 2 * TOL
+
+
+@pytest.mark.parametrize("order", ["shuffled", "y_fastest"])
+def test_separable_contraction_any_order_and_against_full_form(small, order):
+    """The separable contraction (16 x 16 grid, 5 x 4 receive product) with
+    elements listed in shuffled order (gathered into the grid) or y-fastest
+    (bulk copies, the axes' roles swapped) and receive waves in shuffled
+    order matches the oracle; one more receive wave off the product turns
+    the plan to the full form, whose records of the shared pairs agree with
+    the separable ones."""
+    w = small
+    rng = np.random.default_rng(11)
+    rx1x = schemes.even_receive_set(np.deg2rad(12.0), 5)
+    rx1y = schemes.even_receive_set(np.deg2rad(9.0), 4)
+    rxx, rxy = np.tile(rx1x, 4), np.repeat(rx1y, 5)
+    ro = rng.permutation(rxx.shape[0])
+    L = w.elem_x.shape[0]
+    eo = rng.permutation(L) if order == "shuffled" else np.arange(L).reshape(16, 16).T.ravel()
+    ex, ey, rf = w.elem_x[eo], w.elem_y[eo], np.ascontiguousarray(w.rf[:, eo])
+    ps = V.product_set(w.tx_ax, w.tx_ay, [(rxx[ro], rxy[ro])])
+    pairs = np.stack([ps.tx_index, ps.rx_index], 1).astype(np.int32)
+
+    def plan_of(bx, by, pr):
+        return kb.Plan(ex, w.tx_ax, w.grid, w.c, w.fs, w.n_samples, kc.rf_dtype_of(w), rx_angles=bx, pairs=pr,
+                       compound=kb.KK_COMPOUND_COHERENT, elem_y=ey, tx_angles_y=w.tx_ay, rx_angles_y=by,
+                       grid_y=w.grid_y)
+
+    sep = plan_of(ps.rx_ax, ps.rx_ay, pairs)
+    assert (sep.info.sep_lx, sep.info.sep_ly, sep.info.sep_mx, sep.info.sep_my) == (16, 16, 5, 4)
+    B, _, rt = _run(sep, rf)
+    y = V.decompose3(rf, ex, ey, ps, FS, C)
+    assert kc.rel_l2(rt, y) <= 3e-6
+    assert kc.rel_l2(B, V.kk_beamform3(y, ex, ey, ps, w.grid, w.grid_y, FS, C)) <= TOL
+    # one extra receive wave: not a product any more
+    bx, by = np.append(ps.rx_ax, np.deg2rad(1.0)), np.append(ps.rx_ay, np.deg2rad(-2.0))
+    extra = np.array([[i, bx.shape[0] - 1] for i in range(w.tx_ax.shape[0])], np.int32)
+    full = plan_of(bx, by, np.concatenate([pairs, extra]))
+    assert full.info.sep_lx == 0
+    _, _, rt_full = _run(full, rf)
+    assert kc.rel_l2(rt_full[:pairs.shape[0]], rt) <= 2e-6
+
+
+def test_separable_contraction_odd_grid():
+    """7 x 5 elements (odd L: the gathered form), 5 x 5 receive waves, 3 x 2
+    tilts: the separable contraction against the oracle, and a batch of
+    transmits that does not fill the last chunk."""
+    w = kksynth.volume_workload(seed=3200, lx=7, ly=5, ntx=3, nty=2, n_samples=512, nx=24, ny=16, nz=32,
+                                speckle=200)
+    ps = V.product_set(w.tx_ax, w.tx_ay, [_rx_product(10.0, 5)])
+    plan = _plan(w, ps)
+    assert (plan.info.sep_lx, plan.info.sep_ly, plan.info.sep_mx, plan.info.sep_my) == (7, 5, 5, 5)
+    B, _, rt = _run(plan, w.rf)
+    y = V.decompose3(w.rf, w.elem_x, w.elem_y, ps, FS, C)
+    assert kc.rel_l2(rt, y) <= 3e-6
+    assert kc.rel_l2(B, V.kk_beamform3(y, w.elem_x, w.elem_y, ps, w.grid, w.grid_y, FS, C)) <= TOL
 
 
 def test_volume_hybrid_groups_incoherent(small):
