@@ -49,8 +49,10 @@ __host__ __device__ constexpr int fft_radix(int F, int i) {
 // Shared-memory position of point e of a transform: one padding slot per 32
 // points, so that the radix-16 pass's stride-16 writes hit distinct banks.
 __host__ __device__ constexpr int fft_pad(int e) { return e + (e >> 5); }
-// row stride (complex points) of one transform in shared memory
-__host__ __device__ constexpr int fft_row(int F) { return F + F / 32 + 1; }
+// row stride (complex points) of one transform in shared memory: 2 mod 16,
+// so that 8 transforms x 2 neighbouring points read by a half-warp hit 16
+// distinct 8-byte bank pairs
+__host__ __device__ constexpr int fft_row(int F) { return F + F / 32 + 2; }
 __host__ __device__ constexpr int fft_ns(int F, int i) {
   int ns = 1;
   for (int k = 0; k < i; ++k) ns *= fft_radix(F, k);
@@ -185,14 +187,15 @@ __device__ __forceinline__ void stockham_pass(float2 *buf, const float2 *tw, int
   __syncthreads();
 }
 
-template <int F, int FS, int NTR, int NT, int I>
+// passes I .. END - 1 in place
+template <int F, int FS, int NTR, int NT, int I, int END = fft_npass(F)>
 __device__ __forceinline__ void run_passes(float2 *buf, const float2 *tw, int tid) {
-  if constexpr (I < fft_npass(F)) {
+  if constexpr (I < END) {
     constexpr int R = fft_radix(F, I);
     constexpr int NS = fft_ns(F, I);
     constexpr int OFF = fft_twoff(F, I);
     stockham_pass<R, NS, F, FS, NTR, NT>(buf, tw + OFF, tid);
-    run_passes<F, FS, NTR, NT, I + 1>(buf, tw, tid);
+    run_passes<F, FS, NTR, NT, I + 1, END>(buf, tw, tid);
   }
 }
 
@@ -296,6 +299,82 @@ __global__ void __launch_bounds__(NT) k_spectrum(const TIn *__restrict__ rf,
   }
 }
 
+// ---- fused first and last passes of the persistent spectrum ----------------
+// First pass (NS = 1) read straight from the staged real records: point n of
+// record tr is the sample pair (2n, 2n + 1).  Writes the Stockham output of
+// the pass into buf (a different buffer, so no barrier between read and
+// write).  Records tr >= nc are not loaded and give zeros.
+template <int F, int FS, int C, int NT, typename TIn>
+__device__ __forceinline__ void first_pass_staged(const uint4 *stg, int nv, int nc, float2 *buf, int tid) {
+  constexpr int R = fft_radix(F, 0);
+  static_assert(fft_ns(F, 0) == 1, "first pass has NS = 1");
+  constexpr int NBF = C * (F / R);
+#pragma unroll 2
+  for (int j = tid; j < NBF; j += NT) {
+    const int tr = j / (F / R), jj = j - tr * (F / R);
+    float2 v[R];
+    const TIn *rec = reinterpret_cast<const TIn *>(stg + (size_t)tr * nv);
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = tr < nc ? load_pair(rec + 2 * (jj + r * (F / R))) : make_float2(0.f, 0.f);
+    dft<R>(v);
+    float2 *dst = buf + tr * FS;
+#pragma unroll
+    for (int r = 0; r < R; ++r) dst[fft_pad(jj * R + r)] = v[r];
+  }
+}
+
+// Last pass (NS = F / R) fused with the split of the packed transform into the
+// analytic spectrum, which pairs Z[k] with Z[F - k].  Output r of butterfly jj
+// is point jj + r NS, and F - (jj + r NS) is output R - 1 - r of butterfly
+// NS - jj; so one thread takes butterflies t and NS - t (t = 1 .. NS/2 - 1),
+// or 0 and NS/2 (both paired with themselves), and forms the spectrum in
+// registers.  Lanes run over transforms first, so a warp store writes runs of
+// C adjacent channels.
+template <int F, int FS, int C, int NT, typename TOut>
+__device__ __forceinline__ void last_pass_spectrum(const float2 *buf, const float2 *tw, const float2 *rw, int nc,
+                                                   int c0, int n_ch, float xscale, TOut *X, int tid) {
+  constexpr int LAST = fft_npass(F) - 1;
+  constexpr int R = fft_radix(F, LAST);
+  constexpr int NS = fft_ns(F, LAST);
+  static_assert(NS * R == F && NS % 2 == 0, "last pass");
+  constexpr int H = NS / 2;
+  const float2 *twl = tw + fft_twoff(F, LAST);
+  for (int idx = tid; idx < C * H; idx += NT) {
+    const int tr = idx % C, t = idx / C;
+    if (tr >= nc) continue;
+    const int A = t, B = t == 0 ? H : NS - t;
+    const float2 *src = buf + tr * FS;
+    float2 va[R], vb[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      va[r] = src[fft_pad(A + r * NS)];
+      vb[r] = src[fft_pad(B + r * NS)];
+    }
+#pragma unroll
+    for (int r = 1; r < R; ++r) {
+      va[r] = cmul(va[r], twl[A * (R - 1) + (r - 1)]);
+      vb[r] = cmul(vb[r], twl[B * (R - 1) + (r - 1)]);
+    }
+    dft<R>(va);
+    dft<R>(vb);
+    auto emit = [&](int k, float2 zk, float2 zm) {
+      // E = (Z[k] + conj Z[F-k]) / 2,  O = (Z[k] - conj Z[F-k]) / (2i)
+      const float2 e = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
+      const float2 o = make_float2(0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
+      float2 x = cadd(e, cmul(__ldg(rw + k), o));
+      const float h = (k == 0) ? xscale : 2.f * xscale;
+      x.x *= h;
+      x.y *= h;
+      store_x(X, (size_t)k * n_ch + c0 + tr, x);
+    };
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      emit(A + r * NS, va[r], t == 0 ? va[(R - r) % R] : vb[R - 1 - r]);
+      emit(B + r * NS, vb[r], t == 0 ? vb[R - 1 - r] : va[R - 1 - r]);
+    }
+  }
+}
+
 // Persistent form of k_spectrum: each CTA loops over groups of C channels;
 // the group's records (contiguous T samples each) arrive by 1D bulk copies in
 // a staging buffer while the previous group is transformed and stored.
@@ -350,35 +429,11 @@ __global__ void __launch_bounds__(NT, (F == 1024 || F == 2048) ? 2 : 1) k_spectr
     phase ^= 1u;
     const int c0 = g * C;
     const int nc = min(C, n_ch - c0);
-#pragma unroll 4
-    for (int idx = tid; idx < C * NV; idx += NT) {
-      const int cc = idx / NV, v = idx - cc * NV;
-      float2 z[VE / 2];
-      if (cc < nc) {
-        unpack16(stg[idx], rf, z);
-      } else {
-#pragma unroll
-        for (int q = 0; q < VE / 2; ++q) z[q] = make_float2(0.f, 0.f);
-      }
-#pragma unroll
-      for (int q = 0; q < VE / 2; ++q) buf[cc * FS + fft_pad(v * (VE / 2) + q)] = z[q];
-    }
+    first_pass_staged<F, FS, C, NT, TIn>(stg, NV, nc, buf, tid);
     __syncthreads();  // staging consumed: prefetch the next group
     if (tid == 0 && g + (int)gridDim.x < n_groups) issue(g + gridDim.x);
-    run_passes<F, FS, C, NT, 0>(buf, s_tw, tid);
-    for (int idx = tid; idx < C * F; idx += NT) {
-      const int k = idx / C, cc = idx - k * C;
-      if (cc >= nc) continue;
-      const float2 zk = buf[cc * FS + fft_pad(k)];
-      const float2 zm = buf[cc * FS + fft_pad(k == 0 ? 0 : F - k)];
-      const float2 e = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
-      const float2 o = make_float2(0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
-      float2 x = cadd(e, cmul(__ldg(rw + k), o));
-      const float h = (k == 0) ? xscale : 2.f * xscale;
-      x.x *= h;
-      x.y *= h;
-      store_x(X, (size_t)k * n_ch + c0 + cc, x);
-    }
+    run_passes<F, FS, C, NT, 1, fft_npass(F) - 1>(buf, s_tw, tid);
+    last_pass_spectrum<F, FS, C, NT, TOut>(buf, s_tw, rw, nc, c0, n_ch, xscale, X, tid);
     __syncthreads();  // buffers free for the next group
   }
   (void)s_row;
@@ -431,6 +486,78 @@ __global__ void __launch_bounds__(NT) k_inverse(const float2 *__restrict__ Y, in
     const float4 o = make_float4(ev.x * sc, -ev.y * sc, od.x * sc, -od.y * sc);
     const size_t orow = out_row ? (size_t)__ldg(out_row + row) : (size_t)row;
     *reinterpret_cast<float4 *>(out + orow * T + 2 * m) = o;
+  }
+}
+
+// ---- fused first and last passes of the persistent inverse -----------------
+// First pass (NS = 1) of the 2C transforms read straight from the staged Y
+// tile [F][C]: transform 2 rr takes conj Y[k][rr], transform 2 rr + 1 takes
+// conj Y[k][rr] e^{-2 pi i k / T}.  Lanes run over records first, so a warp
+// reads contiguous runs of the tile.
+template <int F, int FS, int C, int NT>
+__device__ __forceinline__ void first_pass_inverse(const float2 *stg, const float2 *rw, float2 *buf, int tid) {
+  constexpr int R = fft_radix(F, 0);
+  static_assert(fft_ns(F, 0) == 1, "first pass has NS = 1");
+  constexpr int NB = F / R;
+  for (int j = tid; j < 2 * C * NB; j += NT) {
+    const int rr = j % C, rest = j / C;
+    const int jj = rest % NB, odd = rest / NB;
+    float2 v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int k = jj + r * NB;
+      const float2 y = stg[k * C + rr];
+      const float2 a = make_float2(y.x, -y.y);
+      v[r] = odd ? cmul(a, __ldg(rw + k)) : a;
+    }
+    dft<R>(v);
+    float2 *dst = buf + (2 * rr + odd) * FS;
+#pragma unroll
+    for (int r = 0; r < R; ++r) dst[fft_pad(jj * R + r)] = v[r];
+  }
+}
+
+// Last pass (NS = F / R) of both transforms of a record, fused with the
+// store: output r of butterfly jj is point m = jj + r NS of the even and the
+// odd transform, i.e. samples 2m and 2m + 1 of the record, written as one
+// 16-byte store (conjugated and scaled).  Lanes run over jj, so a warp
+// store covers 512 contiguous bytes.
+template <int F, int FS, int C, int NT>
+__device__ __forceinline__ void last_pass_inverse(const float2 *buf, const float2 *tw, int r0, int nrow,
+                                                  float2 *out, float scale, const float *row_w,
+                                                  const int32_t *out_row, int tid) {
+  constexpr int LAST = fft_npass(F) - 1;
+  constexpr int R = fft_radix(F, LAST);
+  constexpr int NS = fft_ns(F, LAST);
+  constexpr int T = 2 * F;
+  const float2 *twl = tw + fft_twoff(F, LAST);
+  for (int idx = tid; idx < C * NS; idx += NT) {
+    const int rr = idx / NS, jj = idx - rr * NS;
+    const int row = r0 + rr;
+    if (row >= nrow) continue;
+    const float2 *se = buf + (2 * rr) * FS, *so = se + FS;
+    float2 ve[R], vo[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      ve[r] = se[fft_pad(jj + r * NS)];
+      vo[r] = so[fft_pad(jj + r * NS)];
+    }
+#pragma unroll
+    for (int r = 1; r < R; ++r) {
+      const float2 w = twl[jj * (R - 1) + (r - 1)];
+      ve[r] = cmul(ve[r], w);
+      vo[r] = cmul(vo[r], w);
+    }
+    dft<R>(ve);
+    dft<R>(vo);
+    const float sc = row_w ? scale * __ldg(row_w + row) : scale;
+    float2 *orow = out + (out_row ? (size_t)__ldg(out_row + row) : (size_t)row) * T;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int m = jj + r * NS;
+      *reinterpret_cast<float4 *>(orow + 2 * m) =
+          make_float4(ve[r].x * sc, -ve[r].y * sc, vo[r].x * sc, -vo[r].y * sc);
+    }
   }
 }
 
@@ -489,29 +616,13 @@ __global__ void __launch_bounds__(NT, (F == 1024 || F == 2048) ? 2 : 1) k_invers
     }
     phase ^= 1u;
     const int r0 = g * C;
-    // spread: conj(Y) to the even transform, conj(Y) e^{-2 pi i k / T} to the odd one
-#pragma unroll 4
-    for (int idx = tid; idx < C * F; idx += NT) {
-      const int k = idx / C, rr = idx - k * C;
-      const float2 y = stg[idx];
-      const float2 a = make_float2(y.x, -y.y);
-      buf[(2 * rr) * FS + fft_pad(k)] = a;
-      buf[(2 * rr + 1) * FS + fft_pad(k)] = cmul(a, __ldg(rw + k));
-    }
+    // first pass from the staged tile: conj(Y) to the even transform,
+    // conj(Y) e^{-2 pi i k / T} to the odd one
+    first_pass_inverse<F, FS, C, NT>(stg, rw, buf, tid);
     __syncthreads();  // staging consumed: prefetch the next group while transforming this one
     if (tid == 0 && g + (int)gridDim.x < n_groups) issue(g + gridDim.x);
-    run_passes<F, FS, 2 * C, NT, 0>(buf, s_tw, tid);
-    for (int idx = tid; idx < C * F; idx += NT) {
-      const int rr = idx / F, m = idx - rr * F;
-      const int row = r0 + rr;
-      if (row >= nrow) continue;
-      const float2 ev = buf[(2 * rr) * FS + fft_pad(m)];
-      const float2 od = buf[(2 * rr + 1) * FS + fft_pad(m)];
-      const float sc = row_w ? scale * __ldg(row_w + row) : scale;
-      const float4 o = make_float4(ev.x * sc, -ev.y * sc, od.x * sc, -od.y * sc);
-      const size_t orow = out_row ? (size_t)__ldg(out_row + row) : (size_t)row;
-      *reinterpret_cast<float4 *>(out + orow * T + 2 * m) = o;
-    }
+    run_passes<F, FS, 2 * C, NT, 1, fft_npass(F) - 1>(buf, s_tw, tid);
+    last_pass_inverse<F, FS, C, NT>(buf, s_tw, r0, nrow, out, scale, row_w, out_row, tid);
     __syncthreads();  // transforms stored: the buffers are free for the next group
   }
 }
