@@ -105,6 +105,126 @@ __global__ void __launch_bounds__(256) k_shear_f32(const float2 *__restrict__ X,
   }
 }
 
+// Few transmits (Nu <= 64): a W element serves only Nu transmits, so its
+// sin/cos, not the products, dominated the form above (and a 16 RI transmit
+// tile was mostly padding).  This form takes TN = 8 .. 64 transmits
+// and 4 AG receive angles (the tile with the least padded work), and KB
+// consecutive bins: W of the first bin and
+// E = exp(2 pi i phi) come from the fixed-point phases once per element
+// chunk, later bins step W <- W E (one complex product), at most KB - 1
+// steps from an exact value.
+constexpr int kLCn = 32;   // elements per chunk
+constexpr int kKBn = 4;    // bins per CTA
+
+template <int TN, int AG>
+__global__ void __launch_bounds__(TN * AG, 768 / (TN * AG)) k_shear_f32n(const float2 *__restrict__ X,
+                                                    const unsigned long long *__restrict__ phase,
+                                                    int L, int Nu, int Mu, int F,
+                                                    float2 *__restrict__ Y) {
+  constexpr int NT = TN * AG;    // threads: TN transmits x AG angle groups of 4
+  constexpr int TO = 4 * AG;
+  extern __shared__ __align__(16) float2 n_smem[];
+  float2 (*Ws)[TO] = reinterpret_cast<float2 (*)[TO]>(n_smem);               // [kLCn][TO]
+  float2 (*Es)[TO] = reinterpret_cast<float2 (*)[TO]>(n_smem + kLCn * TO);   // [kLCn][TO]
+  float2 (*Xs)[TN + 1] = reinterpret_cast<float2 (*)[TN + 1]>(n_smem + 2 * kLCn * TO);
+  const int k0 = blockIdx.x * kKBn;
+  const int nk = min(kKBn, F - k0);
+  const int o0 = blockIdx.y * TO;
+  const int i0 = blockIdx.z * TN;
+  const int tid = threadIdx.x;
+  // transmit fastest across lanes: a warp reads 32 / TN angle groups of W
+  // (one or two 128-byte runs) and TN neighbouring X values per element
+  const int ty = tid % TN;   // transmit
+  const int tx = tid / TN;   // angle group
+  const unsigned long long kk64 = (unsigned long long)k0;
+
+  float2 acc[kKBn][4];
+#pragma unroll
+  for (int b = 0; b < kKBn; ++b)
+#pragma unroll
+    for (int a = 0; a < 4; ++a) acc[b][a] = make_float2(0.f, 0.f);
+
+  auto phasor = [](unsigned long long ph) {
+    const int hi = (int)(ph >> 32);   // turns in [-1/2, 1/2) * 2^32
+    float sn, cs;
+    sincospif((float)hi * 0x1p-31f, &sn, &cs);
+    return make_float2(cs, sn);
+  };
+
+  for (int l0 = 0; l0 < L; l0 += kLCn) {
+    for (int e = tid; e < kLCn * TO; e += NT) {
+      const int ll = e / TO, oo = e - ll * TO;
+      const int o = o0 + oo, l = l0 + ll;
+      float2 w = make_float2(0.f, 0.f), r = make_float2(0.f, 0.f);
+      if (o < Mu && l < L) {
+        const unsigned long long ph = __ldg(phase + (size_t)o * L + l);
+        w = phasor(ph * kk64);
+        r = phasor(ph);
+      }
+      Ws[ll][oo] = w;
+      Es[ll][oo] = r;
+    }
+    const int lmax = min(kLCn, L - l0);
+#pragma unroll
+    for (int b = 0; b < kKBn; ++b) {
+      if (b >= nk) break;
+      if (b > 0) {
+        for (int e = tid; e < kLCn * TO; e += NT) {
+          const int ll = e / TO, oo = e - ll * TO;
+          const float2 w = Ws[ll][oo], r = Es[ll][oo];
+          Ws[ll][oo] = make_float2(fmaf(w.x, r.x, -w.y * r.y), fmaf(w.x, r.y, w.y * r.x));
+        }
+      }
+      const float2 *Xk = X + (size_t)(k0 + b) * Nu * L;
+      for (int e = tid; e < kLCn * TN; e += NT) {
+        const int ii = e / kLCn, ll = e - ii * kLCn;
+        const int i = i0 + ii, l = l0 + ll;
+        Xs[ll][ii] = (i < Nu && l < L) ? Xk[(size_t)i * L + l] : make_float2(0.f, 0.f);
+      }
+      __syncthreads();
+      for (int ll = 0; ll < lmax; ++ll) {
+        const float4 w01 = *reinterpret_cast<const float4 *>(&Ws[ll][tx * 4]);
+        const float4 w23 = *reinterpret_cast<const float4 *>(&Ws[ll][tx * 4 + 2]);
+        const float2 w[4] = {make_float2(w01.x, w01.y), make_float2(w01.z, w01.w),
+                             make_float2(w23.x, w23.y), make_float2(w23.z, w23.w)};
+        const float2 x = Xs[ll][ty];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+          acc[b][a].x = fmaf(w[a].x, x.x, acc[b][a].x);
+          acc[b][a].x = fmaf(-w[a].y, x.y, acc[b][a].x);
+          acc[b][a].y = fmaf(w[a].x, x.y, acc[b][a].y);
+          acc[b][a].y = fmaf(w[a].y, x.x, acc[b][a].y);
+        }
+      }
+      __syncthreads();
+    }
+  }
+  const int i = i0 + ty;
+  if (i >= Nu) return;
+#pragma unroll
+  for (int b = 0; b < kKBn; ++b) {
+    if (b >= nk) break;
+    float2 *Yk = Y + ((size_t)(k0 + b) * Nu + i) * Mu;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      const int o = o0 + tx * 4 + a;
+      if (o < Mu) Yk[o] = acc[b][a];
+    }
+  }
+}
+
+template <int TN, int AG>
+cudaError_t launch_n(const kk_plan &p, const float2 *X, float2 *Y, cudaStream_t s) {
+  constexpr int TO = 4 * AG;
+  const size_t smem = sizeof(float2) * (2 * (size_t)kLCn * TO + (size_t)kLCn * (TN + 1));
+  cudaError_t e =
+      cudaFuncSetAttribute(k_shear_f32n<TN, AG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const dim3 grid((p.F + kKBn - 1) / kKBn, (p.Mu + TO - 1) / TO, (p.Nu + TN - 1) / TN);
+  k_shear_f32n<TN, AG><<<grid, TN * AG, smem, s>>>(X, p.t.phase, p.L, p.Nu, p.Mu, p.F, Y);
+  return cudaGetLastError();
+}
+
 template <int RI>
 cudaError_t launch_ri(const kk_plan &p, const float2 *X, float2 *Y, cudaStream_t s) {
   const dim3 grid(p.F, (p.Mu + kTO - 1) / kTO, (p.Nu + 16 * RI - 1) / (16 * RI));
@@ -338,6 +458,40 @@ cudaError_t launch_shear_sep(const kk_plan &p, const float2 *X, float2 *Y, cudaS
 
 cudaError_t launch_shear_f32(const kk_plan &p, const float2 *X, float2 *Y, cudaStream_t s) {
   if (p.sep_Lx > 0) return launch_shear_sep(p, X, Y, s);
+  if (p.Nu <= 64) {
+    // the tile (TN transmits x AG groups of 4 angles, 32 .. 256 threads)
+    // with the least padded work per bin group, then the fewest CTAs
+    int bt = 0, ba = 0;
+    long long best = 0;
+    for (int tn : {8, 16, 32, 64})
+      for (int ag : {1, 2, 4, 8, 16, 32}) {
+        if (tn * ag < 32 || tn * ag > 256) continue;
+        const long long tiles = (long long)((p.Mu + 4 * ag - 1) / (4 * ag)) * ((p.Nu + tn - 1) / tn);
+        const long long work = tiles * tn * ag;
+        if (bt == 0 || work < best || (work == best && tn * ag > bt * ba)) {
+          bt = tn;
+          ba = ag;
+          best = work;
+        }
+      }
+    switch (bt * 100 + ba) {
+      case 804: return launch_n<8, 4>(p, X, Y, s);
+      case 808: return launch_n<8, 8>(p, X, Y, s);
+      case 816: return launch_n<8, 16>(p, X, Y, s);
+      case 832: return launch_n<8, 32>(p, X, Y, s);
+      case 1602: return launch_n<16, 2>(p, X, Y, s);
+      case 1604: return launch_n<16, 4>(p, X, Y, s);
+      case 1608: return launch_n<16, 8>(p, X, Y, s);
+      case 1616: return launch_n<16, 16>(p, X, Y, s);
+      case 3201: return launch_n<32, 1>(p, X, Y, s);
+      case 3202: return launch_n<32, 2>(p, X, Y, s);
+      case 3204: return launch_n<32, 4>(p, X, Y, s);
+      case 3208: return launch_n<32, 8>(p, X, Y, s);
+      case 6401: return launch_n<64, 1>(p, X, Y, s);
+      case 6402: return launch_n<64, 2>(p, X, Y, s);
+      default: return launch_n<64, 4>(p, X, Y, s);
+    }
+  }
   const int ri = (p.Nu + 15) / 16;
   switch (ri) {
     case 1: return launch_ri<1>(p, X, Y, s);

@@ -58,6 +58,33 @@ def test_stage_shear_matches_oracle():
     assert kc.rel_l2(kc.cplx(Y), ref) <= 2e-6
 
 
+@pytest.mark.parametrize("n_tx,M", [(5, 150), (11, 70), (24, 20), (40, 10)])
+def test_stage_shear_few_transmits_matches_oracle(n_tx, M, request):
+    """The few-transmit contraction (8 .. 64 transmits per CTA, four bins per
+    CTA with the phasor stepped bin to bin) on transmit subsets: two angle
+    tiles (5 x 150, 11 x 70), the 32- and 64-transmit tiles (24 x 20 and
+    40 x 10 on the 128-element, T = 2048 frame), against an FP64 einsum of
+    the same FP32 spectra."""
+    import torch
+    w = kksynth.workload_small() if n_tx <= 11 else request.getfixturevalue("large")
+    sub = np.arange(n_tx)
+    ops, (rx, pairs, grp, J) = kc.scheme_both("shifted", w.tx_angles[:n_tx], M, j=1, tx_subset=sub)
+    plan = kc.kk_plan_for(w, rx, pairs, grp, J)
+    assert plan.info.n_tx_used == n_tx and plan.info.n_rx_used == M
+    Xo = kk.analytic_spectrum(np.asarray(w.rf[:n_tx], dtype=np.float64))  # [n][L][F]
+    Xf = np.transpose(Xo, (2, 0, 1)).astype(np.complex64)             # [F][n][L]
+    X = torch.from_numpy(np.ascontiguousarray(np.stack([Xf.real, Xf.imag], -1))).cuda()
+    F = w.n_samples // 2
+    Y = torch.empty((F, n_tx, M, 2), device="cuda:0")
+    plan.shear(X, Y)
+    torch.cuda.synchronize()
+    d = kk.shear_delays(w.elem_x, ops.rx_angles, C)
+    k = np.arange(F)
+    W = np.exp(2j * np.pi * k[None, None, :] * (FS * d)[:, :, None] / w.n_samples)
+    ref = np.einsum("ilk,olk->kio", Xf.transpose(1, 2, 0).astype(np.complex128), W)
+    assert kc.rel_l2(kc.cplx(Y), ref) <= 2e-6
+
+
 def test_stage_inverse_matches_oracle():
     import torch
     w = kksynth.workload_small()
