@@ -254,9 +254,10 @@ cudaError_t launch_ri(const kk_plan &p, const float2 *X, float2 *Y, cudaStream_t
 // row-major grid use a plain gather through the slot table and one stage).
 // In the first contraction the lanes of a warp run along lf, so the
 // unpadded rows are read without bank conflicts and the weights Ws[ls][os]
-// are broadcasts; threads left over split the ls range.  Z goes to the
-// stage's X buffer once every thread has read its rows, and the second
-// contraction adds the parts.
+// are broadcasts; the threads left over take the slow-axis waves in parts of
+// OSN (zero weights pad the last part), each thread summing every row.  Z
+// goes to the stage's X buffer once every thread has read its rows, and the
+// second contraction sums it over lf.
 constexpr int kSepThreads = 256;
 
 struct SepArgs {
@@ -377,6 +378,9 @@ __global__ void __launch_bounds__(kSepThreads) k_shear_sep(const SepArgs a) {
       for (int j = 0; j < OSN; ++j)
         if (h * OSN + j < a.Ms) z[h * OSN + j] = acc[j];
     }
+    // the stage is refilled by bulk copies two items on: order these
+    // ordinary stores before the copies' asynchronous writes
+    if (BULK) tc::fence_async_smem();
     __syncthreads();
 
     // second contraction: thread (t, os, of) over lf, four interleaved
