@@ -45,7 +45,7 @@ def _args():
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-refiner measurement")
     ap.add_argument("--profile", default=None,
                     choices=["kk_image", "decompose", "decompose_bf16", "decompose_f8e4m3", "das", "vernier",
-                             "refiner_step"],
+                             "refiner_step", "volume_contraction", "few_tx_contraction"],
                     help="run three launches of one stage of the benchmark frame and exit "
                          "(a small, bounded target for ncu)")
     return ap.parse_args()
@@ -467,14 +467,8 @@ def _streaming(kb, w, plan, info, groups=(5, 15, 25, 75), frames=40, warm=3):
     return res
 
 
-def _volume(kb, flush, n_sm, peaks, peak_src, reps=10):
-    """Volumetric KK with a 32 x 32 matrix array (1024 elements, 0.3 mm pitch):
-    5 x 5 transmit tilts over +-10 deg, int16 records of 2048 samples (30 dB),
-    7 x 7 receive waves evenly over +-14 deg (1225 pairs), a 128 x 128 x 160
-    voxel grid at 0.15 mm from 5 mm depth.  FP32 decomposition (1024
-    elements: beyond the tensor-core forms), volumes/s and voxel-pairs/s of
-    the image formation against the same shared-memory gather roofline as
-    the 2D frame."""
+def _volume_plan(kb):
+    """The 32 x 32-array volume of the benchmark and its coherent KK plan."""
     import numpy as np
     import kksynth
     w = kksynth.volume_workload(seed=3500, lx=32, ly=32, pitch=0.3e-3, ntx=5, nty=5, theta_max_deg=10.0,
@@ -487,6 +481,18 @@ def _volume(kb, flush, n_sm, peaks, peak_src, reps=10):
     plan = kb.Plan(w.elem_x, w.tx_ax, w.grid, w.c, w.fs, w.n_samples, kb.KK_RF_I16, rx_angles=rxx, pairs=pairs,
                    compound=kb.KK_COMPOUND_COHERENT, elem_y=w.elem_y, tx_angles_y=w.tx_ay, rx_angles_y=rxy,
                    grid_y=w.grid_y)
+    return w, plan
+
+
+def _volume(kb, flush, n_sm, peaks, peak_src, reps=10):
+    """Volumetric KK with a 32 x 32 matrix array (1024 elements, 0.3 mm pitch):
+    5 x 5 transmit tilts over +-10 deg, int16 records of 2048 samples (30 dB),
+    7 x 7 receive waves evenly over +-14 deg (1225 pairs), a 128 x 128 x 160
+    voxel grid at 0.15 mm from 5 mm depth.  FP32 decomposition (1024
+    elements: beyond the tensor-core forms), volumes/s and voxel-pairs/s of
+    the image formation against the same shared-memory gather roofline as
+    the 2D frame."""
+    w, plan = _volume_plan(kb)
     info = plan.info
     import torch
     d_rf = torch.from_numpy(w.rf).cuda()
@@ -831,6 +837,31 @@ def run_profile(args):
             net.adam(1e-5)
         torch.cuda.synchronize()
         print(f"profile target {args.profile}: done (status {net.status()})")
+        return
+    if args.profile in ("volume_contraction", "few_tx_contraction"):
+        import numpy as np
+        import kksynth
+        if args.profile == "volume_contraction":
+            # the separable contraction of the 32 x 32-array volume (~0.6 GB)
+            w, plan = _volume_plan(kb)
+            X = torch.empty((w.n_samples // 2, plan.info.n_tx_used, plan.info.n_elem, 2), device="cuda")
+            plan.spectrum(torch.from_numpy(w.rf).cuda(), X)
+        else:
+            # the batched form's slowest frame shape: 256 elements, T = 4096,
+            # 5 transmits x 90 receive angles, FP32, seeded normal spectra
+            L, T, N = 256, 4096, 5
+            rx = np.deg2rad(np.linspace(-20.0, 20.0, 90))
+            pairs = np.array([(i, o) for i in range(N) for o in range(90)], np.int32)
+            d = 0.075e-3
+            plan = kb.Plan(kksynth.element_positions(L, 0.3e-3), kksynth.tx_angles_even(N, 16.0),
+                           (256, 256, -d * 127.5, d, 5e-3, d), kksynth.C_SOUND, kksynth.FS, T, kb.KK_RF_I16,
+                           rx_angles=rx, pairs=pairs)
+            X = torch.randn((T // 2, N, L, 2), device="cuda", generator=torch.Generator(device="cuda").manual_seed(1))
+        Y = torch.empty((plan.info.n_bins, plan.info.n_tx_used, plan.info.n_rx_used, 2), device="cuda")
+        for _ in range(3):
+            plan.shear(X, Y)
+        torch.cuda.synchronize()
+        print(f"profile target {args.profile}: done (status {plan.status()})")
         return
     w = _workload(0)
     d_rf = torch.from_numpy(w.rf).cuda()
