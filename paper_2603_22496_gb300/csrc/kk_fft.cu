@@ -578,7 +578,6 @@ __global__ void __launch_bounds__(NT, (F == 1024 || F == 2048) ? 2 : 1) k_invers
                                                     const float *__restrict__ row_w,
                                                     const int32_t *__restrict__ out_row, int *status) {
   constexpr int FS = fft_row(F);
-  constexpr int T = 2 * F;
   constexpr int BK = F < 256 ? F : 256;  // bins per box
   constexpr unsigned kTx = (unsigned)(C * F * sizeof(float2));
   extern __shared__ __align__(128) float2 sm[];
