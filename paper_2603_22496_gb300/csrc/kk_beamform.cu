@@ -143,17 +143,12 @@ __device__ __forceinline__ void gather_tile(const GatherArgs &a, int tile, int s
     }
   };
 
-  // image accumulators; with several groups also the running compound state
-  constexpr int CR = MULTI ? ROWS : 1;
-  float2 acc[ROWS], sumB[CR];
-  float Isum[CR];
+  // image accumulators (with several groups, each group's image is written
+  // out when the group ends; the compounded intensity reads them back at the
+  // end, so no running compound state is held through the pair loop)
+  float2 acc[ROWS];
 #pragma unroll
   for (int r = 0; r < ROWS; ++r) acc[r] = make_float2(0.f, 0.f);
-#pragma unroll
-  for (int r = 0; r < CR; ++r) {
-    sumB[r] = make_float2(0.f, 0.f);
-    Isum[r] = 0.f;
-  }
   int gw = 0;  // next group whose image is written
 
   float2 raw0[NPT], raw1[NPT];  // y[k], y[k+1] of this lane's staged entries
@@ -267,11 +262,7 @@ __device__ __forceinline__ void gather_tile(const GatherArgs &a, int tile, int s
       for (int r = 0; r < ROWS; ++r) {
         const int iz = izb + r;
         if (ix < nx && iz < nz) dst[(size_t)iz * nx + ix] = acc[r];
-        if constexpr (MULTI) {
-          sumB[r] = f2add(sumB[r], acc[r]);
-          Isum[r] = fmaf(acc[r].x, acc[r].x, fmaf(acc[r].y, acc[r].y, Isum[r]));
-          acc[r] = make_float2(0.f, 0.f);
-        }
+        if constexpr (MULTI) acc[r] = make_float2(0.f, 0.f);
       }
       ++gw;
     }
@@ -313,23 +304,27 @@ __device__ __forceinline__ void gather_tile(const GatherArgs &a, int tile, int s
     for (int r = 0; r < ROWS; ++r) {
       const int iz = izb + r;
       if (ix < nx && iz < nz) dst[(size_t)iz * nx + ix] = acc[r];
-      if constexpr (MULTI) {
-        sumB[r] = f2add(sumB[r], acc[r]);
-        Isum[r] = fmaf(acc[r].x, acc[r].x, fmaf(acc[r].y, acc[r].y, Isum[r]));
-        acc[r] = make_float2(0.f, 0.f);
-      }
+      if constexpr (MULTI) acc[r] = make_float2(0.f, 0.f);
     }
     ++gw;
   }
   if (split == 1 && I != nullptr && compound != KK_COMPOUND_NONE) {
+    const size_t plane = (size_t)nx * nz * (VOL ? va->ny : 1);
 #pragma unroll
     for (int r = 0; r < ROWS; ++r) {
       const int iz = izb + r;
       if (ix < nx && iz < nz) {
         float v;
         if constexpr (MULTI) {
-          v = (compound == KK_COMPOUND_COHERENT) ? fmaf(sumB[r].x, sumB[r].x, sumB[r].y * sumB[r].y)
-                                                 : Isum[r];
+          // this thread's own group images, in group order (split == 1: slice 0)
+          float2 sb = make_float2(0.f, 0.f);
+          float si = 0.f;
+          for (int g2 = 0; g2 < J; ++g2) {
+            const float2 b = out[(size_t)g2 * plane + (size_t)iz * nx + ix];
+            sb = f2add(sb, b);
+            si = fmaf(b.x, b.x, fmaf(b.y, b.y, si));
+          }
+          v = (compound == KK_COMPOUND_COHERENT) ? fmaf(sb.x, sb.x, sb.y * sb.y) : si;
         } else {
           v = fmaf(acc[r].x, acc[r].x, acc[r].y * acc[r].y);   // one group: |B|^2
         }
