@@ -45,7 +45,7 @@ def _args():
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-refiner measurement")
     ap.add_argument("--profile", default=None,
                     choices=["kk_image", "decompose", "decompose_bf16", "decompose_f8e4m3", "das", "vernier",
-                             "refiner_step", "volume_contraction", "few_tx_contraction"],
+                             "refiner_step", "volume_contraction", "few_tx_contraction", "batch_gather"],
                     help="run three launches of one stage of the benchmark frame and exit "
                          "(a small, bounded target for ncu)")
     return ap.parse_args()
@@ -837,6 +837,15 @@ def run_profile(args):
             net.adam(1e-5)
         torch.cuda.synchronize()
         print(f"profile target {args.profile}: done (status {net.status()})")
+        return
+    if args.profile == "batch_gather":
+        # the batched form on its first 16 uneven frames at the 4 x 8 shape: three graph runs
+        frames = _batch_frames(kb, 16)
+        batch = kb.Batch(frames, shape=408)
+        for _ in range(3):
+            batch.run()
+        torch.cuda.synchronize()
+        print(f"profile target {args.profile}: done ({batch.info.n_items} items)")
         return
     if args.profile in ("volume_contraction", "few_tx_contraction"):
         import numpy as np
