@@ -11,6 +11,13 @@
 // W is never stored: each CTA generates its tile on chip from the 0.64
 // fixed-point phases (k * phi mod 2^64 is exact integer arithmetic), so the
 // contraction reads only X from HBM and writes only Y.
+//
+// Three kernels, chosen by launch_shear_f32:
+//   k_shear_sep   volumetric plans whose elements form a grid and whose receive
+//                 waves form a product of x and y tilts (W factors per axis);
+//   k_shear_f32n  up to 64 transmits in use (tile sized to Nu x Mu, the
+//                 phasor stepped across four bins);
+//   k_shear_f32   everything else.
 #include "kk_internal.h"
 #include "kk_tc.h"
 #include "kk_tma.h"
