@@ -5,7 +5,8 @@ linear array, tilts without a y component and one y-slice at y = 0 must give
 the linear-array result.  V2 ties the y axis to the x axis: transposing the
 problem (array, tilts, phantom, grid) must transpose the volume.  V3 and V5
 are physics (focus at the scatterers; full-pair KK close to DAS), V4 brute
-force on a tiny case.
+force on a tiny case.  V6 pins the per-axis split of the shear on a grid
+array with a product receive set, which the separable GPU contraction uses.
 """
 import cmath
 import math
@@ -167,3 +168,35 @@ def test_v5_full_pairs_approximate_das():
     corr = float(np.sum(Bk * Bd) / np.sqrt(np.sum(Bk ** 2) * np.sum(Bd ** 2)))
     assert corr >= 0.9, corr
     assert np.unravel_index(np.argmax(Bk), Bk.shape) == np.unravel_index(np.argmax(Bd), Bd.shape)
+
+
+def test_v6_shear_separates_per_axis_on_a_grid():
+    """Reading R28 on the oracle's own definition: for elements on an x-y grid
+    and receive waves on a product of x and y tilts, delta_l(o) is the sum of
+    an x term (ox, lx) and a y term (oy, ly), so the per-bin phasor matrix is
+    the Kronecker product of two per-axis matrices and the element sum can
+    run as two per-axis contractions (the separable GPU form)."""
+    lx, ly = 6, 4
+    u, v = kksynth.matrix_elements(lx, ly, 0.3e-3, 0.25e-3)
+    ax1 = np.deg2rad([-11.0, -3.0, 0.0, 7.0, 12.0])
+    ay1 = np.deg2rad([-9.0, 0.0, 5.0])
+    rxx, rxy = np.tile(ax1, ay1.shape[0]), np.repeat(ay1, ax1.shape[0])   # o = oy * Mx + ox
+    d = V.shear_delays3(u, v, rxx, rxy, C)                                  # [M][L], l = ly * Lx + lx
+    sx, sy = np.sin(ax1), np.sin(ay1)
+    xr = np.where(sx > 0, u.max(), np.where(sx < 0, u.min(), 0.0))
+    yr = np.where(sy > 0, v.max(), np.where(sy < 0, v.min(), 0.0))
+    ux, vy = u[:lx], v[::lx]
+    dx = (xr[:, None] - ux[None, :]) * sx[:, None] / C                     # [Mx][Lx]
+    dy = (yr[:, None] - vy[None, :]) * sy[:, None] / C                     # [My][Ly]
+    sep = dy[:, None, :, None] + dx[None, :, None, :]                      # [My][Mx][Ly][Lx]
+    assert np.abs(sep.reshape(d.shape) - d).max() <= 1e-18
+    # the two-step contraction equals the full one on random spectra
+    rng = np.random.default_rng(6)
+    T, k = 256, 37
+    X = rng.standard_normal((3, ly * lx)) + 1j * rng.standard_normal((3, ly * lx))
+    W = np.exp(2j * np.pi * k * FS * d / T)
+    Wx = np.exp(2j * np.pi * k * FS * dx / T)
+    Wy = np.exp(2j * np.pi * k * FS * dy / T)
+    Z = np.einsum("iyx,ax->iya", X.reshape(3, ly, lx), Wx)                 # sum over lx
+    Y2 = np.einsum("iya,by->iba", Z, Wy).reshape(3, -1)                    # sum over ly
+    assert kk.rel_l2(Y2, X @ W.T) <= 1e-13
