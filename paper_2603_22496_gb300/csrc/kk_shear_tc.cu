@@ -28,7 +28,11 @@
 // FP8: the scale is per column (k, i) of X -- it factors out of the sum over
 // elements; X is rounded to e4m3 as X / s with s = max_l |X| / 448, W is
 // stored as 64 W (|W| <= 1, clear of e4m3 subnormals), and the FP32 result is
-// multiplied by s / 64 in the epilogue.
+// multiplied by s / 64 in the epilogue.  Each operand is held as two e4m3
+// terms, hi = e4m3(v) and lo = e4m3(v - hi), and the accumulator takes
+// A_hi B_hi + A_hi B_lo + A_lo B_hi: one e4m3 term per operand (three mantissa
+// bits) leaves the image about 2e-2 from the FP64 result, the two-term form
+// about 5e-4.
 //
 // Every wait is bounded (%globaltimer): on timeout the CTA records
 // KK_ERR_TIMEOUT in the plan's status word, frees its TMEM and returns.
@@ -63,6 +67,20 @@ __device__ __forceinline__ uint32_t pack_e4m3x2(float a, float b) {
   uint16_t r;
   asm("cvt.rn.satfinite.e4m3x2.f32 %0, %1, %2;" : "=h"(r) : "f"(b), "f"(a));
   return r;
+}
+
+// two e4m3 bytes (low byte first) -> two floats (exact: e4m3 is a subset of f16)
+__device__ __forceinline__ float2 e4m3x2_to_float2(uint32_t v) {
+  uint32_t h;
+  asm("cvt.rn.f16x2.e4m3x2 %0, %1;" : "=r"(h) : "h"((uint16_t)v));
+  return __half22float2(*reinterpret_cast<const __half2 *>(&h));
+}
+// two-term e4m3 split of two floats: a ~ hi + lo with lo = e4m3(a - hi); the
+// residual is exact in FP32 (hi lies within a factor two of a, or is zero)
+__device__ __forceinline__ void split_e4m3x2(float a, float b, uint32_t &hi, uint32_t &lo) {
+  hi = pack_e4m3x2(a, b);
+  const float2 h = e4m3x2_to_float2(hi);
+  lo = pack_e4m3x2(a - h.x, b - h.y);
 }
 
 template <int KIND>
@@ -299,9 +317,13 @@ __global__ void __launch_bounds__(kTcThreads, 2)
   constexpr uint32_t LBO = 128u;
   constexpr uint32_t SBO = (uint32_t)(kKC * ES / 16) * 128u;
   extern __shared__ __align__(1024) unsigned char smem[];
-  unsigned char *sA = smem;                                   // kRowsM x kKC elements
-  unsigned char *sB = smem + (size_t)kRowsM * kKC * ES;       // NP x kKC elements
-  float *sScale = reinterpret_cast<float *>(sB + (size_t)NP * kKC * ES);  // [NP] (FP8)
+  // FP8 holds each operand as two terms (hi, lo): A_hi, A_lo, B_hi, B_lo
+  constexpr int NT = (KIND == 2) ? 2 : 1;
+  unsigned char *sA = smem;                                   // NT x kRowsM x kKC elements
+  unsigned char *sB = smem + (size_t)NT * kRowsM * kKC * ES;  // NT x NP x kKC elements
+  [[maybe_unused]] unsigned char *sAl = sA + (size_t)kRowsM * kKC * ES;
+  [[maybe_unused]] unsigned char *sBl = sB + (size_t)NP * kKC * ES;
+  float *sScale = reinterpret_cast<float *>(sB + (size_t)NT * NP * kKC * ES);  // [NP] (FP8)
   __shared__ __align__(8) uint64_t mbar;
   __shared__ uint32_t tmem_slot;
   __shared__ int s_abort;
@@ -346,16 +368,21 @@ __global__ void __launch_bounds__(kTcThreads, 2)
         if (lane == 0) sScale[i] = s;
         // 16-byte core rows: 8 complex elements each
         for (int c = lane; c < kKC / 16; c += 32) {
-          uint32_t w[4];
+          uint32_t w[4], wl[4];
 #pragma unroll
           for (int q = 0; q < 4; ++q) {
             const int l0 = c * 8 + 2 * q;
             float2 a = make_float2(0.f, 0.f), b = make_float2(0.f, 0.f);
             if (i < Nu && l0 < L) a = __half22float2(Xk[(size_t)i * L + l0]);
             if (i < Nu && l0 + 1 < L) b = __half22float2(Xk[(size_t)i * L + l0 + 1]);
-            w[q] = pack_e4m3x2(a.x * inv, a.y * inv) | (pack_e4m3x2(b.x * inv, b.y * inv) << 16);
+            uint32_t ha, la, hb, lb;
+            split_e4m3x2(a.x * inv, a.y * inv, ha, la);
+            split_e4m3x2(b.x * inv, b.y * inv, hb, lb);
+            w[q] = ha | (hb << 16);
+            wl[q] = la | (lb << 16);
           }
           *reinterpret_cast<uint4 *>(sB + core_off<1>(i, c * 16)) = make_uint4(w[0], w[1], w[2], w[3]);
+          *reinterpret_cast<uint4 *>(sBl + core_off<1>(i, c * 16)) = make_uint4(wl[0], wl[1], wl[2], wl[3]);
         }
       }
     } else {
@@ -427,14 +454,23 @@ __global__ void __launch_bounds__(kTcThreads, 2)
         }
         uint4 re, im;
         if constexpr (KIND == 2) {
-          uint32_t r4[4], i4[4];
+          uint32_t r4[4], i4[4], rl4[4], il4[4];
 #pragma unroll
           for (int q = 0; q < 4; ++q) {
-            r4[q] = pack_e4m3x2(wr[2 * q], -wi[2 * q]) | (pack_e4m3x2(wr[2 * q + 1], -wi[2 * q + 1]) << 16);
-            i4[q] = pack_e4m3x2(wi[2 * q], wr[2 * q]) | (pack_e4m3x2(wi[2 * q + 1], wr[2 * q + 1]) << 16);
+            uint32_t h0, l0_, h1, l1, g0, m0_, g1, m1;
+            split_e4m3x2(wr[2 * q], -wi[2 * q], h0, l0_);
+            split_e4m3x2(wr[2 * q + 1], -wi[2 * q + 1], h1, l1);
+            split_e4m3x2(wi[2 * q], wr[2 * q], g0, m0_);
+            split_e4m3x2(wi[2 * q + 1], wr[2 * q + 1], g1, m1);
+            r4[q] = h0 | (h1 << 16);
+            rl4[q] = l0_ | (l1 << 16);
+            i4[q] = g0 | (g1 << 16);
+            il4[q] = m0_ | (m1 << 16);
           }
           re = make_uint4(r4[0], r4[1], r4[2], r4[3]);
           im = make_uint4(i4[0], i4[1], i4[2], i4[3]);
+          *reinterpret_cast<uint4 *>(sAl + core_off<ES>(2 * ol, c * 16)) = make_uint4(rl4[0], rl4[1], rl4[2], rl4[3]);
+          *reinterpret_cast<uint4 *>(sAl + core_off<ES>(2 * ol + 1, c * 16)) = make_uint4(il4[0], il4[1], il4[2], il4[3]);
         } else if constexpr (KIND == 0) {
           re = make_uint4(pack_bf16(wr[0], -wi[0]), pack_bf16(wr[1], -wi[1]), pack_bf16(wr[2], -wi[2]),
                           pack_bf16(wr[3], -wi[3]));
@@ -455,11 +491,18 @@ __global__ void __launch_bounds__(kTcThreads, 2)
         tc_fence_after();
         const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
         const int ksteps = (2 * L + FM::KSTEP - 1) / FM::KSTEP;
+        // FP8: A_hi B_hi + A_hi B_lo + A_lo B_hi into one accumulator (the
+        // lo x lo term is below the accumulation's own rounding)
 #pragma unroll 1
-        for (int s = 0; s < ksteps; ++s) {
-          const uint32_t koff = (uint32_t)s * (FM::KSTEP * ES / 16) * LBO;
-          mma<KIND>(tmem, smem_desc(a0 + koff, LBO, SBO), smem_desc(b0 + koff, LBO, SBO), idesc,
-                    s > 0 ? 1u : 0u);
+        for (int t = 0; t < (KIND == 2 ? 3 : 1); ++t) {
+          const uint32_t at = a0 + (t == 2 ? (uint32_t)(kRowsM * kKC * ES) : 0u);
+          const uint32_t bt = b0 + (t == 1 ? (uint32_t)(NP * kKC * ES) : 0u);
+#pragma unroll 1
+          for (int s = 0; s < ksteps; ++s) {
+            const uint32_t koff = (uint32_t)s * (FM::KSTEP * ES / 16) * LBO;
+            mma<KIND>(tmem, smem_desc(at + koff, LBO, SBO), smem_desc(bt + koff, LBO, SBO), idesc,
+                      (s > 0 || t > 0) ? 1u : 0u);
+          }
         }
         mma_commit(&mbar);
       }
@@ -513,7 +556,8 @@ __global__ void __launch_bounds__(kTcThreads, 2)
 
 size_t tc_shear_smem_bytes(int precision, int NP) {
   const int ES = (precision == KK_PREC_F8E4M3) ? 1 : 2;
-  return (size_t)kRowsM * kKC * ES + (size_t)NP * kKC * ES + sizeof(float) * NP;
+  const int NT = (precision == KK_PREC_F8E4M3) ? 2 : 1;   // FP8: hi and lo terms
+  return (size_t)NT * kRowsM * kKC * ES + (size_t)NT * NP * kKC * ES + sizeof(float) * NP;
 }
 
 // spectra [F * Nu][2 L] 16-bit elements, box {64, NP}, 128-byte swizzle
