@@ -49,7 +49,9 @@ typedef enum kk_status {
   KK_ERR_UNSUPPORTED = 2, /* valid but not implemented (e.g. an FFT length) */
   KK_ERR_CUDA = 3,        /* a CUDA runtime call or launch failed */
   KK_ERR_OOM = 4,         /* device allocation failed at plan time */
-  KK_ERR_TIMEOUT = 5      /* a bounded device-side wait gave up */
+  KK_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up */
+  KK_ERR_BOUNDS = 6       /* bounds-checked build only: a kernel index fell outside
+                             its buffer (the access was skipped) */
 } kk_status;
 
 typedef enum kk_rf_dtype { KK_RF_I16 = 0, KK_RF_F32 = 1 } kk_rf_dtype;
@@ -211,6 +213,17 @@ kk_status kk_plan_set_gather(kk_plan *p, int32_t rows, int32_t stage);
  */
 kk_status kk_plan_status(const kk_plan *p, int32_t *status);
 
+/*
+ * Check of the bounded device-side waits (no counterpart in the paper).
+ * Launches one CTA of 128 threads on `stream` that waits on an mbarrier no
+ * copy or thread ever signals, through the same bounded wait every pipelined
+ * kernel of the library uses, with a limit of limit_ns nanoseconds (clamped
+ * to [1000, 1e9]).  The wait runs out, the CTA records KK_ERR_TIMEOUT in the
+ * plan's status word (read it with kk_plan_status) and returns, as a kernel
+ * that lost a signal does; nothing is in flight, so the context stays usable.
+ */
+kk_status kk_plan_check_wait_timeout(const kk_plan *p, int64_t limit_ns, void *stream);
+
 /* Workspace bytes needed by kk_decompose / kk_beamform / das_beamform. */
 kk_status kk_plan_workspace_size(const kk_plan *p, size_t *bytes);
 
@@ -265,10 +278,12 @@ kk_status kk_beamform(const kk_plan *p, const void *d_rf_theta, void *d_B,
  * pair slices, which kk_beamform keeps in the caller's workspace, live in a
  * fixed 8 MiB device array compiled into the library; every GPU that loads
  * the library holds that array until the process exits.  A plan whose partial
- * images need more than 8 MiB (pair slices x groups x nx x nz x 8 bytes; 0
- * when the plan uses a single slice) is rejected with KK_ERR_INVALID_ARG.
- * The first call on a device looks up the array's device address (a set-up
- * step, no allocation): make that first call before any stream capture.
+ * images need more than 8 MiB (pair slices x groups x nx x nz x ny x 8 bytes,
+ * ny = 1 for 2D grids; 0 when the plan uses a single slice) is rejected with
+ * KK_ERR_INVALID_ARG.  Every call that needs the array looks up its device
+ * address on the plan's device (a set-up step, no allocation; done per call,
+ * so a re-created context is never handed a stale address): make the first
+ * such call on a device before any stream capture.
  * All calls share the one array, which keeps the last call's contents (every
  * call rewrites all it reads, so nothing needs clearing); calls that overlap
  * on the GPU -- different streams, or host threads without ordering -- race

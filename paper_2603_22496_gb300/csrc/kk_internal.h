@@ -164,6 +164,10 @@ struct DeviceGuard {
   ~DeviceGuard();
 };
 
+// Checks shared by the KK image-formation entry points: a KK plan, non-null
+// rf_theta and B, I present when the plan compounds, rf_theta 16-byte aligned.
+kk_status check_beamform_args(const kk_plan *p, const void *rf_theta, const void *B, const float *I);
+
 // spectrum -> contraction -> inverse of one frame on stream s (no checks)
 kk_status enqueue_decompose(const kk_plan *p, const void *rf, void *rf_theta, void *ws, cudaStream_t s);
 // KK image formation of one frame on stream s (no checks)

@@ -9,41 +9,30 @@
 // library, and kk_beamform_noalloc launches the same gather and reduction
 // kernels with it.  Nothing here calls cudaMalloc, cudaFree or any
 // allocating routine.
-#include <mutex>
-
 #include "kk_internal.h"
 
 namespace kk {
 namespace {
 
-// 8 MiB: one million complex partial pixels (pair slices x groups x pixels).
-// Every GPU that loads the library holds this array until the process exits.
+// 8 MiB: one million complex partial pixels (pair slices x groups x pixels
+// x y slices).  Every GPU that loads the library holds this array until the
+// process exits.
 constexpr size_t kNoAllocScratchBytes = size_t(8) << 20;
-constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) float2 g_noalloc_scratch[kNoAllocScratchBytes / sizeof(float2)];
 
-std::mutex g_mu;
-void *g_scratch_ptr[kMaxDevices] = {};
-
-// Device address of the scratch array on `device` (which is current).  Host
-// code cannot use the symbol itself: it names a host-side stand-in.
-kk_status scratch_address(int device, void **out) {
-  if (device < 0 || device >= kMaxDevices) {
-    set_error("device ordinal beyond the no-allocation scratch table");
-    return KK_ERR_INVALID_ARG;
+// Device address of the scratch array on the current device.  Host code
+// cannot use the symbol itself: it names a host-side stand-in.  Looked up on
+// every call (cheap once the module is loaded), so a context that was torn
+// down and re-created never receives a stale address.
+kk_status scratch_address(void **out) {
+  void *ptr = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+  if (e != cudaSuccess || ptr == nullptr) {
+    if (e == cudaSuccess) e = cudaErrorInvalidSymbol;
+    return cuda_fail(e, "cudaGetSymbolAddress(no-allocation scratch)");
   }
-  std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_scratch_ptr[device]) {
-    void *ptr = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
-    if (e != cudaSuccess || ptr == nullptr) {
-      if (e == cudaSuccess) e = cudaErrorInvalidSymbol;
-      return cuda_fail(e, "cudaGetSymbolAddress(no-allocation scratch)");
-    }
-    g_scratch_ptr[device] = ptr;
-  }
-  *out = g_scratch_ptr[device];
+  *out = ptr;
   return KK_OK;
 }
 
@@ -54,11 +43,8 @@ using namespace kk;
 
 extern "C" kk_status kk_beamform_noalloc(const kk_plan *p, const void *d_rf_theta, void *d_B,
                                          float *d_I, void *stream) {
-  if (!p) { set_error("null plan"); return KK_ERR_INVALID_ARG; }
-  if (p->is_das) { set_error("expected a KK plan"); return KK_ERR_INVALID_ARG; }
-  if (!d_rf_theta || !d_B) { set_error("null buffer"); return KK_ERR_INVALID_ARG; }
-  if (p->compound != KK_COMPOUND_NONE && !d_I) { set_error("compound mode set but I is null"); return KK_ERR_INVALID_ARG; }
-  if ((uintptr_t)d_rf_theta % 16) { set_error("rf_theta must be 16-byte aligned"); return KK_ERR_INVALID_ARG; }
+  kk_status st = check_beamform_args(p, d_rf_theta, d_B, d_I);
+  if (st != KK_OK) return st;
   const size_t need = (p->bf_split > 1)
                           ? sizeof(float2) * (size_t)p->bf_split * p->J * p->grid.nx * p->grid.nz * p->ny
                           : 0;
@@ -67,21 +53,14 @@ extern "C" kk_status kk_beamform_noalloc(const kk_plan *p, const void *d_rf_thet
               "scratch holds " + std::to_string(kNoAllocScratchBytes) + " (use kk_beamform with a workspace)");
     return KK_ERR_INVALID_ARG;
   }
-  int old = -1;
-  if (cudaGetDevice(&old) != cudaSuccess) old = -1;
-  if (old != p->device && cudaSetDevice(p->device) != cudaSuccess) {
-    set_error("cudaSetDevice failed");
-    return KK_ERR_CUDA;
-  }
-  kk_status st = KK_OK;
+  DeviceGuard guard(p->device);
+  if (!guard.ok) { set_error("cudaSetDevice failed"); return KK_ERR_CUDA; }
   void *scratch = nullptr;
-  if (need > 0) st = scratch_address(p->device, &scratch);
-  if (st == KK_OK) {
-    // every slice writes each of its partial pixels, so nothing needs clearing
-    cudaError_t e = launch_kk_gather(*p, (const float2 *)d_rf_theta, (float2 *)d_B, d_I,
-                                     (float2 *)scratch, (cudaStream_t)stream);
-    if (e != cudaSuccess) st = cuda_fail(e, "kk gather launch (no-allocation)");
-  }
-  if (old >= 0 && old != p->device) cudaSetDevice(old);
-  return st;
+  if (need > 0) st = scratch_address(&scratch);
+  if (st != KK_OK) return st;
+  // every slice writes each of its partial pixels, so nothing needs clearing
+  cudaError_t e = launch_kk_gather(*p, (const float2 *)d_rf_theta, (float2 *)d_B, d_I,
+                                   (float2 *)scratch, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "kk gather launch (no-allocation)");
+  return KK_OK;
 }

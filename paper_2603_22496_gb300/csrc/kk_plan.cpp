@@ -173,7 +173,7 @@ bool separable_tables(const kk_plan_desc *d, int T, const std::vector<double> &u
       st.phx[(size_t)o * st.Lx + l] = frac64(d->fs * (xr - ux[l]) * sx / d->c / (double)T);
   }
   for (int o = 0; o < st.My; ++o) {
-    const double sy = std::sin(ay[o]), yr = shear_reference(v, sy);
+    const double sy = std::sin(ay[o]), yr = shear_reference(v, ay[o]);
     for (int l = 0; l < st.Ly; ++l)
       st.phy[(size_t)o * st.Ly + l] = frac64(d->fs * (yr - vy[l]) * sy / d->c / (double)T);
   }
@@ -762,6 +762,15 @@ cudaError_t launch_shear(const kk_plan &p, const void *X, float2 *Y, cudaStream_
                                       : launch_shear_tc(p, X, Y, s);
 }
 
+kk_status check_beamform_args(const kk_plan *p, const void *rf_theta, const void *B, const float *I) {
+  kk_status st = check_plan(p, false);
+  if (st != KK_OK) return st;
+  if (!rf_theta || !B) { set_error("null buffer"); return KK_ERR_INVALID_ARG; }
+  if (p->compound != KK_COMPOUND_NONE && !I) { set_error("compound mode set but I is null"); return KK_ERR_INVALID_ARG; }
+  if (!aligned(rf_theta, 16)) { set_error("rf_theta must be 16-byte aligned"); return KK_ERR_INVALID_ARG; }
+  return KK_OK;
+}
+
 kk_status enqueue_beamform(const kk_plan *p, const void *rf_theta, void *B, float *I, void *ws, cudaStream_t s) {
   float2 *part = (p->bf_split > 1) ? at<float2>(ws, p->ws_part) : nullptr;
   cudaError_t e = launch_kk_gather(*p, (const float2 *)rf_theta, (float2 *)B, I, part, s);
@@ -911,12 +920,10 @@ kk_status kk_inverse(const kk_plan *p, const void *d_Y, void *d_rf_theta, void *
 }
 
 kk_status kk_beamform(const kk_plan *p, const void *d_rf_theta, void *d_B, float *d_I, void *d_ws, void *stream) {
-  kk_status st = check_plan(p, false);
+  kk_status st = check_beamform_args(p, d_rf_theta, d_B, d_I);
   if (st != KK_OK) return st;
-  if (!d_rf_theta || !d_B) { set_error("null buffer"); return KK_ERR_INVALID_ARG; }
-  if (p->compound != KK_COMPOUND_NONE && !d_I) { set_error("compound mode set but I is null"); return KK_ERR_INVALID_ARG; }
   if (p->bf_split > 1 && !d_ws) { set_error("workspace required"); return KK_ERR_INVALID_ARG; }
-  if (!aligned(d_rf_theta, 16) || (d_ws && !aligned(d_ws, kAlign))) { set_error("rf_theta must be 16-byte aligned (workspace 256)"); return KK_ERR_INVALID_ARG; }
+  if (d_ws && !aligned(d_ws, kAlign)) { set_error("workspace must be 256-byte aligned"); return KK_ERR_INVALID_ARG; }
   DeviceGuard guard(p->device);
   return enqueue_beamform(p, d_rf_theta, d_B, d_I, d_ws, (cudaStream_t)stream);
 }

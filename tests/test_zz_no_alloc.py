@@ -121,3 +121,55 @@ def test_noalloc_rejects_plans_beyond_its_scratch():
         kb.kk_beamform_noalloc(plan.handle, rt, B, I)
     assert e.value.status == kb.KK_ERR_INVALID_ARG
     assert "scratch" in str(e.value)
+
+
+def test_noalloc_volumetric_plan_with_pair_slices():
+    """A 4-slice volume on a 32 x 32 x-z grid: few tiles, so the pair list is
+    split and the scratch holds pair slices x groups x nx x nz x ny partial
+    voxels (the y-slice factor of the size rule)."""
+    import torch
+    from oracle import schemes, volume as V
+    w = kksynth.volume_workload(nx=32, ny=4, nz=32, speckle=200)
+    rx1 = schemes.even_receive_set(np.deg2rad(12.0), 7)
+    ps = V.product_set(w.tx_ax, w.tx_ay, [(np.tile(rx1, 7), np.repeat(rx1, 7))])
+    pairs = np.stack([ps.tx_index, ps.rx_index], 1).astype(np.int32)
+    plan = kb.Plan(w.elem_x, w.tx_ax, w.grid, w.c, w.fs, w.n_samples, kb.KK_RF_F32, rx_angles=ps.rx_ax,
+                   pairs=pairs, group_of_pair=ps.group.astype(np.int32), n_groups=ps.n_groups,
+                   compound=kb.KK_COMPOUND_COHERENT, elem_y=w.elem_y, tx_angles_y=w.tx_ay,
+                   rx_angles_y=ps.rx_ay, grid_y=w.grid_y)
+    assert plan.info.is_volume == 1 and plan.info.ny == 4
+    assert plan.info.launches_beamform == 2          # pair slices: the scratch is used
+    d_rf = torch.from_numpy(w.rf).cuda()
+    ws, rt = plan.empty_workspace(), plan.empty_rf_theta()
+    plan.decompose(d_rf, rt, ws)
+    B_ref, I_ref = plan.empty_image(), plan.empty_intensity()
+    kb.kk_beamform(plan.handle, rt, B_ref, I_ref, ws)
+    for _ in range(2):
+        B, I = plan.empty_image().fill_(float("nan")), plan.empty_intensity().fill_(float("nan"))
+        kb.kk_beamform_noalloc(plan.handle, rt, B, I)
+        torch.cuda.synchronize()
+        assert _rel(B, B_ref) <= TOL and _rel(I, I_ref) <= TOL
+
+
+def test_noalloc_single_slice_without_intensity():
+    """Three transmits x 7 receive angles: too few pairs to split, so the
+    scratch is never looked up; no compounding and no intensity buffer."""
+    import torch
+    w = kksynth.workload_small()
+    sub = [3, 5, 7]
+    dth = float(w.tx_angles[5] - w.tx_angles[3]) / 2
+    rx = kb.kk_scheme_angles(kb.KK_SCHEME_VERNIER, 3, dth, 7)
+    pairs = np.array([(i, o) for i in sub for o in range(7)], np.int32)
+    plan = kb.Plan(w.elem_x, w.tx_angles, w.grid, w.c, w.fs, w.n_samples, kb.KK_RF_F32, rx_angles=rx,
+                   pairs=pairs, compound=kb.KK_COMPOUND_NONE)
+    assert plan.info.launches_beamform == 1
+    d_rf = torch.from_numpy(w.rf).cuda()
+    ws, rt = plan.empty_workspace(), plan.empty_rf_theta()
+    plan.decompose(d_rf, rt, ws)
+    B_ref = plan.empty_image()
+    kb.kk_beamform(plan.handle, rt, B_ref, None, ws)
+    for _ in range(2):
+        B = plan.empty_image().fill_(float("nan"))
+        kb.kk_beamform_noalloc(plan.handle, rt, B, None)
+        torch.cuda.synchronize()
+        assert _rel(B, B_ref) <= TOL
