@@ -19,7 +19,7 @@ import numpy as np
 
 from . import build as _build
 
-KK_OK, KK_ERR_INVALID_ARG, KK_ERR_UNSUPPORTED, KK_ERR_CUDA, KK_ERR_OOM, KK_ERR_TIMEOUT = range(6)
+KK_OK, KK_ERR_INVALID_ARG, KK_ERR_UNSUPPORTED, KK_ERR_CUDA, KK_ERR_OOM, KK_ERR_TIMEOUT, KK_ERR_BOUNDS = range(7)
 KK_RF_I16, KK_RF_F32 = 0, 1
 KK_PREC_F32, KK_PREC_BF16, KK_PREC_F16, KK_PREC_F8E4M3 = 0, 1, 2, 3
 KK_COMPOUND_NONE, KK_COMPOUND_COHERENT, KK_COMPOUND_INCOHERENT = 0, 1, 2
@@ -29,11 +29,11 @@ KK_REGION_DISK, KK_REGION_ANNULUS, KK_REGION_RECT = 0, 1, 2
 KK_IMAGE_COMPLEX, KK_IMAGE_INTENSITY = 0, 1
 
 _STATUS = {0: "KK_OK", 1: "KK_ERR_INVALID_ARG", 2: "KK_ERR_UNSUPPORTED", 3: "KK_ERR_CUDA",
-           4: "KK_ERR_OOM", 5: "KK_ERR_TIMEOUT"}
+           4: "KK_ERR_OOM", 5: "KK_ERR_TIMEOUT", 6: "KK_ERR_BOUNDS"}
 
 # every symbol declared in include/kkbeam.h
 EXPORTS = ["kk_plan_create", "das_plan_create", "kk_plan_destroy", "kk_plan_get_info",
-           "kk_plan_set_gather", "kk_plan_status", "kk_plan_workspace_size", "kk_decompose", "kk_spectrum", "kk_shear", "kk_inverse",
+           "kk_plan_set_gather", "kk_plan_status", "kk_plan_check_wait_timeout", "kk_plan_workspace_size", "kk_decompose", "kk_spectrum", "kk_shear", "kk_inverse",
            "kk_beamform", "kk_beamform_noalloc", "das_beamform", "kk_run_host_scratch_size", "kk_run_host",
            "kk_scheme_angles", "kk_last_error", "kk_version",
            "kk_batch_create", "kk_batch_run", "kk_batch_get_info", "kk_batch_destroy",
@@ -170,6 +170,7 @@ def load(build_if_missing: bool = False):
         "kk_plan_workspace_size": ([vp, ctypes.POINTER(ctypes.c_size_t)], st),
         "kk_plan_set_gather": ([vp, ctypes.c_int32, ctypes.c_int32], st),
         "kk_plan_status": ([vp, ctypes.POINTER(ctypes.c_int32)], st),
+        "kk_plan_check_wait_timeout": ([vp, ctypes.c_int64, vp], st),
         "kk_decompose": ([vp, vp, vp, vp, vp], st),
         "kk_spectrum": ([vp, vp, vp, vp], st),
         "kk_shear": ([vp, vp, vp, vp], st),
@@ -363,6 +364,12 @@ def kk_plan_status(h) -> int:
     v = ctypes.c_int32()
     _check(load().kk_plan_status(h, ctypes.byref(v)))
     return int(v.value)
+
+
+def kk_plan_check_wait_timeout(h, limit_ns: int, stream=None):
+    """Run the bounded device wait on an mbarrier nothing signals (limit in
+    ns): the plan's status word then reads KK_ERR_TIMEOUT."""
+    _check(load().kk_plan_check_wait_timeout(h, int(limit_ns), _stream(stream)))
 
 
 def kk_decompose(h, rf, rf_theta, workspace, stream=None):
