@@ -85,6 +85,16 @@ def full_pairs(geo: Geometry):
 
 def phantom(seed: int, geo: Geometry):
     """Scatterers [n][4] (x, z, amplitude, 0) and the SNR in dB of one seed."""
+    sc, snr_db, _ = _phantom(seed, geo)
+    return sc, snr_db
+
+
+def wires(seed: int, geo: Geometry) -> np.ndarray:
+    """(x, z) of the point wires of one seed's phantom, [nw][2] metres."""
+    return _phantom(seed, geo)[2]
+
+
+def _phantom(seed: int, geo: Geometry):
     rng = np.random.default_rng(seed)
     nx, nz, x0, dx, z0, dz = geo.grid
     m = 1e-3
@@ -105,7 +115,7 @@ def phantom(seed: int, geo: Geometry):
     z = np.concatenate([sz[keep], wz])
     a = np.concatenate([amp[keep], wa])
     snr_db = float(rng.uniform(20.0, 40.0))
-    return np.stack([x, z, a, np.zeros_like(x)], 1), snr_db
+    return np.stack([x, z, a, np.zeros_like(x)], 1), snr_db, np.stack([wx, wz], 1)
 
 
 class Synth:

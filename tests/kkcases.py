@@ -105,3 +105,22 @@ def run_das(w, grid=None, want_I=False):
 def rel_l2(a, b):
     nb = float(np.linalg.norm(np.ravel(b)))
     return float(np.linalg.norm(np.ravel(a) - np.ravel(b))) / (nb if nb > 0 else 1.0)
+
+
+def nn_oracle_operands(theta, img, s_in, C):
+    """What the refiner's GPU kernels compute with, for the FP64 network
+    oracle: BF16-rounded weights, FP32 biases, the BF16-rounded scaled input
+    (complex [n][H][W] times s_in[n])."""
+    import torch
+    from oracle import nn
+    th = np.asarray(theta).astype(np.float64).copy()
+    off = 0
+    for ci, co, _ in nn.layer_shapes(C):
+        nw = co * 9 * ci
+        th[off:off + nw] = torch.from_numpy(np.asarray(theta[off:off + nw], np.float32)).to(
+            torch.bfloat16).double().numpy()
+        off += nw + co
+    xs = (img * np.asarray(s_in, np.float64)[:, None, None]).astype(np.complex64)
+    re = torch.from_numpy(xs.real.copy()).to(torch.bfloat16).double().numpy()
+    im = torch.from_numpy(xs.imag.copy()).to(torch.bfloat16).double().numpy()
+    return th, re + 1j * im

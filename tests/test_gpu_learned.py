@@ -71,3 +71,85 @@ def test_fallback_returns_the_plain_full_pair_image(trained):
         # the fallback is the full-pair image of that record set, unit rms
         assert torch.allclose(out[n] / out[n].pow(2).sum(-1).mean().sqrt(),
                               Ye[n] / Ye[n].pow(2).sum(-1).mean().sqrt(), rtol=1e-4, atol=1e-4)
+
+
+def _wire_windows(seed, geo, half=3, margin=4):
+    """Pixel windows (ix0, ix1, iz0, iz1) of +-half pixels about each wire of
+    a seed's phantom that lies at least `margin` pixels inside the grid."""
+    from paper_2603_22496_gb300 import learned as L
+    nx, nz, x0, dx, z0, dz = geo.grid
+    out = []
+    for x, z in L.wires(seed, geo):
+        ix, iz = int(round((x - x0) / dx)), int(round((z - z0) / dz))
+        if margin <= ix < nx - margin and margin <= iz < nz - margin:
+            out.append((ix - half, ix + half + 1, iz - half, iz + half + 1))
+    return out
+
+
+def _peak(a, win):
+    ix0, ix1, iz0, iz1 = win
+    sub = a[iz0:iz1, ix0:ix1]
+    k = int(np.argmax(sub))
+    return iz0 + k // sub.shape[1], ix0 + k % sub.shape[1]
+
+
+def test_learned_form_matches_the_oracle_network(trained):
+    """Parity of the learned form: the trained network run by the library's
+    kernels against the FP64 oracle network (oracle.nn) with the same
+    weights on the same held-out inputs (BF16-rounded, as the kernels see
+    them): rel-L2 <= 1e-2 and every wire's peak at the oracle's pixel."""
+    import torch
+    from oracle import nn
+    from tests import kkcases as kc
+    syn, ref, X, Y, Xe, Ye, _ = trained
+    C = 32
+    theta = ref.net.get_params().cpu().numpy()
+    xb = Xe[:2].contiguous()
+    s = kb.kk_net_image_scale(xb)
+    out = ref.net.forward(xb, s)
+    torch.cuda.synchronize()
+    th, xin = kc.nn_oracle_operands(theta, kc.cplx(xb), s.cpu().numpy(), C)
+    ro, _ = nn.forward(th, C, xin, None)
+    got = kc.cplx(out)
+    assert kc.rel_l2(got, ro) <= 1e-2
+    n_checked = 0
+    for n in range(2):
+        for win in _wire_windows(900_000 + n, syn.geo):
+            assert _peak(np.abs(got[n]), win) == _peak(np.abs(ro[n]), win)
+            n_checked += 1
+    assert n_checked >= 1
+
+
+def test_refined_wire_peaks_at_the_full_pair_image_pixels(trained):
+    """The refined image of each held-out seed puts every wire's peak at the
+    pixel where the plain full-pair KK image puts it; that full-pair image is
+    itself checked against the FP64 oracle (decomposition and Eq. (KK)) on
+    the wire windows and 2000 sampled pixels, at the BF16 form's bound."""
+    import torch
+    from oracle import kk, schemes
+    from paper_2603_22496_gb300 import learned as L
+    from tests import kkcases as kc
+    syn, ref, X, Y, Xe, Ye, _ = trained
+    geo = syn.geo
+    out, _ = ref.forward(Xe[:4])
+    torch.cuda.synchronize()
+    got, full = kc.cplx(out), kc.cplx(Ye[:4])
+    n_checked = 0
+    for n in range(4):
+        for win in _wire_windows(900_000 + n, geo):
+            assert _peak(np.abs(got[n]), win) == _peak(np.abs(full[n]), win), (n, win)
+            n_checked += 1
+    assert n_checked >= 4
+    # the full-pair target against the FP64 oracle, first held-out seed
+    rf = syn.simulate(900_000).cpu().numpy().astype(np.float64)
+    rxa = np.deg2rad(np.linspace(-geo.theta_max_deg, geo.theta_max_deg, geo.full_rx))
+    ops = schemes.full_product(geo.tx_angles(), np.arange(geo.n_tx), [rxa])
+    y = kk.decompose(rf, geo.elem_x(), ops, L.FS, L.C_SOUND)
+    rng = np.random.default_rng(5)
+    pix = [np.stack([rng.integers(0, geo.nx, 2000), rng.integers(0, geo.nz, 2000)], 1)]
+    for ix0, ix1, iz0, iz1 in _wire_windows(900_000, geo):
+        gx, gz = np.meshgrid(np.arange(ix0, ix1), np.arange(iz0, iz1))
+        pix.append(np.stack([gx.ravel(), gz.ravel()], 1))
+    pix = np.concatenate(pix)
+    orc = kk.kk_beamform(y, geo.elem_x(), ops, geo.grid, L.FS, L.C_SOUND, pixels=pix)[0]
+    assert kc.rel_l2(full[0][pix[:, 1], pix[:, 0]], orc) <= 1e-2
