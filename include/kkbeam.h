@@ -166,6 +166,10 @@ typedef struct kk_plan_info {
    * run the element sum as two per-axis contractions (the shear delay splits
    * per axis); these are Lx, Ly, Mx, My then, all 0 for the full form */
   int32_t sep_lx, sep_ly, sep_mx, sep_my;
+  /* image-formation launch shape: pixels per thread along z (tile = 32 x 4
+   * gather_rows), pairs (transmits, DAS) per stage, and the number of pair
+   * (element, DAS) slices whose partial images are summed after the gather */
+  int32_t gather_rows, gather_stage, gather_split;
 } kk_plan_info;
 
 /*
@@ -223,6 +227,17 @@ kk_status kk_plan_status(const kk_plan *p, int32_t *status);
  * that lost a signal does; nothing is in flight, so the context stays usable.
  */
 kk_status kk_plan_check_wait_timeout(const kk_plan *p, int64_t limit_ns, void *stream);
+
+/*
+ * Bounds-checked build (no counterpart in the paper).  The library compiled
+ * with KK_DEBUG_BOUNDS checks every staged-window index of the KK and DAS
+ * gathers against its pair's (channel's) window before the shared-memory
+ * read; a failed check skips the read and is counted on the device.
+ * kk_debug_bounds synchronises the device, returns the number of failed
+ * checks since the previous call in *violations and resets it.  The
+ * product build has no checks and returns KK_ERR_UNSUPPORTED.
+ */
+kk_status kk_debug_bounds(int64_t *violations);
 
 /* Workspace bytes needed by kk_decompose / kk_beamform / das_beamform. */
 kk_status kk_plan_workspace_size(const kk_plan *p, size_t *bytes);

@@ -33,7 +33,8 @@ _STATUS = {0: "KK_OK", 1: "KK_ERR_INVALID_ARG", 2: "KK_ERR_UNSUPPORTED", 3: "KK_
 
 # every symbol declared in include/kkbeam.h
 EXPORTS = ["kk_plan_create", "das_plan_create", "kk_plan_destroy", "kk_plan_get_info",
-           "kk_plan_set_gather", "kk_plan_status", "kk_plan_check_wait_timeout", "kk_plan_workspace_size", "kk_decompose", "kk_spectrum", "kk_shear", "kk_inverse",
+           "kk_plan_set_gather", "kk_plan_status", "kk_plan_check_wait_timeout", "kk_debug_bounds",
+           "kk_plan_workspace_size", "kk_decompose", "kk_spectrum", "kk_shear", "kk_inverse",
            "kk_beamform", "kk_beamform_noalloc", "das_beamform", "kk_run_host_scratch_size", "kk_run_host",
            "kk_scheme_angles", "kk_last_error", "kk_version",
            "kk_batch_create", "kk_batch_run", "kk_batch_get_info", "kk_batch_destroy",
@@ -92,7 +93,8 @@ class kk_plan_info(ctypes.Structure):
                 ("launches_decompose", ctypes.c_int32), ("launches_beamform", ctypes.c_int32),
                 ("ny", ctypes.c_int32), ("is_volume", ctypes.c_int32),
                 ("sep_lx", ctypes.c_int32), ("sep_ly", ctypes.c_int32), ("sep_mx", ctypes.c_int32),
-                ("sep_my", ctypes.c_int32)]
+                ("sep_my", ctypes.c_int32), ("gather_rows", ctypes.c_int32), ("gather_stage", ctypes.c_int32),
+                ("gather_split", ctypes.c_int32)]
 
 
 class kk_batch_frame(ctypes.Structure):
@@ -153,12 +155,17 @@ def load(build_if_missing: bool = False):
     global _lib
     if _lib is not None:
         return _lib
-    path = _build.LIB
+    # KKBEAM_VARIANT=bounds selects the bounds-checked build of the same
+    # library (every gather index checked on the device; see kk_debug_bounds)
+    variant = os.environ.get("KKBEAM_VARIANT", "")
+    if variant not in _build.VARIANTS:
+        raise RuntimeError(f"unknown KKBEAM_VARIANT {variant!r}")
+    path = _build.VARIANTS[variant][1]
     if not os.path.exists(path):
         if not build_if_missing:
             raise RuntimeError(f"KK CUDA library not built ({path}); run "
                                "`python -m paper_2603_22496_gb300.build` or __graft_entry__.build()")
-        _build.build()
+        _build.build(variant=variant)
     lib = ctypes.CDLL(path)
     vp, st = ctypes.c_void_p, ctypes.c_int
     pp = ctypes.POINTER(ctypes.c_void_p)
@@ -171,6 +178,7 @@ def load(build_if_missing: bool = False):
         "kk_plan_set_gather": ([vp, ctypes.c_int32, ctypes.c_int32], st),
         "kk_plan_status": ([vp, ctypes.POINTER(ctypes.c_int32)], st),
         "kk_plan_check_wait_timeout": ([vp, ctypes.c_int64, vp], st),
+        "kk_debug_bounds": ([ctypes.POINTER(ctypes.c_int64)], st),
         "kk_decompose": ([vp, vp, vp, vp, vp], st),
         "kk_spectrum": ([vp, vp, vp, vp], st),
         "kk_shear": ([vp, vp, vp, vp], st),
@@ -359,6 +367,7 @@ def kk_plan_set_gather(h, rows: int, stage: int):
     _check(load().kk_plan_set_gather(h, int(rows), int(stage)))
 
 
+
 def kk_plan_status(h) -> int:
     """Device status word (KK_OK or KK_ERR_TIMEOUT); synchronises and resets it."""
     v = ctypes.c_int32()
@@ -370,6 +379,14 @@ def kk_plan_check_wait_timeout(h, limit_ns: int, stream=None):
     """Run the bounded device wait on an mbarrier nothing signals (limit in
     ns): the plan's status word then reads KK_ERR_TIMEOUT."""
     _check(load().kk_plan_check_wait_timeout(h, int(limit_ns), _stream(stream)))
+
+
+def kk_debug_bounds() -> int:
+    """Failed gather-index checks since the last call (bounds-checked build;
+    raises KKError(KK_ERR_UNSUPPORTED) in the product build)."""
+    v = ctypes.c_int64()
+    _check(load().kk_debug_bounds(ctypes.byref(v)))
+    return int(v.value)
 
 
 def kk_decompose(h, rf, rf_theta, workspace, stream=None):

@@ -15,6 +15,10 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libkkbeam.so")
+# bounds-checked variant (-DKK_DEBUG_BOUNDS): every gather index is checked and
+# failures are counted on the device (kk_debug_bounds); built on demand
+LIB_BOUNDS = os.path.join(BUILD, "libkkbeam_bounds.so")
+VARIANTS = {"": (BUILD, LIB, []), "bounds": (os.path.join(BUILD, "bounds"), LIB_BOUNDS, ["-DKK_DEBUG_BOUNDS"])}
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -40,8 +44,8 @@ def _deps_mtime():
     return max(os.path.getmtime(f) for f in files)
 
 
-def _compile(src: str, extra) -> str:
-    obj = os.path.join(BUILD, os.path.basename(src) + ".o")
+def _compile(src: str, extra, outdir: str = BUILD) -> str:
+    obj = os.path.join(outdir, os.path.basename(src) + ".o")
     if os.path.exists(obj) and os.path.getmtime(obj) >= _deps_mtime():
         return obj
     cmd = [nvcc()] + ARCH + NVCC_FLAGS + list(extra) + ["-c", src, "-o", obj + ".tmp"]
@@ -52,26 +56,31 @@ def _compile(src: str, extra) -> str:
     return obj
 
 
-def build(force: bool = False, verbose_ptxas: bool = False, jobs: int | None = None) -> str:
-    os.makedirs(BUILD, exist_ok=True)
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= _deps_mtime():
-        return LIB
+def build(force: bool = False, verbose_ptxas: bool = False, jobs: int | None = None,
+          variant: str = "") -> str:
+    """Compile the library ('' = the product library; 'bounds' = the
+    bounds-checked variant) and return its path."""
+    outdir, lib, vflags = VARIANTS[variant]
+    os.makedirs(outdir, exist_ok=True)
+    if not force and os.path.exists(lib) and os.path.getmtime(lib) >= _deps_mtime():
+        return lib
     if force:
-        for f in os.listdir(BUILD):
+        for f in os.listdir(outdir):
             if f.endswith(".o"):
-                os.remove(os.path.join(BUILD, f))
-    extra = ["-Xptxas", "-v"] if verbose_ptxas else []
+                os.remove(os.path.join(outdir, f))
+    extra = (["-Xptxas", "-v"] if verbose_ptxas else []) + vflags
     srcs = sources()
     with cf.ThreadPoolExecutor(max_workers=jobs or min(len(srcs), os.cpu_count() or 4)) as ex:
-        objs = list(ex.map(lambda s: _compile(s, extra), srcs))
-    tmp = LIB + f".tmp{os.getpid()}"
+        objs = list(ex.map(lambda s: _compile(s, extra, outdir), srcs))
+    tmp = lib + f".tmp{os.getpid()}"
     cmd = [nvcc()] + ARCH + ["-shared", "-o", tmp] + objs
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose_ptxas="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose_ptxas="-v" in sys.argv,
+                variant="bounds" if "--bounds" in sys.argv else ""))

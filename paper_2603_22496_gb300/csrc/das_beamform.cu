@@ -32,6 +32,11 @@ namespace {
 
 constexpr int kMaxStage = 32;
 
+#ifdef KK_DEBUG_BOUNDS
+// failed staged-window index checks of this file's gathers
+static __device__ unsigned g_bounds_das = 0;
+#endif
+
 struct __align__(8) WarpChan {
   unsigned off;
   float phi;
@@ -187,7 +192,9 @@ __global__ void __launch_bounds__(kGatherThreads)
           const float t = __fadd_rd(s, kFloorMagic);
           const float f = s - (t - kFloorMagic);
           const unsigned addr = wc.off + kout16[r] + ((unsigned)__float_as_int(t) << 4);
-          const float4 e = *reinterpret_cast<const float4 *>(swb + addr);
+          float4 e = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (KK_IN_BOUNDS(g_bounds_das, (unsigned)((int)(addr >> 4) - j * win) < (unsigned)win))
+            e = *reinterpret_cast<const float4 *>(swb + addr);
           sacc[r].x += fmaf(f, e.z, e.x);
           sacc[r].y += fmaf(f, e.w, e.y);
         }
@@ -364,7 +371,9 @@ __global__ void __launch_bounds__(kGatherThreads, MINB)
         const float t = __fadd_rd(s, kFloorMagic);
         const float f = s - (t - kFloorMagic);
         const unsigned addr = wc.off + kout16[r] + ((unsigned)__float_as_int(t) << 4);
-        const float4 e = *reinterpret_cast<const float4 *>(swb + addr);
+        float4 e = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (KK_IN_BOUNDS(g_bounds_das, (unsigned)((int)(addr >> 4) - j * win) < (unsigned)win))
+          e = *reinterpret_cast<const float4 *>(swb + addr);
         sacc[r].x += fmaf(f, e.z, e.x);
         sacc[r].y += fmaf(f, e.w, e.y);
       }
@@ -443,6 +452,16 @@ int das_staged_stage(int win) {
   if (q == 8) return 4;
   return 0;
 }
+
+#ifdef KK_DEBUG_BOUNDS
+cudaError_t take_bounds_das(unsigned long long *n) {
+  unsigned v = 0, zero = 0;
+  cudaError_t e = cudaMemcpyFromSymbol(&v, g_bounds_das, sizeof(v));
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_bounds_das, &zero, sizeof(zero));
+  *n = v;
+  return e;
+}
+#endif
 
 cudaError_t launch_das_gather(const kk_plan &p, const float2 *y, float2 *B, float *I,
                               float2 *partial, cudaStream_t s) {

@@ -74,6 +74,11 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 
 __device__ __forceinline__ float2 f2add(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 
+#ifdef KK_DEBUG_BOUNDS
+// failed staged-window index checks of this file's gathers
+static __device__ unsigned g_bounds_kk = 0;
+#endif
+
 // Per-pair state of the delay tables, double-buffered by stage.
 template <int STAGE, bool VOL = false>
 struct GatherSmem {
@@ -280,7 +285,9 @@ __device__ __forceinline__ void gather_tile(const GatherArgs &a, int tile, int s
         const float t = __fadd_rd(s, kFloorMagic);
         const float f = s - (t - kFloorMagic);
         const unsigned addr = wp.off + ((unsigned)__float_as_int(t) << 4);
-        const float4 e = *reinterpret_cast<const float4 *>(swb + addr);
+        float4 e = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (KK_IN_BOUNDS(g_bounds_kk, (unsigned)((int)(addr >> 4) - j * win) < (unsigned)win))
+          e = *reinterpret_cast<const float4 *>(swb + addr);
         sacc[r].x += fmaf(f, e.z, e.x);
         sacc[r].y += fmaf(f, e.w, e.y);
       }
@@ -516,6 +523,16 @@ cudaError_t launch_kk_gather_batch(int rows, int stage, const GatherArgs *frames
     default: return cudaErrorInvalidConfiguration;
   }
 }
+
+#ifdef KK_DEBUG_BOUNDS
+cudaError_t take_bounds_kk(unsigned long long *n) {
+  unsigned v = 0, zero = 0;
+  cudaError_t e = cudaMemcpyFromSymbol(&v, g_bounds_kk, sizeof(v));
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_bounds_kk, &zero, sizeof(zero));
+  *n = v;
+  return e;
+}
+#endif
 
 int gather_entries_per_lane(int win) {
   const int q = (win + 31) / 32;

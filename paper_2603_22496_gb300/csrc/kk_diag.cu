@@ -1,4 +1,5 @@
-// kk_diag.cu -- check of the bounded device-side waits.
+// kk_diag.cu -- checks of the library's failure detection: the bounded
+// device-side waits, and the counters of the bounds-checked build.
 //
 // Every pipelined kernel of the library (bulk-copy-fed FFTs and contractions,
 // tensor-core contractions and convolutions) waits on mbarriers through
@@ -41,4 +42,21 @@ extern "C" kk_status kk_plan_check_wait_timeout(const kk_plan *p, int64_t limit_
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "wait-timeout check launch");
   return KK_OK;
+}
+
+extern "C" kk_status kk_debug_bounds(int64_t *violations) {
+  if (!violations) { set_error("null argument"); return KK_ERR_INVALID_ARG; }
+#ifdef KK_DEBUG_BOUNDS
+  unsigned long long a = 0, b = 0;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = take_bounds_kk(&a);
+  if (e == cudaSuccess) e = take_bounds_das(&b);
+  if (e != cudaSuccess) return cuda_fail(e, "bounds counters");
+  *violations = (int64_t)(a + b);
+  return KK_OK;
+#else
+  *violations = 0;
+  set_error("not a bounds-checked build (compile with KK_DEBUG_BOUNDS)");
+  return KK_ERR_UNSUPPORTED;
+#endif
 }

@@ -127,6 +127,25 @@ struct kk_plan {
 
 namespace kk {
 
+// Bounds-checked build: KK_IN_BOUNDS(counter, ok) counts a failed index check
+// in the translation unit's device counter and yields ok (the caller skips
+// the access); in the product build it is the constant true and the check is
+// not compiled.  Each file with checks keeps its own counter, taken (read and
+// reset) by the host functions below.
+#ifdef KK_DEBUG_BOUNDS
+#define KK_IN_BOUNDS(counter, ok) ::kk::bound_check(&(counter), (ok))
+#ifdef __CUDACC__
+__device__ __forceinline__ bool bound_check(unsigned *counter, bool ok) {
+  if (!ok) atomicAdd(counter, 1u);
+  return ok;
+}
+#endif
+cudaError_t take_bounds_kk(unsigned long long *n);
+cudaError_t take_bounds_das(unsigned long long *n);
+#else
+#define KK_IN_BOUNDS(counter, ok) true
+#endif
+
 // staged entries a lane of the gather kernels holds in registers
 constexpr int kMaxStagedEntries = 8;
 int gather_entries_per_lane(int win);

@@ -876,6 +876,9 @@ kk_status kk_plan_get_info(const kk_plan *p, kk_plan_info *info) {
   info->compression_factor = p->compression;
   info->launches_decompose = p->is_das ? 0 : 3;
   info->launches_beamform = (p->is_das ? 2 : 0) + (p->bf_split > 1 ? 2 : 1);
+  info->gather_rows = p->bf_rows;
+  info->gather_stage = p->bf_stage;
+  info->gather_split = p->bf_split;
   return KK_OK;
 }
 

@@ -111,6 +111,7 @@ int main(void) {
   printf("kk_plan_desc %zu\\nkk_plan_info %zu\\n", sizeof(kk_plan_desc), sizeof(kk_plan_info));
   P(kk_plan_desc, aperture); P(kk_plan_desc, elem_y); P(kk_plan_desc, rx_angles_y); P(kk_plan_desc, ny);
   P(kk_plan_desc, dy); P(kk_plan_info, ny); P(kk_plan_info, is_volume); P(kk_plan_info, sep_my);
+  P(kk_plan_info, gather_rows); P(kk_plan_info, gather_split);
   P(kk_stream_info, n_groups); P(kk_stream_info, events_pushed); P(kk_stream_info, device_bytes);
   return 0;
 }
@@ -141,7 +142,9 @@ int main(void) {
             "kk_plan_desc.rx_angles_y": kb.kk_plan_desc.rx_angles_y.offset,
             "kk_plan_desc.ny": kb.kk_plan_desc.ny.offset, "kk_plan_desc.dy": kb.kk_plan_desc.dy.offset,
             "kk_plan_info.ny": kb.kk_plan_info.ny.offset, "kk_plan_info.is_volume": kb.kk_plan_info.is_volume.offset,
-            "kk_plan_info.sep_my": kb.kk_plan_info.sep_my.offset}
+            "kk_plan_info.sep_my": kb.kk_plan_info.sep_my.offset,
+            "kk_plan_info.gather_rows": kb.kk_plan_info.gather_rows.offset,
+            "kk_plan_info.gather_split": kb.kk_plan_info.gather_split.offset}
     assert {k: int(v) for k, v in got.items()} == want
 
 
@@ -161,3 +164,18 @@ def test_quality_validation_is_host_side(lib, kw):
     with pytest.raises(kb.KKError) as e:
         kb.Quality(**args)
     assert e.value.status == kb.KK_ERR_INVALID_ARG
+
+
+def test_bounds_checked_variant_builds_with_the_same_exports(lib):
+    """The KK_DEBUG_BOUNDS variant compiles for sm_103a and exports the same
+    symbols; the product build answers kk_debug_bounds with
+    KK_ERR_UNSUPPORTED (no device call)."""
+    path = kbuild.build(variant="bounds")
+    sym = {}
+    for p in (kb.library_path(), path):
+        out = subprocess.run(["nm", "-D", "--defined-only", p], capture_output=True, text=True, check=True).stdout
+        sym[p] = {s for s in re.findall(r"\s[TW]\s+(\S+)", out) if s.startswith(("kk_", "das_"))}
+    assert sym[kb.library_path()] == sym[path]
+    with pytest.raises(kb.KKError) as e:
+        kb.kk_debug_bounds()
+    assert e.value.status == kb.KK_ERR_UNSUPPORTED

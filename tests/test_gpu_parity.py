@@ -294,6 +294,7 @@ def test_every_gather_configuration(rows, stage):
     ops, (rx, pairs, grp, J) = kc.scheme_both("hybrid", w.tx_angles, 7, js=[0, 3, 5])
     plan = kc.kk_plan_for(w, rx, pairs, grp, J, kb.KK_COMPOUND_COHERENT, grid)
     plan.set_gather(rows, stage)
+    assert (plan.info.gather_rows, plan.info.gather_stage) == (rows, stage)
     ws, rt, B, I = plan.empty_workspace(), plan.empty_rf_theta(), plan.empty_image(), plan.empty_intensity()
     plan.decompose(kc.to_dev(w.rf), rt, ws)
     plan.beamform(rt, B, I, ws)
@@ -333,13 +334,37 @@ def test_workspace_allocated_before_a_shape_change_stays_valid():
     rt, I = plan.empty_rf_theta(), plan.empty_intensity()
     plan.decompose(kc.to_dev(w.rf), rt, ws)
     images = []
+    splits = set()
     for rows, stage in [(4, 16), (8, 4), (8, 8), (2, 4), (4, 4)]:
         plan.set_gather(rows, stage)
+        splits.add(plan.info.gather_split)
         assert plan.info.workspace_bytes == nbytes
         B = plan.empty_image()
         plan.beamform(rt, B, I, ws)
         torch.cuda.synchronize()
         images.append(kc.cplx(B))
     assert bool((raw[nbytes:] == 0x5A).all())
+    assert len(splits) >= 3
     for img in images[1:]:
         assert kc.rel_l2(img, images[0]) <= 1e-6
+
+
+@pytest.mark.parametrize("dx", [0.075e-3, 0.3e-3])
+def test_windows_before_the_record_start_and_coarse_pitch(dx):
+    """A grid from 0.5 mm below the array to past the record's end: the
+    staged windows of some (tile, pair) start before sample 0 and others run
+    past T - 1, and at the coarse pitch the delay step along x exceeds one
+    sample; every pixel matches the oracle."""
+    import torch
+    w = kksynth.workload_small()
+    nx = int(round(20e-3 / dx)) | 1
+    grid = (nx, 160, -10e-3, dx, 0.5e-3, 0.15e-3)
+    ops, (rx, pairs, grp, J) = kc.scheme_both("confocal", w.tx_angles, 13)
+    plan = kc.kk_plan_for(w, rx, pairs, grp, J, kb.KK_COMPOUND_COHERENT, grid)
+    ws, rt, B, I = plan.empty_workspace(), plan.empty_rf_theta(), plan.empty_image(), plan.empty_intensity()
+    plan.decompose(kc.to_dev(w.rf), rt, ws)
+    plan.beamform(rt, B, I, ws)
+    torch.cuda.synchronize()
+    ref = kk.kk_image(w.rf, w.elem_x, ops, grid, FS, C)
+    assert kc.rel_l2(kc.cplx(B), ref) <= TOL
+    assert kc.rel_l2(I.cpu().numpy(), kk.compound(ref, "coherent")) <= 2 * TOL
