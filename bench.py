@@ -194,7 +194,7 @@ def _vernier_pairs(w, kb):
     return rx, pairs
 
 
-def _batch_frames(kb, n_frames, seed0=4000, speckle_per_mm2=10.0):
+def _batch_frames(kb, n_frames, seed0=4000, speckle_per_mm2=34.0):
     """Frames of uneven size for the batched form: elements in {64, 128, 192,
     256} (0.3 mm pitch), records of 1024-4096 samples, 8-75 transmits over
     +-16 deg, pair sets of 32-512 pairs (vernier, shifted, confocal or hybrid

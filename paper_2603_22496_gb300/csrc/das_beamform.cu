@@ -319,8 +319,8 @@ __global__ void __launch_bounds__(kGatherThreads, MINB)
     DAS_LOAD_RAW(0, 0);
   }
   int cur_l = -1;
-  unsigned kout16[ROWS];
-  float fout[ROWS];
+  float fo[ROWS];     // receive delay of this thread's pixels minus kl16 / 16
+  unsigned kl16 = 0;  // integer receive delay of the thread's first row, x 16 bytes
   const char *swb = reinterpret_cast<const char *>(sw);
   for (int q = 0; q < nq; ++q) {
     const int l = lb + q / spl;
@@ -342,10 +342,14 @@ __global__ void __launch_bounds__(kGatherThreads, MINB)
     __syncthreads();  // entries of this stage and tables of the next visible
     if (q + 1 < nq) DAS_LOAD_RAW(q + 1, buf ^ 1);  // in flight during the gathers
     if (l != cur_l) {
-      // receive delay of this thread's pixels for element l: integer (x16) + fraction
+      // receive delay of this thread's pixels for element l: the integer
+      // delay of its first row (kl, folded into the per-channel offset, so a
+      // lerp adds no integer) plus a small remainder per row (integer part
+      // exact, fraction from the double-float root)
       cur_l = l;
       const float2 u = __ldg(us + l);
       const float2 dx2 = df_sqr(df_sub(xq, u));
+      int kl = 0;
 #pragma unroll
       for (int r = 0; r < ROWS; ++r) {
         const float2 S = df_add(dx2, z2[r]);
@@ -353,9 +357,10 @@ __global__ void __launch_bounds__(kGatherThreads, MINB)
         const float t = fmaf(-rh, rh, S.x) + S.y;
         const float corr = (rh > 0.f) ? t / (2.f * rh) : 0.f;
         const float kf = floorf(rh);
-        kout16[r] = (unsigned)(int)kf * 16u;
-        fout[r] = (rh - kf) + corr;
+        if (r == 0) kl = (int)kf;
+        fo[r] = (float)((int)kf - kl) + ((rh - kf) + corr);
       }
+      kl16 = (unsigned)kl * 16u;
     }
     float2 sacc[ROWS];
 #pragma unroll
@@ -365,12 +370,13 @@ __global__ void __launch_bounds__(kGatherThreads, MINB)
       const float2 ab = s_ab[buf][j];
       const WarpChan wc = s_wc[buf][warp][j];
       const float base = fmaf(ab.x, dl, wc.phi);
+      const unsigned offl = wc.off + kl16;
 #pragma unroll
       for (int r = 0; r < ROWS; ++r) {
-        const float s = fmaf(ab.y, (float)(r - ROWS / 2), base) + fout[r];
+        const float s = fmaf(ab.y, (float)(r - ROWS / 2), base) + fo[r];
         const float t = __fadd_rd(s, kFloorMagic);
         const float f = s - (t - kFloorMagic);
-        const unsigned addr = wc.off + kout16[r] + ((unsigned)__float_as_int(t) << 4);
+        const unsigned addr = offl + ((unsigned)__float_as_int(t) << 4);
         float4 e = make_float4(0.f, 0.f, 0.f, 0.f);
         if (KK_IN_BOUNDS(g_bounds_das, (unsigned)((int)(addr >> 4) - j * win) < (unsigned)win))
           e = *reinterpret_cast<const float4 *>(swb + addr);

@@ -307,6 +307,229 @@ __global__ void __launch_bounds__(kT2Threads, 1)
   if (warp == 0) tmem_dealloc(tmem, 2 * ncols);
 }
 
+// ---- warp-specialised pipelined form (BF16 / FP16) --------------------------
+// Same operands, layouts, arithmetic and K order as k_shear_tc2, with the
+// work split over warp roles that meet only at mbarriers (no CTA-wide
+// barrier in the main loop):
+//   * 16 producer warps generate A one 64-element K chunk (128 rows x 128
+//     bytes) at a time into a ring of kT3Slots chunk slots (two items), from
+//     shear phases read through the cache (the ring leaves no room for them);
+//   * one thread issues the bin's 2D bulk copies of B (two stages, one bin
+//     ahead) and, per chunk, the four MMAs, committing each chunk's slot back
+//     to the producers and each item's accumulator to the epilogue;
+//   * 8 epilogue warps read the two alternating TMEM accumulators and store Y.
+// A producer reuses a slot after the MMAs that read it have completed; the
+// issuer starts an item's MMAs once its accumulator has been drained.
+// Every wait is bounded; a role that gives up raises the CTA's abort flag,
+// which every other wait also watches.
+constexpr int kT3Producers = 512;
+constexpr int kT3Epi = 256;
+constexpr int kT3Threads = kT3Producers + 32 + kT3Epi;
+constexpr int kT3Slots = 8;
+
+template <int KIND>
+__global__ void __launch_bounds__(kT3Threads, 1)
+    k_shear_tc3(const __grid_constant__ CUtensorMap xmap, const uint32_t *__restrict__ phase, int F, int L,
+                int Nu, int Mu, int NP, float yscale, float2 *__restrict__ Y, int *__restrict__ status) {
+  static_assert(KIND == 0 || KIND == 1, "BF16 / FP16 forms");
+  constexpr uint32_t CH_BYTES = (uint32_t)kRowsM * 128u;  // one chunk of A: 16 KB
+  constexpr uint32_t SBO = 1024u;                         // 8 rows x 128 bytes
+  extern __shared__ __align__(1024) unsigned char smem[];
+  __shared__ __align__(8) uint64_t afull[kT3Slots], aempty[kT3Slots], bfull[2], bempty[2], accfull[2],
+      accempty[2], drain;
+  __shared__ uint32_t tmem_slot;
+  __shared__ int s_abort;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int nch = (2 * L + 63) / 64;                       // chunks holding data (<= 4)
+  const uint32_t B_BYTES = (uint32_t)nch * (uint32_t)NP * 128u;
+  const uint32_t sbase = smem_u32(smem);
+  const uint32_t sA = sbase;                               // ring of chunk slots
+  const uint32_t sB0 = sbase + kT3Slots * CH_BYTES;        // two B stages
+  const int ntile = (Mu + kRowsM / 2 - 1) / (kRowsM / 2);
+  const int nbins = (int)blockIdx.x < F ? (F - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+  const int nitems = nbins * ntile;
+  uint32_t ncols = 32;
+  while ((int)ncols < NP) ncols <<= 1;
+  if (warp == 0) {
+    tmem_alloc(&tmem_slot, 2 * ncols);
+    tmem_relinquish();
+  }
+  if (tid == 0) {
+    for (int q = 0; q < kT3Slots; ++q) {
+      mbar_init(&afull[q], kT3Producers);
+      mbar_init(&aempty[q], 1);
+    }
+    for (int q = 0; q < 2; ++q) {
+      mbar_init(&bfull[q], 1);
+      mbar_init(&bempty[q], 1);
+      mbar_init(&accfull[q], 1);
+      mbar_init(&accempty[q], kT3Epi);
+    }
+    mbar_init(&drain, 1);
+    s_abort = 0;
+    mbar_init_fence();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+  volatile int *abort_flag = &s_abort;
+  // bounded wait that also gives up when another role has aborted
+  auto wait = [&](uint64_t *bar, uint32_t parity) -> bool {
+    if (mbar_try_wait(bar, parity)) return true;  // the timer is read only when the wait is real
+    const unsigned long long t0 = globaltimer();
+    while (!mbar_try_wait(bar, parity)) {
+      if (*abort_flag || globaltimer() - t0 > kWaitNs) {
+        *abort_flag = 1;
+        return false;
+      }
+    }
+    return true;
+  };
+  auto bin_of = [&](int jj) { return (int)blockIdx.x + jj * (int)gridDim.x; };
+  if (warp < kT3Producers / 32) {
+    // ---- producers: chunk c of item n's A into slot (n nch + c) % kT3Slots;
+    // thread = (row pair ol, 16-byte unit u) of a chunk; two chunks per step
+    // (eight W values in flight) ----
+    const int ol = tid >> 3, u = tid & 7;
+    const int R0 = 2 * ol, R1 = R0 + 1;
+    bool ok = true;
+    for (int n = 0; ok && n < nitems; ++n) {
+      const int jj = n / ntile, t = n - jj * ntile;
+      const uint32_t k32 = (uint32_t)bin_of(jj);
+      const int o = t * (kRowsM / 2) + ol;
+      for (int c = 0; ok && c < nch; c += 2) {
+        const int nc2 = min(2, nch - c);
+        uint4 re[2], im[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int l0 = 32 * (c + h) + 4 * u;
+          uint4 p4 = make_uint4(0u, 0u, 0u, 0u);
+          if (h < nc2 && o < Mu && l0 < L) p4 = __ldg(reinterpret_cast<const uint4 *>(phase + (size_t)o * L + l0));
+          const uint32_t ph4[4] = {p4.x, p4.y, p4.z, p4.w};
+          float wr[4], wi[4];
+#pragma unroll
+          for (int qq = 0; qq < 4; ++qq) {
+            wr[qq] = wi[qq] = 0.f;
+            if (h < nc2 && o < Mu && l0 + qq < L) {
+              const uint32_t ph = ph4[qq] * k32;                            // k phi mod 1 turn
+              const float ang = (float)(int)ph * 1.4629180792671596e-09f;  // 2 pi / 2^32
+              float sn, cs;
+              __sincosf(ang, &sn, &cs);
+              wr[qq] = cs;
+              wi[qq] = sn;
+            }
+          }
+          if constexpr (KIND == 0) {
+            re[h] = make_uint4(pack_bf16(wr[0], -wi[0]), pack_bf16(wr[1], -wi[1]), pack_bf16(wr[2], -wi[2]),
+                               pack_bf16(wr[3], -wi[3]));
+            im[h] = make_uint4(pack_bf16(wi[0], wr[0]), pack_bf16(wi[1], wr[1]), pack_bf16(wi[2], wr[2]),
+                               pack_bf16(wi[3], wr[3]));
+          } else {
+            re[h] = make_uint4(pack_f16(wr[0], -wi[0]), pack_f16(wr[1], -wi[1]), pack_f16(wr[2], -wi[2]),
+                               pack_f16(wr[3], -wi[3]));
+            im[h] = make_uint4(pack_f16(wi[0], wr[0]), pack_f16(wi[1], wr[1]), pack_f16(wi[2], wr[2]),
+                               pack_f16(wi[3], wr[3]));
+          }
+        }
+        for (int h = 0; h < nc2; ++h) {
+          const int q = n * nch + c + h, s = q % kT3Slots;
+          if (q >= kT3Slots && !(ok = wait(&aempty[s], (uint32_t)((q / kT3Slots) - 1) & 1u))) break;
+          unsigned char *base = smem + (size_t)s * CH_BYTES;
+          *reinterpret_cast<uint4 *>(base + R0 * 128 + ((u ^ (R0 & 7)) << 4)) = re[h];
+          *reinterpret_cast<uint4 *>(base + R1 * 128 + ((u ^ (R1 & 7)) << 4)) = im[h];
+          fence_async_smem();
+          mbar_arrive(&afull[s]);
+        }
+      }
+    }
+  } else if (warp == kT3Producers / 32) {
+    // ---- one thread: copies of B and the MMAs ----
+    if (lane == 0) {
+      const uint32_t idesc = instr_desc(Fmt<KIND>::code, kRowsM, (uint32_t)NP);
+      auto issue_b = [&](int jj) {
+        const uint32_t dst = sB0 + (uint32_t)(jj & 1) * B_BYTES;
+        tma::mbar_expect_tx(&bfull[jj & 1], B_BYTES);
+        for (int c = 0; c < nch; ++c)
+          tma::tma_2d(dst + (uint32_t)c * (uint32_t)NP * 128u, &xmap, 64 * c, bin_of(jj) * Nu, &bfull[jj & 1]);
+      };
+      int issued = 0, waited = 0;
+      if (nbins > 0) issue_b(issued++);
+      if (nbins > 1) issue_b(issued++);
+      bool ok = true;
+      for (int jj = 0; ok && jj < nbins; ++jj) {
+        if (jj >= 1 && jj + 1 < nbins) {
+          // stage (jj + 1) & 1 held bin jj - 1: refill it once that bin's MMAs are done
+          if (!(ok = wait(&bempty[(jj - 1) & 1], (uint32_t)((jj - 1) >> 1) & 1u))) break;
+          issue_b(issued++);
+        }
+        if (!(ok = wait(&bfull[jj & 1], (uint32_t)(jj >> 1) & 1u))) break;
+        waited = jj + 1;
+        const uint32_t sB = sB0 + (uint32_t)(jj & 1) * B_BYTES;
+        for (int t = 0; ok && t < ntile; ++t) {
+          const int n = jj * ntile + t;
+          if (n >= 2 && !(ok = wait(&accempty[n & 1], (uint32_t)((n >> 1) - 1) & 1u))) break;
+          const uint32_t acc = tmem + (uint32_t)(n & 1) * ncols;
+          for (int c = 0; ok && c < nch; ++c) {
+            const int q = n * nch + c, s = q % kT3Slots;
+            if (!(ok = wait(&afull[s], (uint32_t)(q / kT3Slots) & 1u))) break;
+            tc_fence_after();
+#pragma unroll
+            for (int ks = 0; ks < 4; ++ks) {
+              const uint64_t ad = smem_desc(sA + (uint32_t)s * CH_BYTES + (uint32_t)ks * 32u, 16, SBO) | (2ull << 61);
+              const uint64_t bd =
+                  smem_desc(sB + (uint32_t)c * (uint32_t)NP * 128u + (uint32_t)ks * 32u, 16, SBO) | (2ull << 61);
+              mma<KIND>(acc, ad, bd, idesc, (c > 0 || ks > 0) ? 1u : 0u);
+            }
+            mma_commit(&aempty[s]);
+          }
+          if (ok) mma_commit(&accfull[n & 1]);
+        }
+        if (ok) mma_commit(&bempty[jj & 1]);
+      }
+      // every MMA this thread issued has completed (bounded), and so has
+      // every copy it issued, before the CTA frees TMEM and exits
+      mma_commit(&drain);
+      mbar_wait(&drain, 0u);
+      if (!ok) {
+        atomicExch(status, (int)KK_ERR_TIMEOUT);
+        for (int jb = waited; jb < issued; ++jb) mbar_wait(&bfull[jb & 1], (uint32_t)(jb >> 1) & 1u);
+      }
+    }
+  } else {
+    // ---- epilogue: warp reads TMEM lane quarter warp % 4, column half ew / 4 ----
+    const int ew = warp - (kT3Producers / 32 + 1);
+    const int quarter = warp & 3, half = ew >> 2;
+    const int r = quarter * 32 + lane;
+    for (int n = 0; n < nitems; ++n) {
+      const int jj = n / ntile, t = n - jj * ntile;
+      const int k = bin_of(jj);
+      bool ok = lane == 0 ? wait(&accfull[n & 1], (uint32_t)(n >> 1) & 1u) : true;
+      ok = __shfl_sync(0xffffffffu, ok, 0);
+      if (!ok) break;
+      tc_fence_after();
+      const int o = t * (kRowsM / 2) + (r >> 1), part = r & 1;
+      const uint32_t trow = tmem + (uint32_t)(n & 1) * ncols + ((uint32_t)(quarter * 32) << 16);
+      float *Yf = reinterpret_cast<float *>(Y + (size_t)k * Nu * Mu);
+      for (int c0 = 16 * half; c0 < NP; c0 += 32) {
+        float v[16];
+        tmem_ld16(trow + (uint32_t)c0, v);
+#pragma unroll
+        for (int qq = 0; qq < 16; ++qq) {
+          const int i = c0 + qq;
+          if (i < Nu && o < Mu) Yf[((size_t)i * Mu + o) * 2 + part] = v[qq] * yscale;
+        }
+      }
+      tc_fence_before();
+      mbar_arrive(&accempty[n & 1]);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0) tmem_dealloc(tmem, 2 * ncols);
+}
+
 template <int KIND>
 __global__ void __launch_bounds__(kTcThreads, 2)
     k_shear_tc(const void *__restrict__ Xv, const uint32_t *__restrict__ phase, int F,
@@ -581,22 +804,14 @@ cudaError_t launch_shear_tc(const kk_plan &p, const void *X, float2 *Y, cudaStre
       p.Mu * p.L <= kT2MaxPhases && ((uintptr_t)X % 16) == 0) {
     CUtensorMap m;
     if (map_x(&m, X, p.F, p.Nu, p.L, NP, p.precision == KK_PREC_BF16)) {
-      const size_t smem2 = (size_t)kRowsM * kKC * 2 + 2 * (size_t)NP * kKC * 2 + (size_t)p.Mu * p.L * 4;
-      const int grid2 = std::min(p.F, sms);
-      cudaError_t e;
-      if (p.precision == KK_PREC_BF16) {
-        auto k = k_shear_tc2<0>;
-        e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
-        if (e != cudaSuccess) return e;
-        k<<<grid2, kT2Threads, smem2, s>>>(m, p.t.phase32, p.F, p.L, p.Nu, p.Mu, NP, 1.f / p.x_scale, Y,
-                                          p.t.status);
-      } else {
-        auto k = k_shear_tc2<1>;
-        e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
-        if (e != cudaSuccess) return e;
-        k<<<grid2, kT2Threads, smem2, s>>>(m, p.t.phase32, p.F, p.L, p.Nu, p.Mu, NP, 1.f / p.x_scale, Y,
-                                          p.t.status);
-      }
+      const int nch = (2 * p.L + 63) / 64;
+      const size_t smem3 = (size_t)kT3Slots * kRowsM * 128 + 2 * (size_t)nch * NP * 128;
+      const int grid3 = std::min(p.F, sms);
+      auto k = p.precision == KK_PREC_BF16 ? k_shear_tc3<0> : k_shear_tc3<1>;
+      cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem3);
+      if (e != cudaSuccess) return e;
+      k<<<grid3, kT3Threads, smem3, s>>>(m, p.t.phase32, p.F, p.L, p.Nu, p.Mu, NP, 1.f / p.x_scale, Y,
+                                         p.t.status);
       return cudaGetLastError();
     }
   }

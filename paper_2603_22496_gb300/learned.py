@@ -28,8 +28,8 @@ import time
 
 import numpy as np
 
-from . import (KK_COMPOUND_NONE, KK_PREC_BF16, KK_PREC_F32, KK_RF_F32, KK_SCHEME_VERNIER, Net, Plan,
-               kk_net_image_scale, kk_scheme_angles, kk_simulate_rf, load)
+from . import (KK_COMPOUND_NONE, KK_PREC_BF16, KK_PREC_F32, KK_RF_F32, KK_SCHEME_SHIFTED, KK_SCHEME_VERNIER, Net,
+               Plan, kk_net_image_scale, kk_scheme_angles, kk_simulate_rf, load)
 
 FS = 20e6
 C_SOUND = 1540.0
@@ -165,6 +165,57 @@ class Synth:
                 torch.cuda.synchronize()
                 print(f"  simulated {k + 1}/{len(seeds)}", flush=True)
         return X, Y
+
+    CORRUPTIONS = ("other_pair_set", "das", "noise", "wrong_sound_speed")
+
+    def corrupted(self, seed: int, kind: str, out=None):
+        """A wrong input for the judge, [nz][nx][2], from one seed's channel
+        data: the KK image of another 72-pair set (shifted scheme, j = N/2),
+        the DAS image, the compressed image plus white noise at 20 % of its
+        rms, or the compressed image beamformed with c = 1480 m/s instead of
+        1540 m/s."""
+        import torch
+        g = self.geo
+        if out is None:
+            out = torch.empty((g.nz, g.nx, 2), dtype=torch.float32, device="cuda")
+        rf = self.simulate(int(seed))
+        if kind == "other_pair_set":
+            if not hasattr(self, "plan_o"):
+                a = g.vernier_tx
+                rc, pc = vernier_pairs(g)
+                sub = np.unique(pc[:, 0])
+                dth = float(self.tx[sub[-1]] - self.tx[sub[0]]) / (a - 1)
+                ro = kk_scheme_angles(KK_SCHEME_SHIFTED, a, dth, g.vernier_rx, a // 2)
+                self.plan_o = Plan(self.elem_x, self.tx, g.grid, C_SOUND, FS, g.n_samples, KK_RF_F32,
+                                   rx_angles=ro, pairs=pc, compound=KK_COMPOUND_NONE)
+                self.bufs_o = (self.plan_o.empty_workspace(), self.plan_o.empty_rf_theta())
+            ws, rt = self.bufs_o
+            self.plan_o.decompose(rf, rt, ws)
+            self.plan_o.beamform(rt, out, None, ws)
+        elif kind == "das":
+            if not hasattr(self, "plan_d"):
+                self.plan_d = Plan(self.elem_x, self.tx, g.grid, C_SOUND, FS, g.n_samples, KK_RF_F32, das=True)
+                self.ws_d = self.plan_d.empty_workspace()
+            self.plan_d.das(rf, out, None, self.ws_d)
+        elif kind == "noise":
+            p, ws, rt = self.bufs[0]
+            p.decompose(rf, rt, ws)
+            p.beamform(rt, out, None, ws)
+            gen = torch.Generator(device="cuda").manual_seed(int(seed) + 17)
+            rms = out.pow(2).sum(-1).mean().sqrt()
+            out.add_(torch.randn(out.shape, device="cuda", generator=gen) * (0.2 * rms / np.sqrt(2.0)))
+        elif kind == "wrong_sound_speed":
+            if not hasattr(self, "plan_c"):
+                rc, pc = vernier_pairs(g)
+                self.plan_c = Plan(self.elem_x, self.tx, g.grid, 1480.0, FS, g.n_samples, KK_RF_F32,
+                                   rx_angles=rc, pairs=pc, compound=KK_COMPOUND_NONE)
+                self.bufs_c = (self.plan_c.empty_workspace(), self.plan_c.empty_rf_theta())
+            ws, rt = self.bufs_c
+            self.plan_c.decompose(rf, rt, ws)
+            self.plan_c.beamform(rt, out, None, ws)
+        else:
+            raise ValueError(kind)
+        return out
 
     def psf(self):
         """KK images of one point at the grid centre (no noise), both pair sets."""
@@ -326,13 +377,19 @@ def main(argv=None):
     tau = ref.calibrate(X[:min(1000, X.shape[0])])
     e_in, e_net, st = ref.evaluate(Xe, Ye)
     acc = (st[:, 0] <= tau[0]) & (st[:, 1] <= tau[1])
+    rejected = {}
+    n_bad = min(a.eval_frames, 200)
+    for kind in Synth.CORRUPTIONS:
+        Xb = torch.stack([syn.corrupted(900_000 + i, kind).clone() for i in range(n_bad)])
+        _, stb = ref.forward(Xb)
+        rejected[kind] = float((~ref.accept(stb)).float().mean())
     print(json.dumps({
         "train_frames": a.train_frames, "eval_frames": a.eval_frames, "steps": a.steps, "batch": a.batch,
         "params": ref.net.n_params, "loss_first": float(losses[:50].mean()) if losses.size else None,
         "loss_last": float(losses[-50:].mean()) if losses.size else None,
         "err_compressed_mean": float(e_in.mean()), "err_refined_mean": float(e_net.mean()),
         "gain": float(e_in.mean() / e_net.mean()), "refined_better_frac": float((e_net < e_in).mean()),
-        "judge_tau": tau, "accepted_frac": float(acc.mean()),
+        "judge_tau": tau, "accepted_frac": float(acc.mean()), "corrupted_rejected_frac": rejected,
         "data_s": round(t_data, 1), "train_s": round(t_train, 1),
         "train_images_per_s": round(len(losses) * a.batch / max(t_train, 1e-9), 1)}))
 
