@@ -46,7 +46,8 @@ def _args():
     ap.add_argument("--oracle-timing", default=None, help=argparse.SUPPRESS)
     ap.add_argument("--profile", default=None,
                     choices=["kk_image", "decompose", "decompose_bf16", "decompose_f8e4m3", "das", "vernier",
-                             "refiner_step", "volume_contraction", "few_tx_contraction", "batch_gather"],
+                             "refiner_step", "volume_contraction", "few_tx_contraction", "batch_gather",
+                             "batch_graph"],
                     help="run three launches of one stage of the benchmark frame and exit "
                          "(a small, bounded target for ncu)")
     return ap.parse_args()
@@ -956,6 +957,15 @@ def run_profile(args):
             net.adam(1e-5)
         torch.cuda.synchronize()
         print(f"profile target {args.profile}: done (status {net.status()})")
+        return
+    if args.profile == "batch_graph":
+        # the whole 256-frame batch at the 4 x 8 shape (no autotuning): two graph runs
+        frames = _batch_frames(kb, 256)
+        batch = kb.Batch(frames, shape=408)
+        for _ in range(2):
+            batch.run()
+        torch.cuda.synchronize()
+        print(f"profile target {args.profile}: done ({batch.info.n_items} items, {batch.info.graph_nodes} nodes)")
         return
     if args.profile == "batch_gather":
         # the batched form on its first 16 uneven frames at the 4 x 8 shape: three graph runs

@@ -99,218 +99,18 @@ __device__ __forceinline__ uint32_t core_off(int row, int kbyte) {
          (uint32_t)(kbyte & 15);
 }
 
-// ---- pipelined form (BF16 / FP16, up to 96 transmits, Mu * L <= 16384) -------
+// ---- pipelined form (BF16 / FP16, up to 96 transmits) -----------------------
 // One persistent CTA per SM walks its bins; each bin is ceil(Mu / 64) items
-// (tiles of 128 rows of A).  The shear phases (independent of the bin) are
-// copied once into shared memory.  Operands use the 128-byte-swizzled K-major
+// (tiles of 128 rows of A).  Operands use the 128-byte-swizzled K-major
 // layout in chunks of 64 elements (128 rows / NP rows x 128 bytes, 16-byte
 // units XOR-ed with the row index within each 8-row group):
 //   B (the bin's spectrum rows) by 2D bulk copies of the [F * Nu][2L] spectra,
 //     box {64, NP}, into two stages one bin ahead (rows past Nu are the next
 //     bin's and only reach discarded outputs; past the last bin they are the
 //     copy's zero fill);
-//   A generated by all threads from the shared phases.
-// Two TMEM accumulators alternate, so item n's MMAs run while the threads
-// store item n - 1's accumulator.  Arithmetic and K order equal k_shear_tc's.
-constexpr int kT2Threads = 1024;
-constexpr int kT2MaxNP = 96;
-constexpr int kT2MaxPhases = 16384;  // Mu * L phases held in shared memory (64 KB)
-
-template <int KIND>
-__global__ void __launch_bounds__(kT2Threads, 1)
-    k_shear_tc2(const __grid_constant__ CUtensorMap xmap, const uint32_t *__restrict__ phase, int F, int L,
-                int Nu, int Mu, int NP, float yscale, float2 *__restrict__ Y, int *__restrict__ status) {
-  static_assert(KIND == 0 || KIND == 1, "BF16 / FP16 forms");
-  constexpr uint32_t A_BYTES = (uint32_t)kRowsM * kKC * 2;  // 64 KB
-  constexpr uint32_t SBO = 1024u;                           // 8 rows x 128 bytes
-  extern __shared__ __align__(1024) unsigned char smem[];
-  __shared__ __align__(8) uint64_t bbar[2], mbar[2], pbar;
-  __shared__ uint32_t tmem_slot;
-  __shared__ int s_abort;
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const uint32_t B_BYTES = (uint32_t)NP * kKC * 2;
-  const uint32_t sbase = smem_u32(smem);
-  const uint32_t sA = sbase;                                 // A: one stage
-  const uint32_t sB0 = sbase + A_BYTES;                      // B: two stages
-  const uint32_t *sPh = reinterpret_cast<const uint32_t *>(smem + A_BYTES + 2 * (size_t)B_BYTES);
-  const int nch = (2 * L + 63) / 64;                         // 64-element chunks holding data
-  const uint32_t btx = (uint32_t)nch * (uint32_t)NP * 128u;
-  const int ntile = (Mu + kRowsM / 2 - 1) / (kRowsM / 2);
-  const int ksteps = (2 * L + 15) / 16;
-  uint32_t ncols = 32;
-  while ((int)ncols < NP) ncols <<= 1;
-  if (warp == 0) {
-    tmem_alloc(&tmem_slot, 2 * ncols);
-    tmem_relinquish();
-  }
-  if (tid == 0) {
-    for (int q = 0; q < 2; ++q) {
-      mbar_init(&bbar[q], 1);
-      mbar_init(&mbar[q], 1);
-    }
-    mbar_init(&pbar, 1);
-    s_abort = 0;
-    mbar_init_fence();
-  }
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
-  const uint32_t tmem = tmem_slot;
-  const uint32_t idesc = instr_desc(Fmt<KIND>::code, kRowsM, (uint32_t)NP);
-  auto bin_of = [&](int j) { return (int)blockIdx.x + j * (int)gridDim.x; };
-  auto issue_b = [&](int j) {  // thread 0: bin j of this CTA into stage j & 1
-    const int k = bin_of(j);
-    const uint32_t dst = sB0 + (uint32_t)(j & 1) * B_BYTES;
-    tma::mbar_expect_tx(&bbar[j & 1], btx);
-    for (int c = 0; c < nch; ++c)
-      tma::tma_2d(dst + (uint32_t)c * (uint32_t)NP * 128u, &xmap, 64 * c, k * Nu, &bbar[j & 1]);
-  };
-  if (tid == 0) {
-    const uint32_t pbytes = (uint32_t)(Mu * L) * 4u;
-    tma::mbar_expect_tx(&pbar, pbytes);
-    tma::bulk_1d(smem_u32(sPh), phase, pbytes, &pbar);
-    if (bin_of(0) < F) issue_b(0);
-    if (bin_of(1) < F) issue_b(1);
-  }
-  bool ok = !__syncthreads_or(!mbar_wait(&pbar, 0u));
-  // epilogue of item m (bin j, tile t) from accumulator m & 1
-  auto epilogue = [&](int m, int j, int t) {
-    const int k = bin_of(j);
-    // warp w reads TMEM lane quarter w % 4 and every (kT2Threads / 128)-th
-    // 16-column chunk starting at chunk w / 4
-    const int quarter = warp & 3, half = warp >> 2;
-    const int r = quarter * 32 + lane;
-    const int o = t * (kRowsM / 2) + (r >> 1), part = r & 1;
-    const uint32_t trow = tmem + (uint32_t)(m & 1) * ncols + ((uint32_t)(quarter * 32) << 16);
-    float *Yf = reinterpret_cast<float *>(Y + (size_t)k * Nu * Mu);
-    for (int c0 = 16 * half; c0 < NP; c0 += 16 * (kT2Threads / 128)) {
-      float v[16];
-      tmem_ld16(trow + (uint32_t)c0, v);
-#pragma unroll
-      for (int q = 0; q < 16; ++q) {
-        const int i = c0 + q;
-        if (i < Nu && o < Mu) Yf[((size_t)i * Mu + o) * 2 + part] = v[q] * yscale;
-      }
-    }
-  };
-  int n = 0, pj = -1, pt = 0;  // item counter; bin and tile of item n - 1
-  for (int j = 0; ok && bin_of(j) < F; ++j) {
-    const uint32_t k32 = (uint32_t)bin_of(j);
-    for (int t = 0; ok && t < ntile; ++t, ++n) {
-      // ---- item n - 1's MMAs done: A is free, its accumulator is ready ----
-      bool prev = true;
-      if (n >= 1) {
-        prev = !__syncthreads_or(!mbar_wait(&mbar[(n - 1) & 1], (uint32_t)((n - 1) >> 1) & 1u));
-        if (prev && tid == 0 && t == 0 && j >= 1 && bin_of(j + 1) < F) issue_b(j + 1);  // bin j - 1's stage
-      }
-      if (!prev) {
-        ok = false;
-        break;
-      }
-      // ---- generate A (rows (o, re) / (o, im), o = 64 t + row / 2) ----
-#pragma unroll 2
-      for (int e = tid; e < (kRowsM / 2) * (kKC / 8); e += kT2Threads) {
-        const int ol = e / (kKC / 8), c = e - ol * (kKC / 8);
-        const int o = t * (kRowsM / 2) + ol;
-        const int l0 = c * 4;
-        uint4 p4 = make_uint4(0u, 0u, 0u, 0u);
-        if (o < Mu && l0 < L) p4 = *reinterpret_cast<const uint4 *>(sPh + o * L + l0);  // L % 4 == 0
-        const uint32_t ph4[4] = {p4.x, p4.y, p4.z, p4.w};
-        float wr[4], wi[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          wr[q] = wi[q] = 0.f;
-          if (o < Mu && l0 + q < L) {
-            const uint32_t ph = ph4[q] * k32;
-            const float ang = (float)(int)ph * 1.4629180792671596e-09f;  // 2 pi / 2^32
-            float sn, cs;
-            __sincosf(ang, &sn, &cs);
-            wr[q] = cs;
-            wi[q] = sn;
-          }
-        }
-        uint4 re, im;
-        if constexpr (KIND == 0) {
-          re = make_uint4(pack_bf16(wr[0], -wi[0]), pack_bf16(wr[1], -wi[1]), pack_bf16(wr[2], -wi[2]),
-                          pack_bf16(wr[3], -wi[3]));
-          im = make_uint4(pack_bf16(wi[0], wr[0]), pack_bf16(wi[1], wr[1]), pack_bf16(wi[2], wr[2]),
-                          pack_bf16(wi[3], wr[3]));
-        } else {
-          re = make_uint4(pack_f16(wr[0], -wi[0]), pack_f16(wr[1], -wi[1]), pack_f16(wr[2], -wi[2]),
-                          pack_f16(wr[3], -wi[3]));
-          im = make_uint4(pack_f16(wi[0], wr[0]), pack_f16(wi[1], wr[1]), pack_f16(wi[2], wr[2]),
-                          pack_f16(wi[3], wr[3]));
-        }
-        const int chunk = c >> 3, u = c & 7;
-        const int R0 = 2 * ol, R1 = 2 * ol + 1;
-        unsigned char *base = smem + (size_t)chunk * (kRowsM * 128);
-        *reinterpret_cast<uint4 *>(base + R0 * 128 + ((u ^ (R0 & 7)) << 4)) = re;
-        *reinterpret_cast<uint4 *>(base + R1 * 128 + ((u ^ (R1 & 7)) << 4)) = im;
-      }
-      fence_async_smem();
-      __syncthreads();
-      if (tid == 0) {
-        bool got = true;
-        if (t == 0) got = mbar_wait(&bbar[j & 1], (uint32_t)(j >> 1) & 1u);
-        if (!got) {
-          s_abort = 1;
-        } else {
-          tc_fence_after();
-          const uint32_t sB = sB0 + (uint32_t)(j & 1) * B_BYTES;
-          const uint32_t acc = tmem + (uint32_t)(n & 1) * ncols;
-#pragma unroll 1
-          for (int st = 0; st < ksteps; ++st) {
-            const uint32_t ch = (uint32_t)(st >> 2), w = (uint32_t)(st & 3) * 32u;
-            const uint64_t ad = smem_desc(sA + ch * (uint32_t)(kRowsM * 128) + w, 16, SBO) | (2ull << 61);
-            const uint64_t bd = smem_desc(sB + ch * (uint32_t)NP * 128u + w, 16, SBO) | (2ull << 61);
-            mma<KIND>(acc, ad, bd, idesc, st > 0 ? 1u : 0u);
-          }
-          mma_commit(&mbar[n & 1]);
-        }
-      }
-      // ---- store item n - 1 while item n's MMAs run ----
-      if (n >= 1) {
-        tc_fence_after();
-        epilogue(n - 1, pj, pt);
-      }
-      pj = j;
-      pt = t;
-      tc_fence_before();
-      __syncthreads();
-      if (s_abort) ok = false;
-    }
-  }
-  if (ok && n >= 1) {
-    const bool done = !__syncthreads_or(!mbar_wait(&mbar[(n - 1) & 1], (uint32_t)((n - 1) >> 1) & 1u));
-    if (done) {
-      tc_fence_after();
-      epilogue(n - 1, pj, pt);
-    } else {
-      ok = false;
-    }
-  }
-  __syncthreads();
-  if (!ok || s_abort) {
-    if (tid == 0) {
-      atomicExch(status, (int)KK_ERR_TIMEOUT);
-      // bounded waits for whatever this CTA may still have in flight before TMEM is freed
-      for (int q = 0; q < 2; ++q) {
-        mbar_wait(&mbar[q], 0u);
-        mbar_wait(&bbar[q], 0u);
-      }
-      mbar_wait(&pbar, 0u);
-    }
-  }
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
-  if (warp == 0) tmem_dealloc(tmem, 2 * ncols);
-}
-
-// ---- warp-specialised pipelined form (BF16 / FP16) --------------------------
-// Same operands, layouts, arithmetic and K order as k_shear_tc2, with the
-// work split over warp roles that meet only at mbarriers (no CTA-wide
-// barrier in the main loop):
+//   A generated on chip from the shear phases (0.32 fixed-point turns).
+// Arithmetic and K order equal k_shear_tc's.  The work is split over warp
+// roles that meet only at mbarriers (no CTA-wide barrier in the main loop):
 //   * 16 producer warps generate A one 64-element K chunk (128 rows x 128
 //     bytes) at a time into a ring of kT3Slots chunk slots (two items), from
 //     shear phases read through the cache (the ring leaves no room for them);
@@ -318,6 +118,7 @@ __global__ void __launch_bounds__(kT2Threads, 1)
 //     ahead) and, per chunk, the four MMAs, committing each chunk's slot back
 //     to the producers and each item's accumulator to the epilogue;
 //   * 8 epilogue warps read the two alternating TMEM accumulators and store Y.
+constexpr int kT3MaxNP = 96;
 // A producer reuses a slot after the MMAs that read it have completed; the
 // issuer starts an item's MMAs once its accumulator has been drained.
 // Every wait is bounded; a role that gives up raises the CTA's abort flag,
@@ -800,8 +601,8 @@ cudaError_t launch_shear_tc(const kk_plan &p, const void *X, float2 *Y, cudaStre
   const int NP = ((p.Nu + 15) / 16) * 16;
   int sms = 148;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p.device);
-  if ((p.precision == KK_PREC_BF16 || p.precision == KK_PREC_F16) && NP <= kT2MaxNP && p.L % 4 == 0 &&
-      p.Mu * p.L <= kT2MaxPhases && ((uintptr_t)X % 16) == 0) {
+  if ((p.precision == KK_PREC_BF16 || p.precision == KK_PREC_F16) && NP <= kT3MaxNP && p.L % 4 == 0 &&
+      ((uintptr_t)X % 16) == 0) {
     CUtensorMap m;
     if (map_x(&m, X, p.F, p.Nu, p.L, NP, p.precision == KK_PREC_BF16)) {
       const int nch = (2 * p.L + 63) / 64;

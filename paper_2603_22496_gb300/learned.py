@@ -205,14 +205,14 @@ class Synth:
             rms = out.pow(2).sum(-1).mean().sqrt()
             out.add_(torch.randn(out.shape, device="cuda", generator=gen) * (0.2 * rms / np.sqrt(2.0)))
         elif kind == "wrong_sound_speed":
-            if not hasattr(self, "plan_c"):
+            if not hasattr(self, "plan_w"):
                 rc, pc = vernier_pairs(g)
-                self.plan_c = Plan(self.elem_x, self.tx, g.grid, 1480.0, FS, g.n_samples, KK_RF_F32,
+                self.plan_w = Plan(self.elem_x, self.tx, g.grid, 1480.0, FS, g.n_samples, KK_RF_F32,
                                    rx_angles=rc, pairs=pc, compound=KK_COMPOUND_NONE)
-                self.bufs_c = (self.plan_c.empty_workspace(), self.plan_c.empty_rf_theta())
-            ws, rt = self.bufs_c
-            self.plan_c.decompose(rf, rt, ws)
-            self.plan_c.beamform(rt, out, None, ws)
+                self.bufs_w = (self.plan_w.empty_workspace(), self.plan_w.empty_rf_theta())
+            ws, rt = self.bufs_w
+            self.plan_w.decompose(rf, rt, ws)
+            self.plan_w.beamform(rt, out, None, ws)
         else:
             raise ValueError(kind)
         return out

@@ -161,3 +161,16 @@ def test_refined_wire_peaks_at_the_full_pair_image_pixels(trained):
     pix = np.concatenate(pix)
     orc = kk.kk_beamform(y, geo.elem_x(), ops, geo.grid, L.FS, L.C_SOUND, pixels=pix)[0]
     assert kc.rel_l2(full[0][pix[:, 1], pix[:, 0]], orc) <= 1e-2
+
+
+def test_judge_rejects_kk_images_of_other_pair_sets_and_das(trained):
+    """Wrong inputs that are real beamformed images, not noise: the KK image of
+    another 72-pair set (shifted scheme) and the DAS image of the same channel
+    data have k-space support off the compressed pair set's mask, and the
+    judge rejects them (the fallback then returns the plain full-pair image)."""
+    import torch
+    syn, ref, X, Y, Xe, Ye, _ = trained
+    for kind in ("other_pair_set", "das"):
+        Xb = torch.stack([syn.corrupted(900_000 + i, kind).clone() for i in range(8)])
+        _, st = ref.forward(Xb)
+        assert (~ref.accept(st)).float().mean().item() >= 0.9, kind
