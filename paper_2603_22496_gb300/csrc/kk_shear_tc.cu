@@ -112,12 +112,12 @@ __device__ __forceinline__ uint32_t core_off(int row, int kbyte) {
 // Arithmetic and K order equal k_shear_tc's.  The work is split over warp
 // roles that meet only at mbarriers (no CTA-wide barrier in the main loop):
 //   * 16 producer warps generate A one 64-element K chunk (128 rows x 128
-//     bytes) at a time into a ring of kT3Slots chunk slots (two items), from
+//     bytes) at a time into a ring of kT3Slots chunk slots (two tiles), from
 //     shear phases read through the cache (the ring leaves no room for them);
-//   * one thread issues the bin's 2D bulk copies of B (two stages, one bin
-//     ahead) and, per chunk, the four MMAs, committing each chunk's slot back
+//   * one thread issues the bins' 2D bulk copies of B (up to four stages, as
+//     many bins ahead as shared memory holds) and, per chunk, the four MMAs, committing each chunk's slot back
 //     to the producers and each item's accumulator to the epilogue;
-//   * 8 epilogue warps read the two alternating TMEM accumulators and store Y.
+//   * 8 epilogue warps read the TMEM accumulators (up to four, in turn) and store Y.
 constexpr int kT3MaxNP = 96;
 // A producer reuses a slot after the MMAs that read it have completed; the
 // issuer starts an item's MMAs once its accumulator has been drained.
@@ -127,17 +127,19 @@ constexpr int kT3Producers = 512;
 constexpr int kT3Epi = 256;
 constexpr int kT3Threads = kT3Producers + 32 + kT3Epi;
 constexpr int kT3Slots = 8;
+constexpr int kT3MaxB = 4;   // B stages (bins in flight), as many as shared memory holds
+constexpr int kT3MaxAcc = 4;
 
 template <int KIND>
 __global__ void __launch_bounds__(kT3Threads, 1)
     k_shear_tc3(const __grid_constant__ CUtensorMap xmap, const uint32_t *__restrict__ phase, int F, int L,
-                int Nu, int Mu, int NP, float yscale, float2 *__restrict__ Y, int *__restrict__ status) {
+                int Nu, int Mu, int NP, int nb, float yscale, float2 *__restrict__ Y, int *__restrict__ status) {
   static_assert(KIND == 0 || KIND == 1, "BF16 / FP16 forms");
   constexpr uint32_t CH_BYTES = (uint32_t)kRowsM * 128u;  // one chunk of A: 16 KB
   constexpr uint32_t SBO = 1024u;                         // 8 rows x 128 bytes
   extern __shared__ __align__(1024) unsigned char smem[];
-  __shared__ __align__(8) uint64_t afull[kT3Slots], aempty[kT3Slots], bfull[2], bempty[2], accfull[2],
-      accempty[2], drain;
+  __shared__ __align__(8) uint64_t afull[kT3Slots], aempty[kT3Slots], bfull[kT3MaxB], bempty[kT3MaxB], accfull[kT3MaxAcc],
+      accempty[kT3MaxAcc], drain;
   __shared__ uint32_t tmem_slot;
   __shared__ int s_abort;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -145,26 +147,31 @@ __global__ void __launch_bounds__(kT3Threads, 1)
   const uint32_t B_BYTES = (uint32_t)nch * (uint32_t)NP * 128u;
   const uint32_t sbase = smem_u32(smem);
   const uint32_t sA = sbase;                               // ring of chunk slots
-  const uint32_t sB0 = sbase + kT3Slots * CH_BYTES;        // two B stages
+  const uint32_t sB0 = sbase + kT3Slots * CH_BYTES;        // nb B stages
   const int ntile = (Mu + kRowsM / 2 - 1) / (kRowsM / 2);
   const int nbins = (int)blockIdx.x < F ? (F - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
   const int nitems = nbins * ntile;
   uint32_t ncols = 32;
   while ((int)ncols < NP) ncols <<= 1;
+  // as many accumulators as the SM's 512 TMEM columns hold (up to four), so
+  // the MMAs can run that many tiles ahead of the epilogue
+  const int nacc = (int)min(512u / ncols, (uint32_t)kT3MaxAcc);
   if (warp == 0) {
-    tmem_alloc(&tmem_slot, 2 * ncols);
+    tmem_alloc(&tmem_slot, nacc * ncols);
     tmem_relinquish();
   }
   if (tid == 0) {
     for (int q = 0; q < kT3Slots; ++q) {
-      mbar_init(&afull[q], kT3Producers);
+      mbar_init(&afull[q], kT3Producers / 32);   // one arrival per producer warp
       mbar_init(&aempty[q], 1);
     }
-    for (int q = 0; q < 2; ++q) {
+    for (int q = 0; q < kT3MaxB; ++q) {
       mbar_init(&bfull[q], 1);
       mbar_init(&bempty[q], 1);
+    }
+    for (int q = 0; q < kT3MaxAcc; ++q) {
       mbar_init(&accfull[q], 1);
-      mbar_init(&accempty[q], kT3Epi);
+      mbar_init(&accempty[q], kT3Epi / 32);      // one arrival per epilogue warp
     }
     mbar_init(&drain, 1);
     s_abort = 0;
@@ -235,12 +242,18 @@ __global__ void __launch_bounds__(kT3Threads, 1)
         }
         for (int h = 0; h < nc2; ++h) {
           const int q = n * nch + c + h, s = q % kT3Slots;
-          if (q >= kT3Slots && !(ok = wait(&aempty[s], (uint32_t)((q / kT3Slots) - 1) & 1u))) break;
+          if (q >= kT3Slots) {
+            // one lane waits for the slot, the warp follows its answer
+            bool got = lane == 0 ? wait(&aempty[s], (uint32_t)((q / kT3Slots) - 1) & 1u) : true;
+            got = __shfl_sync(0xffffffffu, got, 0);
+            if (!(ok = got)) break;
+          }
           unsigned char *base = smem + (size_t)s * CH_BYTES;
           *reinterpret_cast<uint4 *>(base + R0 * 128 + ((u ^ (R0 & 7)) << 4)) = re[h];
           *reinterpret_cast<uint4 *>(base + R1 * 128 + ((u ^ (R1 & 7)) << 4)) = im[h];
           fence_async_smem();
-          mbar_arrive(&afull[s]);
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&afull[s]);
         }
       }
     }
@@ -249,28 +262,28 @@ __global__ void __launch_bounds__(kT3Threads, 1)
     if (lane == 0) {
       const uint32_t idesc = instr_desc(Fmt<KIND>::code, kRowsM, (uint32_t)NP);
       auto issue_b = [&](int jj) {
-        const uint32_t dst = sB0 + (uint32_t)(jj & 1) * B_BYTES;
-        tma::mbar_expect_tx(&bfull[jj & 1], B_BYTES);
+        const uint32_t dst = sB0 + (uint32_t)(jj % nb) * B_BYTES;
+        tma::mbar_expect_tx(&bfull[jj % nb], B_BYTES);
         for (int c = 0; c < nch; ++c)
-          tma::tma_2d(dst + (uint32_t)c * (uint32_t)NP * 128u, &xmap, 64 * c, bin_of(jj) * Nu, &bfull[jj & 1]);
+          tma::tma_2d(dst + (uint32_t)c * (uint32_t)NP * 128u, &xmap, 64 * c, bin_of(jj) * Nu, &bfull[jj % nb]);
       };
       int issued = 0, waited = 0;
-      if (nbins > 0) issue_b(issued++);
-      if (nbins > 1) issue_b(issued++);
+      while (issued < nb && issued < nbins) issue_b(issued++);
       bool ok = true;
       for (int jj = 0; ok && jj < nbins; ++jj) {
-        if (jj >= 1 && jj + 1 < nbins) {
-          // stage (jj + 1) & 1 held bin jj - 1: refill it once that bin's MMAs are done
-          if (!(ok = wait(&bempty[(jj - 1) & 1], (uint32_t)((jj - 1) >> 1) & 1u))) break;
+        if (jj >= 1 && jj + nb - 1 < nbins) {
+          // stage (jj - 1) % nb held bin jj - 1: refill it with bin jj + nb - 1
+          // once that bin's MMAs are done
+          if (!(ok = wait(&bempty[(jj - 1) % nb], (uint32_t)((jj - 1) / nb) & 1u))) break;
           issue_b(issued++);
         }
-        if (!(ok = wait(&bfull[jj & 1], (uint32_t)(jj >> 1) & 1u))) break;
+        if (!(ok = wait(&bfull[jj % nb], (uint32_t)(jj / nb) & 1u))) break;
         waited = jj + 1;
-        const uint32_t sB = sB0 + (uint32_t)(jj & 1) * B_BYTES;
+        const uint32_t sB = sB0 + (uint32_t)(jj % nb) * B_BYTES;
         for (int t = 0; ok && t < ntile; ++t) {
           const int n = jj * ntile + t;
-          if (n >= 2 && !(ok = wait(&accempty[n & 1], (uint32_t)((n >> 1) - 1) & 1u))) break;
-          const uint32_t acc = tmem + (uint32_t)(n & 1) * ncols;
+          if (n >= nacc && !(ok = wait(&accempty[n % nacc], (uint32_t)((n / nacc) - 1) & 1u))) break;
+          const uint32_t acc = tmem + (uint32_t)(n % nacc) * ncols;
           for (int c = 0; ok && c < nch; ++c) {
             const int q = n * nch + c, s = q % kT3Slots;
             if (!(ok = wait(&afull[s], (uint32_t)(q / kT3Slots) & 1u))) break;
@@ -284,9 +297,9 @@ __global__ void __launch_bounds__(kT3Threads, 1)
             }
             mma_commit(&aempty[s]);
           }
-          if (ok) mma_commit(&accfull[n & 1]);
+          if (ok) mma_commit(&accfull[n % nacc]);
         }
-        if (ok) mma_commit(&bempty[jj & 1]);
+        if (ok) mma_commit(&bempty[jj % nb]);
       }
       // every MMA this thread issued has completed (bounded), and so has
       // every copy it issued, before the CTA frees TMEM and exits
@@ -294,7 +307,7 @@ __global__ void __launch_bounds__(kT3Threads, 1)
       mbar_wait(&drain, 0u);
       if (!ok) {
         atomicExch(status, (int)KK_ERR_TIMEOUT);
-        for (int jb = waited; jb < issued; ++jb) mbar_wait(&bfull[jb & 1], (uint32_t)(jb >> 1) & 1u);
+        for (int jb = waited; jb < issued; ++jb) mbar_wait(&bfull[jb % nb], (uint32_t)(jb / nb) & 1u);
       }
     }
   } else {
@@ -305,12 +318,12 @@ __global__ void __launch_bounds__(kT3Threads, 1)
     for (int n = 0; n < nitems; ++n) {
       const int jj = n / ntile, t = n - jj * ntile;
       const int k = bin_of(jj);
-      bool ok = lane == 0 ? wait(&accfull[n & 1], (uint32_t)(n >> 1) & 1u) : true;
+      bool ok = lane == 0 ? wait(&accfull[n % nacc], (uint32_t)(n / nacc) & 1u) : true;
       ok = __shfl_sync(0xffffffffu, ok, 0);
       if (!ok) break;
       tc_fence_after();
       const int o = t * (kRowsM / 2) + (r >> 1), part = r & 1;
-      const uint32_t trow = tmem + (uint32_t)(n & 1) * ncols + ((uint32_t)(quarter * 32) << 16);
+      const uint32_t trow = tmem + (uint32_t)(n % nacc) * ncols + ((uint32_t)(quarter * 32) << 16);
       float *Yf = reinterpret_cast<float *>(Y + (size_t)k * Nu * Mu);
       for (int c0 = 16 * half; c0 < NP; c0 += 32) {
         float v[16];
@@ -322,13 +335,14 @@ __global__ void __launch_bounds__(kT3Threads, 1)
         }
       }
       tc_fence_before();
-      mbar_arrive(&accempty[n & 1]);
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&accempty[n % nacc]);
     }
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if (warp == 0) tmem_dealloc(tmem, 2 * ncols);
+  if (warp == 0) tmem_dealloc(tmem, nacc * ncols);
 }
 
 template <int KIND>
@@ -606,12 +620,15 @@ cudaError_t launch_shear_tc(const kk_plan &p, const void *X, float2 *Y, cudaStre
     CUtensorMap m;
     if (map_x(&m, X, p.F, p.Nu, p.L, NP, p.precision == KK_PREC_BF16)) {
       const int nch = (2 * p.L + 63) / 64;
-      const size_t smem3 = (size_t)kT3Slots * kRowsM * 128 + 2 * (size_t)nch * NP * 128;
+      const size_t bbytes = (size_t)nch * NP * 128;
+      const size_t amax = (size_t)kT3Slots * kRowsM * 128;
+      const int nb = (int)std::min<size_t>(kT3MaxB, (227 * 1024 - 1024 - amax) / bbytes);
+      const size_t smem3 = amax + (size_t)nb * bbytes;
       const int grid3 = std::min(p.F, sms);
       auto k = p.precision == KK_PREC_BF16 ? k_shear_tc3<0> : k_shear_tc3<1>;
       cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem3);
       if (e != cudaSuccess) return e;
-      k<<<grid3, kT3Threads, smem3, s>>>(m, p.t.phase32, p.F, p.L, p.Nu, p.Mu, NP, 1.f / p.x_scale, Y,
+      k<<<grid3, kT3Threads, smem3, s>>>(m, p.t.phase32, p.F, p.L, p.Nu, p.Mu, NP, nb, 1.f / p.x_scale, Y,
                                          p.t.status);
       return cudaGetLastError();
     }
