@@ -365,23 +365,36 @@ __global__ void __launch_bounds__(kGatherThreads, MINB)
     float2 sacc[ROWS];
 #pragma unroll
     for (int r = 0; r < ROWS; ++r) sacc[r] = make_float2(0.f, 0.f);
+    // two rows per packed (f32x2) instruction: the scalar form's IEEE
+    // operations in the same order, at half the issue slots
+    const float2 magic2 = make_float2(kFloorMagic, kFloorMagic);
+    const float2 nmagic2 = make_float2(-kFloorMagic, -kFloorMagic);
+    const float2 neg1 = make_float2(-1.f, -1.f);
 #pragma unroll 2
     for (int j = 0; j < ns; ++j) {
       const float2 ab = s_ab[buf][j];
       const WarpChan wc = s_wc[buf][warp][j];
       const float base = fmaf(ab.x, dl, wc.phi);
       const unsigned offl = wc.off + kl16;
+      const float2 b2 = make_float2(ab.y, ab.y), base2 = make_float2(base, base);
 #pragma unroll
-      for (int r = 0; r < ROWS; ++r) {
-        const float s = fmaf(ab.y, (float)(r - ROWS / 2), base) + fo[r];
-        const float t = __fadd_rd(s, kFloorMagic);
-        const float f = s - (t - kFloorMagic);
-        const unsigned addr = offl + ((unsigned)__float_as_int(t) << 4);
-        float4 e = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (KK_IN_BOUNDS(g_bounds_das, (unsigned)((int)(addr >> 4) - j * win) < (unsigned)win))
-          e = *reinterpret_cast<const float4 *>(swb + addr);
-        sacc[r].x += fmaf(f, e.z, e.x);
-        sacc[r].y += fmaf(f, e.w, e.y);
+      for (int r = 0; r < ROWS; r += 2) {
+        const float2 s = __fadd2_rn(
+            __ffma2_rn(b2, make_float2((float)(r - ROWS / 2), (float)(r + 1 - ROWS / 2)), base2),
+            make_float2(fo[r], fo[r + 1]));
+        const float2 t = __fadd2_rd(s, magic2);                        // floor in the mantissa
+        const float2 f = __ffma2_rn(__fadd2_rn(t, nmagic2), neg1, s);  // s - floor(s)
+        const unsigned addr0 = offl + ((unsigned)__float_as_int(t.x) << 4);
+        const unsigned addr1 = offl + ((unsigned)__float_as_int(t.y) << 4);
+        float4 e0 = make_float4(0.f, 0.f, 0.f, 0.f), e1 = e0;
+        if (KK_IN_BOUNDS(g_bounds_das, (unsigned)((int)(addr0 >> 4) - j * win) < (unsigned)win))
+          e0 = *reinterpret_cast<const float4 *>(swb + addr0);
+        if (KK_IN_BOUNDS(g_bounds_das, (unsigned)((int)(addr1 >> 4) - j * win) < (unsigned)win))
+          e1 = *reinterpret_cast<const float4 *>(swb + addr1);
+        sacc[r] = __fadd2_rn(sacc[r], __ffma2_rn(make_float2(f.x, f.x), make_float2(e0.z, e0.w),
+                                                 make_float2(e0.x, e0.y)));
+        sacc[r + 1] = __fadd2_rn(sacc[r + 1], __ffma2_rn(make_float2(f.y, f.y), make_float2(e1.z, e1.w),
+                                                         make_float2(e1.x, e1.y)));
       }
     }
     if (two_f > 0.f) {
