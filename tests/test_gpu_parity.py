@@ -38,6 +38,28 @@ def test_stage_spectrum_matches_oracle():
     assert kc.rel_l2(kc.cplx(X), ref) <= 2e-6
 
 
+@pytest.mark.parametrize("which", ["large_int16", "f32_odd_channels"])
+def test_stage_spectrum_1024_bins_matches_oracle(which, request):
+    """T = 2048 (F = 1024 bins, a 16 x 16 x 4 transform): every channel of the
+    75 x 128 int16 frame, and a float32 record set whose channel count
+    (5 x 37) is not a multiple of the records a CTA takes at a time."""
+    import torch
+    if which == "large_int16":
+        w = request.getfixturevalue("large")
+    else:
+        grid = (40, 36, -3e-3, 0.15e-3, 4e-3, 0.15e-3)
+        w = kksynth.workload_custom("spec1024", 77, 37, 0.3e-3, 5, 10.0, 2048, grid,
+                                    kksynth.point_phantom([(0.0, 5.0), (1.5, 20.0)]), snr_db=25.0)
+    ops, (rx, pairs, grp, J) = kc.scheme_both("same", w.tx_angles, 3)
+    plan = kc.kk_plan_for(w, rx, pairs, grp, J)
+    F = w.n_samples // 2
+    X = torch.empty((F, plan.info.n_tx_used, w.n_elem, 2), device="cuda:0")
+    plan.spectrum(kc.to_dev(w.rf), X)
+    torch.cuda.synchronize()
+    ref = np.transpose(kk.analytic_spectrum(w.rf), (2, 0, 1))       # [F][N][L]
+    assert kc.rel_l2(kc.cplx(X), ref) <= 2e-6
+
+
 def test_stage_shear_matches_oracle():
     """Feed the oracle's spectra (rounded to FP32) and compare Y per bin."""
     import torch
