@@ -44,6 +44,8 @@ def _args():
     ap.add_argument("--batch-frames", type=int, default=256)
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-refiner measurement")
     ap.add_argument("--oracle-timing", default=None, help=argparse.SUPPRESS)
+    ap.add_argument("--record", default=None, metavar="PATH",
+                    help="also append a one-line JSON run record (run_record) to PATH")
     ap.add_argument("--profile", default=None,
                     choices=["kk_image", "decompose", "decompose_bf16", "decompose_f8e4m3", "das", "vernier",
                              "refiner_step", "volume_contraction", "few_tx_contraction", "batch_gather",
@@ -857,6 +859,8 @@ def run_ours(args):
             out["cpu_baseline"] = cpu_baseline(w, plans)
     if rank == 0:
         print(json.dumps(out), flush=True)
+        if args.record:
+            append_record(args.record, run_record(out))
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
@@ -1054,7 +1058,24 @@ def cpu_baseline(w, plans=None):
     matrix["threads_all_cores"] = cores
     out["matrix"] = matrix
     if plans:
-        rel = {}
+        import kksynth
+        nx, nz, x0, dx, z0, dz = w.grid
+        hw = int(round(0.5e-3 / dx))
+        wires = [(int(round((x * 1e-3 - x0) / dx)), int(round((z * 1e-3 - z0) / dz)))
+                 for x, z in kksynth.LARGE_WIRES_MM]
+
+        def peaks(img):
+            a = np.abs(img)
+            res = []
+            for cx, cz in wires:
+                xa, xb, za, zb = max(cx - hw, 0), min(cx + hw + 1, nx), max(cz - hw, 0), min(cz + hw + 1, nz)
+                sub = a[za:zb, xa:xb]
+                iz, ix = np.unravel_index(int(np.argmax(sub)), sub.shape)
+                res.append((za + iz, xa + ix))
+            return res
+
+        ref_peaks = peaks(B_ref[0])
+        rel, exact = {}, {}
         for name, p in plans.items():
             try:
                 ws, rt, B, I = p.empty_workspace(), p.empty_rf_theta(), p.empty_image(), p.empty_intensity()
@@ -1062,10 +1083,13 @@ def cpu_baseline(w, plans=None):
                 p.beamform(rt, B, I, ws)
                 torch.cuda.synchronize()
                 g = B[0].cpu().numpy().astype(np.float64)
-                rel[name] = kk.rel_l2(g[..., 0] + 1j * g[..., 1], B_ref[0])
+                gi = g[..., 0] + 1j * g[..., 1]
+                rel[name] = kk.rel_l2(gi, B_ref[0])
+                exact[name] = sum(a == b for a, b in zip(peaks(gi), ref_peaks))
             except Exception as e:  # pragma: no cover - report, do not hide
                 rel[name] = f"error: {e}"
         out["gpu_rel_l2_vs_oracle_whole_image"] = rel
+        out["gpu_wire_peaks_at_oracle_pixel"] = {"wires": len(wires), "window_px": 2 * hw + 1, "exact": exact}
     if LEARNED_PROBE:
         out["learned_network_vs_oracle"] = _learned_vs_oracle(**LEARNED_PROBE)
     return out
@@ -1093,6 +1117,46 @@ def _learned_vs_oracle(theta, x, s, out, C=32):
     rel = float(np.linalg.norm(out - ro) / np.linalg.norm(ro))
     return {"rel_l2": rel, "bound": 1e-2, "within_bound": rel <= 1e-2,
             "what": "one held-out 256 x 256 input, trained weights, FP64 oracle network (oracle.nn)"}
+
+
+def run_record(out, argv=None, seed=2000):
+    """One JSONL record of a run: when, how it was invoked, the workload, seed
+    and chosen form, each GPU form's rel-L2 against the FP64 oracle (when the
+    CPU baseline ran) and where each form puts the wire peaks against the
+    oracle's image, throughput, roofline
+    fractions, clocks and the host core count.  Keys a run did not measure
+    are null."""
+    import datetime
+    bd = out.get("breakdown", {}) or {}
+    cpu = out.get("cpu_baseline", {}) or {}
+    roof = out.get("roofline", {}) or {}
+    forms = bd.get("forms", {}) or {}
+    rec = {
+        "time_utc": datetime.datetime.now(datetime.timezone.utc).strftime("%Y-%m-%dT%H:%M:%SZ"),
+        "argv": list(sys.argv[1:] if argv is None else argv),
+        "impl": out.get("impl", "ours"),
+        "workload": (out.get("config") or {}).get("workload"),
+        "seed": seed,
+        "form": (out.get("config") or {}).get("form"),
+        "metric": out.get("metric"), "value": out.get("value"), "unit": out.get("unit"),
+        "ms_per_step": out.get("ms_per_step"), "n_gpus": out.get("n_gpus"),
+        "e2e": (out.get("e2e") or {}).get("value"),
+        "gpixel_pairs_per_s": bd.get("gpixel_pairs_per_s"),
+        "frames_per_s_by_form": {k: v.get("frames_per_s") for k, v in forms.items()} or None,
+        "rel_l2_vs_oracle": cpu.get("gpu_rel_l2_vs_oracle_whole_image"),
+        "wire_peaks_at_oracle_pixel": cpu.get("gpu_wire_peaks_at_oracle_pixel"),
+        "roofline": {"kernel": roof.get("kernel"), "bound": roof.get("bound"), "frac": roof.get("frac")}
+        if roof else None,
+        "clocks": out.get("clocks"),
+        "host_cores": cpu.get("cores", os.cpu_count()),
+        "cpu_baseline_value": cpu.get("value"),
+    }
+    return rec
+
+
+def append_record(path, rec):
+    with open(path, "a") as f:
+        f.write(json.dumps(rec) + "\n")
 
 
 def run_reference(args):
@@ -1124,6 +1188,8 @@ def run_reference(args):
            "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0,
                    "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
+    if args.record:
+        append_record(args.record, run_record(out))
 
 
 if __name__ == "__main__":

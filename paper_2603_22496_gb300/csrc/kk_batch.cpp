@@ -313,6 +313,7 @@ kk_status kk_batch_create(kk_batch **out, const kk_batch_frame *frames, int32_t 
 }
 
 kk_status kk_batch_run(kk_batch *b, void *stream) {
+  NvtxRange range("kk_batch_run");
   if (!b || !b->exec) { set_error("null batch"); return KK_ERR_INVALID_ARG; }
   DeviceGuard guard(b->device);
   cudaError_t e = cudaGraphLaunch(b->exec, (cudaStream_t)stream);

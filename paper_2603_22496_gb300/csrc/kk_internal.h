@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include <string>
@@ -126,6 +127,16 @@ struct kk_plan {
 };
 
 namespace kk {
+
+// NVTX range over a host scope: the stages a call enqueues show up by name in
+// a profiler's timeline (nvtx3 is header-only; with no tool attached a push
+// or pop is one test of a function pointer).
+struct NvtxRange {
+  explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange &) = delete;
+  NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 // Bounds-checked build: KK_IN_BOUNDS(counter, ok) counts a failed index check
 // in the translation unit's device counter and yields ok (the caller skips

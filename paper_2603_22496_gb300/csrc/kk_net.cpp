@@ -415,6 +415,7 @@ kk_status kk_net_forward(kk_net *n, int32_t nb, const void *d_in, const float *d
     return KK_ERR_INVALID_ARG;
   }
   kk::DeviceGuard g(n->device);
+  kk::NvtxRange range("kk_net_forward");
   const cudaStream_t s = (cudaStream_t)stream;
   if ((st = forward(*n, nb, d_in, d_in_scale, s)) != KK_OK) return st;
   KK_TRY(kk::nn::residual_mse(n->x, kInChannels, n->head, kHeadChannels, nullptr, nullptr, nb, n->H * n->W,
@@ -433,6 +434,7 @@ kk_status kk_net_loss_grad(kk_net *n, int32_t nb, const void *d_in, const float 
     return KK_ERR_INVALID_ARG;
   }
   kk::DeviceGuard g(n->device);
+  kk::NvtxRange range("kk_net_loss_grad");
   const cudaStream_t s = (cudaStream_t)stream;
   if ((st = forward(*n, nb, d_in, d_in_scale, s)) != KK_OK) return st;
   const int hw = n->H * n->W;
@@ -440,6 +442,7 @@ kk_status kk_net_loss_grad(kk_net *n, int32_t nb, const void *d_in, const float 
                               d_target_scale, nb, hw, (float2 *)d_out, n->dhead, n->loss_part, s), "loss");
   KK_TRY(kk::nn::sum_scalar(n->loss_part, kk::nn::residual_blocks(nb, hw), 1.f / (2.f * (float)nb * (float)hw),
                             d_loss, s), "loss sum");
+  kk::NvtxRange rb("kk_net_loss_grad/backward");
   if ((st = backward(*n, nb, s)) != KK_OK) return st;
   if (d_grad)
     KK_TRY(cudaMemcpyAsync(d_grad, n->g, n->n_params * sizeof(float), cudaMemcpyDeviceToDevice, s), "grad copy");

@@ -43,6 +43,7 @@ using namespace kk;
 
 extern "C" kk_status kk_beamform_noalloc(const kk_plan *p, const void *d_rf_theta, void *d_B,
                                          float *d_I, void *stream) {
+  NvtxRange range("kk_beamform_noalloc");
   kk_status st = check_beamform_args(p, d_rf_theta, d_B, d_I);
   if (st != KK_OK) return st;
   const size_t need = (p->bf_split > 1)

@@ -745,12 +745,21 @@ bool aligned(const void *ptr, size_t a) { return ((uintptr_t)ptr % a) == 0; }
 }  // namespace
 
 kk_status enqueue_decompose(const kk_plan *p, const void *rf, void *rf_theta, void *ws, cudaStream_t s) {
+  NvtxRange range("kk_decompose");
   void *X = at<unsigned char>(ws, p->ws_X);
   float2 *Y = at<float2>(ws, p->ws_Y);
-  cudaError_t e = launch_spectrum(*p, rf, X, p->Nu, p->t.tx_used, s);
+  cudaError_t e;
+  {
+    NvtxRange r("kk_decompose/spectrum");
+    e = launch_spectrum(*p, rf, X, p->Nu, p->t.tx_used, s);
+  }
   if (e != cudaSuccess) return cuda_fail(e, "spectrum launch");
-  e = launch_shear(*p, X, Y, s);
+  {
+    NvtxRange r("kk_decompose/contraction");
+    e = launch_shear(*p, X, Y, s);
+  }
   if (e != cudaSuccess) return cuda_fail(e, "shear launch");
+  NvtxRange r("kk_decompose/inverse");
   e = launch_inverse(*p, Y, p->Nu * p->Mu, p->pair_q_identity ? nullptr : p->t.pair_q, p->P, (float2 *)rf_theta, s,
                      p->t.pair_w);
   if (e != cudaSuccess) return cuda_fail(e, "inverse launch");
@@ -772,6 +781,7 @@ kk_status check_beamform_args(const kk_plan *p, const void *rf_theta, const void
 }
 
 kk_status enqueue_beamform(const kk_plan *p, const void *rf_theta, void *B, float *I, void *ws, cudaStream_t s) {
+  NvtxRange range("kk_beamform");
   float2 *part = (p->bf_split > 1) ? at<float2>(ws, p->ws_part) : nullptr;
   cudaError_t e = launch_kk_gather(*p, (const float2 *)rf_theta, (float2 *)B, I, part, s);
   if (e != cudaSuccess) return cuda_fail(e, "kk gather launch");
@@ -781,13 +791,18 @@ kk_status enqueue_beamform(const kk_plan *p, const void *rf_theta, void *B, floa
 namespace {
 
 kk_status enqueue_das(const kk_plan *p, const void *rf, void *B, float *I, void *ws, cudaStream_t s) {
+  NvtxRange range("das_beamform");
   float2 *X = at<float2>(ws, p->ws_X);
   float2 *y = at<float2>(ws, p->ws_Y);
-  cudaError_t e = launch_spectrum(*p, rf, X, p->N, p->t.tx_used, s);
-  if (e != cudaSuccess) return cuda_fail(e, "spectrum launch");
-  e = launch_inverse(*p, X, p->N * p->L, nullptr, p->N * p->L, y, s);
-  if (e != cudaSuccess) return cuda_fail(e, "inverse launch");
+  cudaError_t e;
+  {
+    NvtxRange r("das_beamform/analytic");
+    e = launch_spectrum(*p, rf, X, p->N, p->t.tx_used, s);
+    if (e == cudaSuccess) e = launch_inverse(*p, X, p->N * p->L, nullptr, p->N * p->L, y, s);
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "analytic signal launch");
   float2 *part = (p->bf_split > 1) ? at<float2>(ws, p->ws_part) : nullptr;
+  NvtxRange r("das_beamform/gather");
   e = launch_das_gather(*p, y, (float2 *)B, I, part, s);
   if (e != cudaSuccess) return cuda_fail(e, "das gather launch");
   return KK_OK;

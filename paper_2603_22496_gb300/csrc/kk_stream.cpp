@@ -141,6 +141,7 @@ cudaError_t add_copy(kk_stream *s, unsigned char *dst, const void *src, cudaMemc
 
 // Enqueues the decomposition of group g (just completed) on s_dec.
 kk_status run_group(kk_stream *s, int g) {
+  NvtxRange range("kk_stream/decompose_group");
   const int b = (int)(s->group_seq % s->R);
   Group &gr = s->groups[g];
   cudaError_t e = flush_copy(s);
@@ -389,6 +390,7 @@ kk_status kk_stream_push_many(kk_stream *s, int32_t first_row, int32_t n_rows, c
 }
 
 kk_status kk_stream_end_frame(kk_stream *s, void *d_B, float *d_I) {
+  NvtxRange range("kk_stream_end_frame");
   if (!s) {
     set_error("kk_stream_end_frame: null stream");
     return KK_ERR_INVALID_ARG;
