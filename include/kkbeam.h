@@ -188,7 +188,11 @@ typedef struct kk_plan_info {
 kk_status kk_plan_create(kk_plan **out, const kk_plan_desc *d);
 
 /* DAS plan (Eq. (DAS)): receive/pair/group/precision fields are ignored,
- * every transmit of rf is used, J = 1. */
+ * every transmit of rf is used, J = 1.  A volumetric description (2D array,
+ * tilted transmits, ny y slices) gives the volumetric sum over elements at
+ * (elem_x, elem_y) and voxels (x, y, z), full aperture only (f_number > 0:
+ * KK_ERR_UNSUPPORTED), and pixel pitches fine enough for 256-sample staged
+ * windows (otherwise KK_ERR_UNSUPPORTED). */
 kk_status das_plan_create(kk_plan **out, const kk_plan_desc *d);
 
 /* Frees the plan's device tables.  NULL is a no-op.  The caller must make
@@ -312,6 +316,9 @@ kk_status kk_beamform_noalloc(const kk_plan *p, const void *d_rf_theta, void *d_
  * mask and inverse as step 1, no shear), then
  *   B(ix, iz) = sum_{i,l} lerp(y_il, fs (tau_in + |r - (u_l, 0)| / c))
  * d_rf [N][L][T], d_B [nz][nx] cfloat, d_I [nz][nx] float (|B|^2) or NULL.
+ * Volumetric plans: tau_in = (x sx_i + y sy_i + z sz_i) / c with the unit
+ * direction of transmit tilts (ax_i, ay_i), the receive distance to element
+ * (u_l, v_l, 0), and d_B [ny][nz][nx], d_I [ny][nz][nx].
  */
 kk_status das_beamform(const kk_plan *p, const void *d_rf, void *d_B,
                        float *d_I, void *d_workspace, void *stream);

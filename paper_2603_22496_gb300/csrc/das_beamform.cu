@@ -218,17 +218,30 @@ __global__ void __launch_bounds__(kGatherThreads)
   }
 }
 
+// Per-slice terms of the volumetric (2D-array) form: the transmit delay's
+// step per y slice (32.32 samples per slice, per transmit), the slices' y
+// and the elements' y (fs / c units, as (hi, lo)), and the xz tiles per slice.
+struct DasVolArgs {
+  const long long *dY;
+  const float2 *ys, *us_y;
+  int ny, tiles_xz;
+};
+
 // Staged-window DAS gather for windows of at most 256 entries (see above).
 // Entries E[k] = (y[k], y[k+1] - y[k]) (zero outside [0, T-2]): one 16-byte
-// load and two FMAs per pixel-pair.
-template <int STAGE, int NPT, int MINB>
+// load and two FMAs per pixel-pair.  VOL: 2D array over a volume; the block
+// index also runs over y slices, each tile lies in one slice (an [nz][nx]
+// plane of the [ny][nz][nx] image), the transmit delay gains dY * slice and
+// the receive distance the squared y offset of slice and element.
+template <int STAGE, int NPT, int MINB, bool VOL = false>
 __global__ void __launch_bounds__(kGatherThreads, MINB)
     k_das_gather_staged(const float2 *__restrict__ y, int N, int L, int T, const long long *__restrict__ dA,
                         const long long *__restrict__ dB, const long long *__restrict__ dC,
                         const float *__restrict__ dAf, const float *__restrict__ dBf,
                         const float2 *__restrict__ xs, const float2 *__restrict__ zs,
                         const float2 *__restrict__ us, int nx, int nz, int tiles_x, int win, int split,
-                        float two_f, int window, float2 *__restrict__ B, float *__restrict__ I) {
+                        float two_f, int window, float2 *__restrict__ B, float *__restrict__ I,
+                        const DasVolArgs va) {
   constexpr int ROWS = 4, TZ = 16;
   constexpr int PPW = STAGE / 4;   // channels staged by each warp
   constexpr int QPP = NPT / PPW;   // entries per lane per staged channel
@@ -241,7 +254,16 @@ __global__ void __launch_bounds__(kGatherThreads, MINB)
 
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
-  const int tile = blockIdx.x;
+  int tile = blockIdx.x;
+  [[maybe_unused]] int slice = 0;
+  size_t plane = (size_t)nx * nz;  // one image (all slices) per pair slice of the split
+  if constexpr (VOL) {
+    slice = tile / va.tiles_xz;
+    tile -= slice * va.tiles_xz;
+    plane *= (size_t)va.ny;
+    B += (size_t)slice * nx * nz;
+    if (I != nullptr) I += (size_t)slice * nx * nz;
+  }
   const int ix0 = (tile % tiles_x) * kTileX;
   const int iz0 = (tile / tiles_x) * TZ;
   const int ix = ix0 + lane;
@@ -253,6 +275,8 @@ __global__ void __launch_bounds__(kGatherThreads, MINB)
   for (int r = 0; r < ROWS; ++r) z2[r] = df_sqr(__ldg(zs + izb + r));
   const float xlo = __ldg(xs + ix0).x, xhi = __ldg(xs + ix0 + kTileX - 1).x;
   const float zlo = __ldg(zs + iz0).x;
+  [[maybe_unused]] float2 ysl = make_float2(0.f, 0.f);  // this slice's y (fs / c units)
+  if constexpr (VOL) ysl = __ldg(va.ys + slice);
 
   float2 acc[ROWS];
 #pragma unroll
@@ -270,9 +294,15 @@ __global__ void __launch_bounds__(kGatherThreads, MINB)
     if (lane < ns_) {                                                                                 \
       const float2 u_ = __ldg(us + l_);                                                               \
       const float xc_ = fminf(fmaxf(u_.x, xlo), xhi) - u_.x;                                          \
-      const int kmin_ = (int)floorf(sqrtf(fmaf(xc_, xc_, zlo * zlo)));                                \
+      float r2_ = fmaf(xc_, xc_, zlo * zlo);                                                          \
+      if constexpr (VOL) {                                                                            \
+        const float yc_ = ysl.x - __ldg(va.us_y + l_).x;                                              \
+        r2_ = fmaf(yc_, yc_, r2_);                                                                    \
+      }                                                                                               \
+      const int kmin_ = (int)floorf(sqrtf(r2_));                                                      \
       const int i_ = ps_ + lane;                                                                      \
-      const long long A_ = __ldg(dA + i_), Bq_ = __ldg(dB + i_), Cq_ = __ldg(dC + i_);                \
+      const long long A_ = __ldg(dA + i_), Bq_ = __ldg(dB + i_);                                      \
+      const long long Cq_ = __ldg(dC + i_) + (VOL ? __ldg(va.dY + i_) * (long long)slice : 0LL);      \
       const long long smin_ = Cq_ + Bq_ * (long long)iz0 + A_ * (long long)(A_ >= 0 ? ix0 : ix0 + kTileX - 1); \
       const int w0_ = (int)(smin_ >> 32) + kmin_ - 2;                                                 \
       const long long sref_ = Cq_ + Bq_ * (long long)(iz0 + warp * ROWS + ROWS / 2) + A_ * (long long)(ix0 + 16); \
@@ -348,7 +378,8 @@ __global__ void __launch_bounds__(kGatherThreads, MINB)
       // exact, fraction from the double-float root)
       cur_l = l;
       const float2 u = __ldg(us + l);
-      const float2 dx2 = df_sqr(df_sub(xq, u));
+      float2 dx2 = df_sqr(df_sub(xq, u));
+      if constexpr (VOL) dx2 = df_add(dx2, df_sqr(df_sub(ysl, __ldg(va.us_y + l))));
       int kl = 0;
 #pragma unroll
       for (int r = 0; r < ROWS; ++r) {
@@ -417,7 +448,7 @@ __global__ void __launch_bounds__(kGatherThreads, MINB)
   }
 #undef DAS_TABLES
 #undef DAS_LOAD_RAW
-  float2 *dst = B + (size_t)sidx * nx * nz;
+  float2 *dst = B + (size_t)sidx * plane;
 #pragma unroll
   for (int r = 0; r < ROWS; ++r) {
     const int iz = izb + r;
@@ -450,13 +481,15 @@ template <int STAGE, int NPT>
 cudaError_t launch_staged(const kk_plan &p, const float2 *y, float2 *dst, float *I, cudaStream_t s) {
   constexpr int MINB = 7;
   const size_t smem = sizeof(float4) * (size_t)STAGE * p.bf_win;
-  auto k = k_das_gather_staged<STAGE, NPT, MINB>;
+  // volumetric plans: the slice terms cost registers, one CTA per SM fewer
+  auto k = p.vol ? k_das_gather_staged<STAGE, NPT, MINB - 1, true> : k_das_gather_staged<STAGE, NPT, MINB, false>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  const dim3 grid(p.tiles_x * p.tiles_z, p.bf_split);
+  DasVolArgs va{p.t.das_Y, p.t.ys, p.t.us_y, p.ny, p.tiles_x * p.tiles_z};
+  const dim3 grid(p.tiles_x * p.tiles_z * p.ny, p.bf_split);
   k<<<grid, kGatherThreads, smem, s>>>(y, p.N, p.L, p.T, p.t.das_A, p.t.das_B, p.t.das_C, p.t.das_Af,
                                        p.t.das_Bf, p.t.xs, p.t.zs, p.t.us, p.grid.nx, p.grid.nz, p.tiles_x,
-                                       p.bf_win, p.bf_split, p.das_two_f, p.das_window, dst, I);
+                                       p.bf_win, p.bf_split, p.das_two_f, p.das_window, dst, I, va);
   return cudaGetLastError();
 }
 }  // namespace
@@ -495,6 +528,7 @@ cudaError_t launch_das_gather(const kk_plan &p, const float2 *y, float2 *B, floa
       default: return cudaErrorInvalidValue;
     }
   } else {
+    if (p.vol) return cudaErrorInvalidConfiguration;  // the plan refuses such volumes
     const size_t smem = sizeof(float4) * (size_t)p.bf_stage * p.bf_win;
     cudaFuncSetAttribute(k_das_gather, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     const dim3 grid(p.tiles_x * p.tiles_z, p.bf_split);
@@ -505,7 +539,7 @@ cudaError_t launch_das_gather(const kk_plan &p, const float2 *y, float2 *B, floa
     e = cudaGetLastError();
   }
   if (e != cudaSuccess || p.bf_split == 1) return e;
-  const int npix = p.grid.nx * p.grid.nz;
+  const int npix = p.grid.nx * p.grid.nz * p.ny;
   k_das_reduce<<<(npix + 255) / 256, 256, 0, s>>>(partial, p.bf_split, npix, B, I);
   return cudaGetLastError();
 }

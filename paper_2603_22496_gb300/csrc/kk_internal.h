@@ -69,6 +69,11 @@ struct DevTables {
   float2 *xs = nullptr;                // [nx] x fs / c as (hi, lo)
   float2 *zs = nullptr;                // [nz] z fs / c as (hi, lo)
   float2 *us = nullptr;                // [L]  u fs / c as (hi, lo)
+  // volumetric DAS: transmit delay step per y slice (32.32), slice y and
+  // element y (fs / c, as (hi, lo))
+  long long *das_Y = nullptr;          // [N]
+  float2 *ys = nullptr;                // [ny]
+  float2 *us_y = nullptr;              // [L]
   int *status = nullptr;               // device status word (KK_OK or KK_ERR_TIMEOUT)
 };
 

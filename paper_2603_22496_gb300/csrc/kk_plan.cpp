@@ -591,13 +591,13 @@ kk_status make_kk(kk_plan &p, const kk_plan_desc *d) {
 }
 
 kk_status make_das(kk_plan &p, const kk_plan_desc *d) {
-  if (p.vol) {
-    set_error("volumetric DAS is not implemented (the volumetric path is KK only)");
-    return KK_ERR_UNSUPPORTED;
-  }
   if (!std::isfinite(d->f_number) || (d->aperture != KK_APERTURE_BOXCAR && d->aperture != KK_APERTURE_HANN)) {
     set_error("bad receive aperture (finite f_number, KK_APERTURE_BOXCAR or KK_APERTURE_HANN)");
     return KK_ERR_INVALID_ARG;
+  }
+  if (p.vol && d->f_number > 0) {
+    set_error("volumetric DAS sums the full aperture (f_number 0)");
+    return KK_ERR_UNSUPPORTED;
   }
   p.das_two_f = d->f_number > 0 ? (float)(2.0 * d->f_number) : 0.f;
   p.das_window = d->aperture;
@@ -617,17 +617,20 @@ kk_status make_das(kk_plan &p, const kk_plan_desc *d) {
   const size_t off_txu = blob.add(txu);
   const kk_grid &g = p.grid;
   const double k_s = d->fs / d->c;
-  std::vector<long long> A(p.N), Bv(p.N), C(p.N);
+  std::vector<long long> A(p.N), Bv(p.N), C(p.N), Yv(p.vol ? p.N : 0);
   std::vector<float> Af(p.N), Bf(p.N);
   // staged kernel: 32 x 16 tiles, window from the transmit-delay span plus the
-  // receive-delay span, which the tile diameter bounds (|grad R| <= 1);
-  // windows over 256 entries go to the synchronous 32 x 32 kernel
+  // receive-delay span, which the tile diameter bounds (|grad R| <= 1, also
+  // within one y slice of a volume); windows over 256 entries go to the
+  // synchronous 32 x 32 kernel (linear arrays only)
   const double diam16 = std::hypot(g.dx * (kTileX - 1), g.dz * 15.0);
   double span_in16 = 0, span_in32 = 0;
   for (int i = 0; i < p.N; ++i) {
-    const double th = d->tx_angles[i];
-    const double a = k_s * g.dx * std::sin(th), b = k_s * g.dz * std::cos(th);
-    const double c0 = k_s * (g.x0 * std::sin(th) + g.z0 * std::cos(th));
+    double sx, sy, sz;
+    direction(p.vol, d->tx_angles[i], d->tx_angles_y ? d->tx_angles_y[i] : 0.0, sx, sy, sz);
+    const double a = k_s * g.dx * sx, b = k_s * g.dz * sz;
+    const double c0 = k_s * (g.x0 * sx + p.y0 * sy + g.z0 * sz);
+    if (p.vol) Yv[i] = to_fixed32(k_s * p.dy * sy);
     A[i] = to_fixed32(a);
     Bv[i] = to_fixed32(b);
     C[i] = to_fixed32(c0);
@@ -638,6 +641,10 @@ kk_status make_das(kk_plan &p, const kk_plan_desc *d) {
   }
   const int win16 = (int)std::ceil(span_in16 + k_s * diam16) + 6;
   const int stage16 = das_staged_stage(win16);
+  if (p.vol && stage16 == 0) {
+    set_error("volumetric DAS needs staged windows of at most 256 samples (a finer x / z pitch)");
+    return KK_ERR_UNSUPPORTED;
+  }
   const int TZ = stage16 > 0 ? 16 : kTileZ;
   p.tiles_x = (g.nx + kTileX - 1) / kTileX;
   p.tiles_z = (g.nz + TZ - 1) / TZ;
@@ -649,9 +656,14 @@ kk_status make_das(kk_plan &p, const kk_plan_desc *d) {
   for (size_t k = 0; k < xs.size(); ++k) xs[k] = split_df(k_s * (g.x0 + g.dx * (double)k));
   for (size_t k = 0; k < zs.size(); ++k) zs[k] = split_df(k_s * (g.z0 + g.dz * (double)k));
   for (int l = 0; l < p.L; ++l) us[l] = split_df(k_s * d->elem_x[l]);
+  std::vector<float2> ysl(p.vol ? p.ny : 0), usy(p.vol ? p.L : 0);
+  for (int k = 0; k < (int)ysl.size(); ++k) ysl[k] = split_df(k_s * (p.y0 + p.dy * (double)k));
+  for (int l = 0; l < (int)usy.size(); ++l) usy[l] = split_df(k_s * (d->elem_y ? d->elem_y[l] : 0.0));
   const size_t off_A = blob.add(A), off_B = blob.add(Bv), off_C = blob.add(C);
   const size_t off_Af = blob.add(Af), off_Bf = blob.add(Bf);
   const size_t off_xs = blob.add(xs), off_zs = blob.add(zs), off_us = blob.add(us);
+  const size_t off_Y = p.vol ? blob.add(Yv) : 0, off_ys = p.vol ? blob.add(ysl) : 0;
+  const size_t off_usy = p.vol ? blob.add(usy) : 0;
   if (stage16 > 0) {
     p.bf_rows = 4;
     p.bf_win = win16;
@@ -665,7 +677,7 @@ kk_status make_das(kk_plan &p, const kk_plan_desc *d) {
   // split the element loop so the grid covers the GPU (~4 CTAs per SM)
   int sms = 148;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p.device);
-  const int tiles = p.tiles_x * p.tiles_z;
+  const int tiles = p.tiles_x * p.tiles_z * p.ny;
   p.bf_split = std::max(1, std::min((4 * sms + tiles - 1) / tiles, p.L / 4));
   // workspace: X [F][N*L], analytic channels y [N*L][T], partial images
   size_t off = 0;
@@ -674,7 +686,7 @@ kk_status make_das(kk_plan &p, const kk_plan_desc *d) {
   p.ws_Y = off;
   off = align_up(off + sizeof(float2) * (size_t)p.N * p.L * p.T);
   p.ws_part = off;
-  if (p.bf_split > 1) off = align_up(off + sizeof(float2) * (size_t)p.bf_split * g.nx * g.nz);
+  if (p.bf_split > 1) off = align_up(off + sizeof(float2) * (size_t)p.bf_split * g.nx * g.nz * p.ny);
   p.ws_total = off;
   kk_status st = upload(p, blob);
   if (st != KK_OK) return st;
@@ -690,6 +702,11 @@ kk_status make_das(kk_plan &p, const kk_plan_desc *d) {
   p.t.xs = at<float2>(b, off_xs);
   p.t.zs = at<float2>(b, off_zs);
   p.t.us = at<float2>(b, off_us);
+  if (p.vol) {
+    p.t.das_Y = at<long long>(b, off_Y);
+    p.t.ys = at<float2>(b, off_ys);
+    p.t.us_y = at<float2>(b, off_usy);
+  }
   p.t.status = at<int>(b, p.status_off);
   return KK_OK;
 }

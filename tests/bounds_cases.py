@@ -99,6 +99,15 @@ def main() -> int:
     check("kk_volume_4x3_9x3x11", kc.cplx(B3),
           V.kk_beamform3(y3, wv.elem_x, wv.elem_y, ps, wv.grid, wv.grid_y, fs, c))
 
+    # volumetric DAS on the same volume (slice terms in the staged DAS gather)
+    dp = kb.Plan(wv.elem_x, wv.tx_ax, wv.grid, wv.c, wv.fs, wv.n_samples, kb.KK_RF_F32, das=True,
+                 elem_y=wv.elem_y, tx_angles_y=wv.tx_ay, grid_y=wv.grid_y)
+    dws, dB = dp.empty_workspace(), dp.empty_image()
+    dp.das(kc.to_dev(wv.rf), dB, None, dws)
+    torch.cuda.synchronize()
+    check("das_volume_4x3_9x3x11", kc.cplx(dB)[0],
+          V.das_volume(wv.rf, wv.tx_ax, wv.tx_ay, wv.elem_x, wv.elem_y, wv.grid, wv.grid_y, fs, c))
+
     # batched form: two uneven frames through the persistent gather
     frames, refs = [], []
     for seed, (M, gg) in enumerate([(5, (33, 20, -4e-3, 0.15e-3, 5e-3, 0.15e-3)),

@@ -190,10 +190,6 @@ def test_volume_streaming_equals_whole_frame(small):
 def test_volume_rejections(small):
     import torch
     w = small
-    with pytest.raises(kb.KKError) as e:       # volumetric DAS is not implemented
-        kb.Plan(w.elem_x, w.tx_ax, w.grid, w.c, w.fs, w.n_samples, kb.KK_RF_F32, das=True, elem_y=w.elem_y,
-                tx_angles_y=w.tx_ay, grid_y=w.grid_y)
-    assert e.value.status == kb.KK_ERR_UNSUPPORTED
     ps = V.product_set(w.tx_ax, w.tx_ay, [_rx_product(12.0, 3)])
     pairs = np.stack([ps.tx_index, ps.rx_index], 1).astype(np.int32)
     bad = [dict(rx_angles_y=np.full(ps.rx_ay.shape, np.deg2rad(75.0))),        # tilts do not propagate
@@ -213,3 +209,66 @@ def test_volume_rejections(small):
         kb.Batch(fr, shape=404)
     assert e.value.status == kb.KK_ERR_UNSUPPORTED
     torch.cuda.synchronize()
+
+
+# --------------------------------------------------------------------------
+# volumetric DAS (Eq. (DAS) with a 2D array): the staged DAS gather with the
+# per-slice transmit term and the elements' y offsets
+# --------------------------------------------------------------------------
+def _das_plan(w, f_number=0.0, grid=None):
+    return kb.Plan(w.elem_x, w.tx_ax, grid or w.grid, w.c, w.fs, w.n_samples, kc.rf_dtype_of(w), das=True,
+                   elem_y=w.elem_y, tx_angles_y=w.tx_ay, grid_y=w.grid_y, f_number=f_number)
+
+
+def test_volume_das_matches_oracle(small):
+    import torch
+    w = small
+    plan = _das_plan(w)
+    info = plan.info
+    assert info.is_das == 1 and info.is_volume == 1 and info.ny == 48
+    assert info.launches_beamform == 4           # analytic signal (2), gather, slice reduce
+    ws, B, I = plan.empty_workspace(), plan.empty_image(), plan.empty_intensity()
+    assert B.shape == (1, 48, 64, 48, 2)
+    plan.das(kc.to_dev(w.rf), B, I, ws)
+    torch.cuda.synchronize()
+    assert plan.status() == 0
+    ref = V.das_volume(w.rf, w.tx_ax, w.tx_ay, w.elem_x, w.elem_y, w.grid, w.grid_y, FS, C)
+    got = kc.cplx(B)[0]
+    assert kc.rel_l2(got, ref) <= TOL
+    assert kc.rel_l2(I.cpu().numpy().astype(np.float64), np.abs(ref) ** 2) <= 2 * TOL
+    # each point target's peak sits on the oracle's voxel, within a voxel of
+    # the target
+    nx, nz, x0, dx, z0, dz = w.grid
+    ny, y0, dy = w.grid_y
+    for px, py, pz in w.points[:w.n_points, :3]:
+        ix, iy, iz = (int(round((px - x0) / dx)), int(round((py - y0) / dy)), int(round((pz - z0) / dz)))
+        win = np.s_[iy - 3:iy + 4, iz - 3:iz + 4, ix - 3:ix + 4]
+        pg = np.unravel_index(int(np.argmax(np.abs(got[win]))), (7, 7, 7))
+        pr = np.unravel_index(int(np.argmax(np.abs(ref[win]))), (7, 7, 7))
+        assert pg == pr and max(abs(int(v) - 3) for v in pg) <= 1, (pg, pr)
+
+
+def test_volume_das_ragged_and_int16():
+    """A ragged volume (nx, nz off the tile grid, odd ny) from int16 RF with a
+    3 x 4 array: more pair slices than tiles per SM, so the slice reduce runs."""
+    import torch
+    w = kksynth.volume_workload(seed=3100, lx=3, ly=4, nx=37, ny=5, nz=23, n_samples=512, speckle=60,
+                                rf_dtype="i16", snr_db=30.0,
+                                points=((0.0, 0.0, 7e-3), (1e-3, -0.3e-3, 8e-3)))
+    plan = _das_plan(w)
+    ws, B = plan.empty_workspace(), plan.empty_image()
+    plan.das(kc.to_dev(w.rf), B, None, ws)
+    torch.cuda.synchronize()
+    ref = V.das_volume(w.rf, w.tx_ax, w.tx_ay, w.elem_x, w.elem_y, w.grid, w.grid_y, FS, C)
+    assert kc.rel_l2(kc.cplx(B)[0], ref) <= TOL
+
+
+def test_volume_das_refusals(small):
+    w = small
+    with pytest.raises(kb.KKError) as e:
+        _das_plan(w, f_number=1.5)
+    assert e.value.status == kb.KK_ERR_UNSUPPORTED
+    nx, nz, x0, dx, z0, dz = w.grid
+    with pytest.raises(kb.KKError) as e:               # 1 mm voxels: windows beyond 256 samples
+        _das_plan(w, grid=(nx, nz, x0, 1e-3, z0, 1e-3))
+    assert e.value.status == kb.KK_ERR_UNSUPPORTED
