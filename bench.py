@@ -536,7 +536,8 @@ def _volume(kb, flush, n_sm, peaks, peak_src, reps=10):
     voxel grid at 0.15 mm from 5 mm depth.  FP32 decomposition (1024
     elements: beyond the tensor-core forms), volumes/s and voxel-pairs/s of
     the image formation against the same shared-memory gather roofline as
-    the 2D frame."""
+    the 2D frame; then volumetric DAS of the same volume (25 x 1024
+    channels per voxel)."""
     w, plan = _volume_plan(kb)
     info = plan.info
     import torch
@@ -570,7 +571,22 @@ def _volume(kb, flush, n_sm, peaks, peak_src, reps=10):
            "kk_image_ms": round(ms_bf, 4), "gvoxel_pairs_per_s": round(ach, 1),
            "gather_frac_of_8pp_per_clk_sm": round(ach / peak_pp, 4),
            "compression": round(info.compression_factor, 2), "status": plan.status()}
-    del plan, d_rf, ws, rt, B, I, X, Y
+    del plan, ws, rt, B, I, X, Y
+    torch.cuda.empty_cache()
+    # volumetric DAS of the same volume: every (transmit, element) channel
+    dplan = kb.Plan(w.elem_x, w.tx_ax, w.grid, w.c, w.fs, w.n_samples, kb.KK_RF_I16, das=True,
+                    elem_y=w.elem_y, tx_angles_y=w.tx_ay, grid_y=w.grid_y)
+    dws, dB, dI = dplan.empty_workspace(), dplan.empty_image(), dplan.empty_intensity()
+    dplan.das(d_rf, dB, dI, dws)
+    torch.cuda.synchronize()
+    ms_das = _time_loop(lambda: dplan.das(d_rf, dB, dI, dws), 3, flush)
+    dvp = float(dplan.info.n_tx) * dplan.info.n_elem * info.nx * info.nz * info.ny
+    dach = dvp / (ms_das / 1e3) / 1e9
+    res["das"] = {"channels": int(dplan.info.n_tx * dplan.info.n_elem), "ms": round(ms_das, 3),
+                  "volumes_per_s": round(1e3 / ms_das, 2), "gvoxel_pairs_per_s": round(dach, 1),
+                  "whole_step_frac_of_8pp_per_clk_sm": round(dach / peak_pp, 4),
+                  "kk_speedup": round(ms_das / (ms_dec + ms_bf), 2), "status": dplan.status()}
+    del dplan, dws, dB, dI, d_rf
     return res
 
 
