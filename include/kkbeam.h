@@ -338,8 +338,11 @@ kk_status das_beamform(const kk_plan *p, const void *d_rf, void *d_B,
  * {2, 4, 8}, stage in {4, 8, 16}) sets it.  Results match the per-frame calls
  * up to FP32 summation order.  The buffers given here are baked into the
  * graph: refill them in place between runs.  Each frame needs its own
- * workspace (frames run concurrently).  Volumetric plans are not accepted
- * (KK_ERR_UNSUPPORTED).
+ * workspace (frames run concurrently).  Volumetric plans may be mixed in:
+ * their (frame, tile) items, tiles running over every y slice, form a
+ * second list with its own persistent launch and launch shape (timed the
+ * same way with shape = 0; a set shape applies to both lists), after the
+ * linear-array frames' launch.
  *
  * kk_batch_run enqueues the graph on `stream`.  A batch must not run twice
  * concurrently (it owns one work counter).
@@ -357,9 +360,12 @@ typedef struct kk_batch_frame {
 
 typedef struct kk_batch_info {
   int32_t n_frames, n_items, rows, stage, max_window, grid, graph_nodes, n_tuned;
-  double pixel_pairs;      /* sum over frames of pairs x pixels */
+  double pixel_pairs;      /* sum over frames of pairs x pixels (x y slices) */
   int32_t tuned_shape[16]; /* shapes timed by the autotuner (rows * 100 + stage) */
   float tuned_ms[16];      /* their image-formation times */
+  /* the volumetric frames' list (all 0 without volumetric frames); the
+   * fields above describe the linear-array frames' list */
+  int32_t n_volume_frames, n_items_volume, rows_volume, stage_volume, max_window_volume;
 } kk_batch_info;
 
 kk_status kk_batch_create(kk_batch **out, const kk_batch_frame *frames, int32_t n_frames,

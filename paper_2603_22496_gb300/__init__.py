@@ -107,7 +107,9 @@ class kk_batch_info(ctypes.Structure):
                 ("stage", ctypes.c_int32), ("max_window", ctypes.c_int32), ("grid", ctypes.c_int32),
                 ("graph_nodes", ctypes.c_int32), ("n_tuned", ctypes.c_int32),
                 ("pixel_pairs", ctypes.c_double), ("tuned_shape", ctypes.c_int32 * 16),
-                ("tuned_ms", ctypes.c_float * 16)]
+                ("tuned_ms", ctypes.c_float * 16), ("n_volume_frames", ctypes.c_int32),
+                ("n_items_volume", ctypes.c_int32), ("rows_volume", ctypes.c_int32),
+                ("stage_volume", ctypes.c_int32), ("max_window_volume", ctypes.c_int32)]
 
 
 class kk_net_desc(ctypes.Structure):

@@ -8,6 +8,8 @@
 // (frame, tile) work items of all frames, largest frames first.  The launch
 // shape of that gather (tile rows, pairs per stage) is picked by timing the
 // feasible shapes on the batch itself (the autotuner) or set by the caller.
+// Volumetric frames form a second work list (tiles over every y slice) with
+// its own persistent launch, counter and launch shape, after the first.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -26,16 +28,30 @@ size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
 }  // namespace
 
+// One persistent launch's work: the (frame, tile) items of the linear-array
+// frames (vol = false) or of the volumetric ones, and its launch shape.
+struct BatchList {
+  bool vol = false;
+  int2 *d_items = nullptr;
+  int *d_counter = nullptr;
+  size_t cap = 0;
+  int n_frames = 0, n_items = 0, max_win = 0, rows = 4, stage = 16;
+  float tuned_ms[16] = {};
+  int tuned_cfg[16] = {};
+  int n_tuned = 0;
+};
+
 struct kk_batch {
   int device = 0;
   std::vector<kk_batch_frame> frames;
-  // device block: GatherArgs[n] | int2 items[] | int counter
+  // device block: GatherArgs[n] | GatherVolArgs[n] | per list: int2 items[], int counter
   void *dev = nullptr;
   kk::GatherArgs *d_args = nullptr;
-  int2 *d_items = nullptr;
-  int *d_counter = nullptr;
-  size_t items_cap = 0;
-  int n_items = 0, max_win = 0, rows = 4, stage = 16, grid = 0;
+  kk::GatherVolArgs *d_vols = nullptr;
+  std::vector<kk::GatherArgs> h_args;   // host copies, both lists' frames
+  std::vector<kk::GatherVolArgs> h_vols;
+  BatchList lists[2];                   // linear-array frames, volumetric frames
+  int grid = 0;
   double pixel_pairs = 0;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -43,9 +59,6 @@ struct kk_batch {
   cudaStream_t main_stream = nullptr;  // private: capture and autotuning
   cudaStream_t streams[kCaptureStreams] = {};
   cudaEvent_t fork = nullptr, join[kCaptureStreams] = {};
-  float tuned_ms[16] = {};
-  int tuned_cfg[16] = {};
-  int n_tuned = 0;
 };
 
 namespace kk {
@@ -60,16 +73,15 @@ int frame_window(const kk_plan &p, int rows) {
   return (int)std::ceil(span) + 4;
 }
 
-// Frame descriptors and work items of a launch shape; false if a frame's
-// window does not fit the shape.
-bool build_items(kk_batch &b, int rows, int stage, std::vector<GatherArgs> &args,
-                 std::vector<int2> &items, int &max_win) {
-  args.clear();
+// Frame descriptors (into the host copies) and work items of a launch shape
+// for one list; false if a frame's window does not fit the shape.
+bool build_items(kk_batch &b, BatchList &L, int rows, int stage, std::vector<int2> &items, int &max_win) {
   items.clear();
   max_win = 0;
   std::vector<std::pair<double, int>> order;
   for (size_t f = 0; f < b.frames.size(); ++f) {
     const kk_plan &p = *b.frames[f].plan;
+    if (p.vol != L.vol) continue;
     const int win = frame_window(p, rows);
     if (!gather_config_supported(rows, stage, win)) return false;
     max_win = std::max(max_win, win);
@@ -78,7 +90,12 @@ bool build_items(kk_batch &b, int rows, int stage, std::vector<GatherArgs> &args
     a.win = win;
     a.split = 1;
     a.tiles_x = (p.grid.nx + kTileX - 1) / kTileX;
-    args.push_back(a);
+    b.h_args[f] = a;
+    if (L.vol) {
+      GatherVolArgs v = gather_vol_args(p);
+      v.tiles_xz = a.tiles_x * ((p.grid.nz + 4 * rows - 1) / (4 * rows));
+      b.h_vols[f] = v;
+    }
     order.push_back({(double)p.P, (int)f});
   }
   if (!gather_config_supported(rows, stage, max_win)) return false;
@@ -86,47 +103,48 @@ bool build_items(kk_batch &b, int rows, int stage, std::vector<GatherArgs> &args
   std::stable_sort(order.begin(), order.end(), [](auto &x, auto &y) { return x.first > y.first; });
   for (auto &o : order) {
     const kk_plan &p = *b.frames[o.second].plan;
-    const int tiles = args[o.second].tiles_x * ((p.grid.nz + 4 * rows - 1) / (4 * rows));
+    const int tiles = b.h_args[o.second].tiles_x * ((p.grid.nz + 4 * rows - 1) / (4 * rows)) * (L.vol ? p.ny : 1);
     for (int t = 0; t < tiles; ++t) items.push_back(make_int2(o.second, t));
   }
   return true;
 }
 
-kk_status upload_items(kk_batch &b, const std::vector<GatherArgs> &args, const std::vector<int2> &items,
-                       cudaStream_t s) {
-  cudaError_t e = cudaMemcpyAsync(b.d_args, args.data(), sizeof(GatherArgs) * args.size(),
+kk_status upload_items(kk_batch &b, BatchList &L, const std::vector<int2> &items, cudaStream_t s) {
+  cudaError_t e = cudaMemcpyAsync(b.d_args, b.h_args.data(), sizeof(GatherArgs) * b.h_args.size(),
                                   cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(b.d_items, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice, s);
+    e = cudaMemcpyAsync(b.d_vols, b.h_vols.data(), sizeof(GatherVolArgs) * b.h_vols.size(),
+                        cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && !items.empty())
+    e = cudaMemcpyAsync(L.d_items, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   return e == cudaSuccess ? KK_OK : cuda_fail(e, "batch descriptor upload");
 }
 
-kk_status enqueue_gather(kk_batch &b, cudaStream_t s) {
-  cudaError_t e = cudaMemsetAsync(b.d_counter, 0, sizeof(int), s);
+kk_status enqueue_gather(kk_batch &b, const BatchList &L, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(L.d_counter, 0, sizeof(int), s);
   if (e == cudaSuccess)
-    e = launch_kk_gather_batch(b.rows, b.stage, b.d_args, b.d_items, b.n_items, b.d_counter, b.max_win,
-                               b.grid, s);
+    e = launch_kk_gather_batch(L.rows, L.stage, b.d_args, L.vol ? b.d_vols : nullptr, L.d_items, L.n_items,
+                               L.d_counter, L.max_win, b.grid, s);
   return e == cudaSuccess ? KK_OK : cuda_fail(e, "batched gather launch");
 }
 
-kk_status select_shape(kk_batch &b, int rows, int stage, cudaStream_t s) {
-  std::vector<GatherArgs> args;
+kk_status select_shape(kk_batch &b, BatchList &L, int rows, int stage, cudaStream_t s) {
   std::vector<int2> items;
   int max_win = 0;
-  if (!build_items(b, rows, stage, args, items, max_win)) {
-    set_error("launch shape does not fit the batch's windows");
+  if (!build_items(b, L, rows, stage, items, max_win)) {
+    set_error(std::string("launch shape does not fit the batch's ") + (L.vol ? "volumetric " : "") + "windows");
     return KK_ERR_UNSUPPORTED;
   }
-  if (items.size() > b.items_cap) {
+  if (items.size() > L.cap) {
     set_error("work list larger than allocated");
     return KK_ERR_INVALID_ARG;
   }
-  b.rows = rows;
-  b.stage = stage;
-  b.max_win = max_win;
-  b.n_items = (int)items.size();
-  return upload_items(b, args, items, s);
+  L.rows = rows;
+  L.stage = stage;
+  L.max_win = max_win;
+  L.n_items = (int)items.size();
+  return upload_items(b, L, items, s);
 }
 
 kk_status capture_graph(kk_batch &b, cudaStream_t s) {
@@ -147,7 +165,8 @@ kk_status capture_graph(kk_batch &b, cudaStream_t s) {
     e = cudaEventRecord(b.join[k], b.streams[k]);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(s, b.join[k], 0);
   }
-  if (e == cudaSuccess && st == KK_OK) st = enqueue_gather(b, s);
+  for (const BatchList &L : b.lists)
+    if (e == cudaSuccess && st == KK_OK && L.n_items > 0) st = enqueue_gather(b, L, s);
   cudaGraph_t g = nullptr;
   cudaError_t e2 = cudaStreamEndCapture(s, &g);
   if (st != KK_OK) {
@@ -168,22 +187,23 @@ kk_status capture_graph(kk_batch &b, cudaStream_t s) {
   return KK_OK;
 }
 
-// Time the batched gather alone for every feasible shape; keep the fastest.
-kk_status autotune(kk_batch &b, cudaStream_t s) {
+// Time one list's batched gather alone for every feasible shape; keep the
+// fastest.
+kk_status autotune(kk_batch &b, BatchList &L, cudaStream_t s) {
   static const int cands[][2] = {{4, 16}, {4, 8}, {8, 8}, {8, 4}, {2, 16}, {4, 4}, {2, 8}};
   cudaEvent_t t0, t1;
   cudaEventCreate(&t0);
   cudaEventCreate(&t1);
   float best = 1e30f;
   int best_i = -1;
-  b.n_tuned = 0;
+  L.n_tuned = 0;
   for (int c = 0; c < (int)(sizeof(cands) / sizeof(cands[0])); ++c) {
-    if (select_shape(b, cands[c][0], cands[c][1], s) != KK_OK) continue;
+    if (select_shape(b, L, cands[c][0], cands[c][1], s) != KK_OK) continue;
     float ms = 0;
     bool ok = true;
     for (int rep = 0; rep < 3 && ok; ++rep) {  // first launch warms up
       cudaEventRecord(t0, s);
-      ok = enqueue_gather(b, s) == KK_OK;
+      ok = enqueue_gather(b, L, s) == KK_OK;
       cudaEventRecord(t1, s);
       if (cudaEventSynchronize(t1) != cudaSuccess) ok = false;
       float m = 0;
@@ -192,9 +212,9 @@ kk_status autotune(kk_batch &b, cudaStream_t s) {
     }
     if (!ok) continue;
     ms /= 2;
-    b.tuned_ms[b.n_tuned] = ms;
-    b.tuned_cfg[b.n_tuned] = cands[c][0] * 100 + cands[c][1];
-    ++b.n_tuned;
+    L.tuned_ms[L.n_tuned] = ms;
+    L.tuned_cfg[L.n_tuned] = cands[c][0] * 100 + cands[c][1];
+    ++L.n_tuned;
     if (ms < best) {
       best = ms;
       best_i = c;
@@ -204,10 +224,10 @@ kk_status autotune(kk_batch &b, cudaStream_t s) {
   cudaEventDestroy(t1);
   cudaGetLastError();
   if (best_i < 0) {
-    set_error("no launch shape fits this batch");
+    set_error(std::string("no launch shape fits this batch's ") + (L.vol ? "volumetric " : "") + "frames");
     return KK_ERR_UNSUPPORTED;
   }
-  return select_shape(b, cands[best_i][0], cands[best_i][1], s);
+  return select_shape(b, L, cands[best_i][0], cands[best_i][1], s);
 }
 
 void destroy(kk_batch *b) {
@@ -240,7 +260,6 @@ kk_status kk_batch_create(kk_batch **out, const kk_batch_frame *frames, int32_t 
   for (int f = 0; f < n_frames; ++f) {
     const kk_batch_frame &fr = frames[f];
     if (!fr.plan || fr.plan->is_das) { set_error("every frame needs a KK plan"); return KK_ERR_INVALID_ARG; }
-    if (fr.plan->vol) { set_error("volumetric plans are not supported in the batched form"); return KK_ERR_UNSUPPORTED; }
     if (fr.plan->device != device) { set_error("all plans must live on one device"); return KK_ERR_INVALID_ARG; }
     if (!fr.d_rf || !fr.d_rf_theta || !fr.d_B || !fr.d_workspace) { set_error("null frame buffer"); return KK_ERR_INVALID_ARG; }
     if (fr.plan->compound != KK_COMPOUND_NONE && !fr.d_I) { set_error("compound mode set but I is null"); return KK_ERR_INVALID_ARG; }
@@ -259,16 +278,22 @@ kk_status kk_batch_create(kk_batch **out, const kk_batch_frame *frames, int32_t 
   if (!b) { set_error("host allocation failed"); return KK_ERR_OOM; }
   b->device = device;
   b->frames.assign(frames, frames + n_frames);
+  b->h_args.assign(n_frames, GatherArgs{});
+  b->h_vols.assign(n_frames, GatherVolArgs{});
+  b->lists[1].vol = true;
   cudaStream_t s = (cudaStream_t)stream;
-  // work list capacity: the most tiles any shape produces (rows = 2)
-  size_t cap = 0;
+  // work list capacities: the most tiles any shape produces (rows = 2)
   for (int f = 0; f < n_frames; ++f) {
     const kk_plan &p = *frames[f].plan;
-    cap += (size_t)((p.grid.nx + kTileX - 1) / kTileX) * ((p.grid.nz + 7) / 8);
-    b->pixel_pairs += (double)p.P * p.grid.nx * p.grid.nz;
+    BatchList &L = b->lists[p.vol ? 1 : 0];
+    L.cap += (size_t)((p.grid.nx + kTileX - 1) / kTileX) * ((p.grid.nz + 7) / 8) * p.ny;
+    ++L.n_frames;
+    b->pixel_pairs += (double)p.P * p.grid.nx * p.grid.nz * p.ny;
   }
-  b->items_cap = cap;
-  const size_t bytes = align_up(sizeof(GatherArgs) * n_frames) + align_up(sizeof(int2) * cap) + kAlign;
+  const size_t o_vols = align_up(sizeof(GatherArgs) * n_frames);
+  const size_t o_list0 = o_vols + align_up(sizeof(GatherVolArgs) * n_frames);
+  const size_t o_list1 = o_list0 + align_up(sizeof(int2) * b->lists[0].cap) + kAlign;
+  const size_t bytes = o_list1 + align_up(sizeof(int2) * b->lists[1].cap) + kAlign;
   cudaError_t e = cudaMalloc(&b->dev, bytes);
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -278,8 +303,11 @@ kk_status kk_batch_create(kk_batch **out, const kk_batch_frame *frames, int32_t 
   }
   unsigned char *base = (unsigned char *)b->dev;
   b->d_args = (GatherArgs *)base;
-  b->d_items = (int2 *)(base + align_up(sizeof(GatherArgs) * n_frames));
-  b->d_counter = (int *)(base + align_up(sizeof(GatherArgs) * n_frames) + align_up(sizeof(int2) * cap));
+  b->d_vols = (GatherVolArgs *)(base + o_vols);
+  b->lists[0].d_items = (int2 *)(base + o_list0);
+  b->lists[0].d_counter = (int *)(base + o_list0 + align_up(sizeof(int2) * b->lists[0].cap));
+  b->lists[1].d_items = (int2 *)(base + o_list1);
+  b->lists[1].d_counter = (int *)(base + o_list1 + align_up(sizeof(int2) * b->lists[1].cap));
   int sms = 148;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
   b->grid = 8 * sms;  // persistent: up to 8 resident CTAs per SM
@@ -298,7 +326,10 @@ kk_status kk_batch_create(kk_batch **out, const kk_batch_frame *frames, int32_t 
     return st;
   }
   cudaStream_t ms = b->main_stream;
-  kk_status st = (shape == 0) ? autotune(*b, ms) : select_shape(*b, shape / 100, shape % 100, ms);
+  kk_status st = KK_OK;
+  for (BatchList &L : b->lists)
+    if (st == KK_OK && L.n_frames > 0)
+      st = (shape == 0) ? autotune(*b, L, ms) : select_shape(*b, L, shape / 100, shape % 100, ms);
   if (st == KK_OK) st = capture_graph(*b, ms);
   if (st == KK_OK) {
     e = cudaStreamSynchronize(ms);
@@ -323,19 +354,25 @@ kk_status kk_batch_run(kk_batch *b, void *stream) {
 kk_status kk_batch_get_info(const kk_batch *b, kk_batch_info *info) {
   if (!b || !info) { set_error("null argument"); return KK_ERR_INVALID_ARG; }
   std::memset(info, 0, sizeof(*info));
+  const BatchList &L = b->lists[0], &V = b->lists[1];
   info->n_frames = (int32_t)b->frames.size();
-  info->n_items = b->n_items;
-  info->rows = b->rows;
-  info->stage = b->stage;
-  info->max_window = b->max_win;
+  info->n_items = L.n_items;
+  info->rows = L.n_frames ? L.rows : 0;
+  info->stage = L.n_frames ? L.stage : 0;
+  info->max_window = L.max_win;
   info->grid = b->grid;
   info->graph_nodes = (int32_t)b->graph_nodes;
   info->pixel_pairs = b->pixel_pairs;
-  info->n_tuned = b->n_tuned;
-  for (int i = 0; i < b->n_tuned && i < 16; ++i) {
-    info->tuned_shape[i] = b->tuned_cfg[i];
-    info->tuned_ms[i] = b->tuned_ms[i];
+  info->n_tuned = L.n_tuned;
+  for (int i = 0; i < L.n_tuned && i < 16; ++i) {
+    info->tuned_shape[i] = L.tuned_cfg[i];
+    info->tuned_ms[i] = L.tuned_ms[i];
   }
+  info->n_volume_frames = V.n_frames;
+  info->n_items_volume = V.n_items;
+  info->rows_volume = V.n_frames ? V.rows : 0;
+  info->stage_volume = V.n_frames ? V.stage : 0;
+  info->max_window_volume = V.max_win;
   return KK_OK;
 }
 

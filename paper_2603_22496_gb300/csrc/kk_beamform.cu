@@ -390,6 +390,28 @@ __global__ void __launch_bounds__(kGatherThreads, MINB)
   }
 }
 
+// Batched form, volumetric frames: the same persistent loop over (frame,
+// tile) items, tiles running over every y slice of the frame.
+template <int ROWS, int STAGE, int NPT, int MINB>
+__global__ void __launch_bounds__(kGatherThreads, MINB)
+    k_kk_gather_batch_vol(const GatherArgs *__restrict__ frames, const GatherVolArgs *__restrict__ vols,
+                          const int2 *__restrict__ items, int n_items, int *__restrict__ counter) {
+  extern __shared__ float4 sw[];
+  __shared__ GatherSmem<STAGE, true> sm;
+  __shared__ int s_item;
+  for (;;) {
+    __syncthreads();  // previous item fully done with shared memory
+    if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
+    __syncthreads();
+    const int it = s_item;
+    if (it >= n_items) break;
+    const int2 w = items[it];
+    const GatherArgs a = frames[w.x];
+    const GatherVolArgs v = vols[w.x];
+    gather_tile<ROWS, STAGE, NPT, true, true>(a, w.y, 0, sw, sm, &v);
+  }
+}
+
 // Sum the pair-slice partials in slice order and compound.
 __global__ void k_kk_reduce(const float2 *__restrict__ part, int split, int J, int npix,
                             float2 *__restrict__ B, float *__restrict__ I, int compound) {
@@ -489,10 +511,18 @@ GatherVolArgs gather_vol_args(const kk_plan &p) {
 }
 
 template <int ROWS, int STAGE, int NPT>
-static cudaError_t batch_cfg(const GatherArgs *frames, const int2 *items, int n_items, int *counter,
-                             int max_win, int grid, cudaStream_t s) {
-  auto k = k_kk_gather_batch<ROWS, STAGE, NPT, (ROWS <= 4 ? 7 : 5)>;
+static cudaError_t batch_cfg(const GatherArgs *frames, const GatherVolArgs *vols, const int2 *items,
+                             int n_items, int *counter, int max_win, int grid, cudaStream_t s) {
   const size_t smem = sizeof(float4) * (size_t)STAGE * max_win;
+  if (vols != nullptr) {
+    // the slice term costs registers: one CTA per SM fewer, as for one volume
+    auto k = k_kk_gather_batch_vol<ROWS, STAGE, NPT, (ROWS <= 4 ? 6 : 4)>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k<<<grid, kGatherThreads, smem, s>>>(frames, vols, items, n_items, counter);
+    return cudaGetLastError();
+  }
+  auto k = k_kk_gather_batch<ROWS, STAGE, NPT, (ROWS <= 4 ? 7 : 5)>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   k<<<grid, kGatherThreads, smem, s>>>(frames, items, n_items, counter);
@@ -500,38 +530,38 @@ static cudaError_t batch_cfg(const GatherArgs *frames, const int2 *items, int n_
 }
 
 template <int ROWS, int STAGE>
-static cudaError_t batch_rs(const GatherArgs *frames, const int2 *items, int n_items, int *counter,
-                            int max_win, int grid, cudaStream_t s) {
+static cudaError_t batch_rs(const GatherArgs *frames, const GatherVolArgs *vols, const int2 *items, int n_items,
+                            int *counter, int max_win, int grid, cudaStream_t s) {
   constexpr int PPW = STAGE / 4;
   const int q = gather_entries_per_lane(max_win);
   if constexpr (PPW * 1 <= kMaxStagedEntries) {
-    if (q == 1) return batch_cfg<ROWS, STAGE, PPW>(frames, items, n_items, counter, max_win, grid, s);
+    if (q == 1) return batch_cfg<ROWS, STAGE, PPW>(frames, vols, items, n_items, counter, max_win, grid, s);
   }
   if constexpr (PPW * 2 <= kMaxStagedEntries) {
-    if (q == 2) return batch_cfg<ROWS, STAGE, PPW * 2>(frames, items, n_items, counter, max_win, grid, s);
+    if (q == 2) return batch_cfg<ROWS, STAGE, PPW * 2>(frames, vols, items, n_items, counter, max_win, grid, s);
   }
   if constexpr (PPW * 4 <= kMaxStagedEntries) {
-    if (q <= 4) return batch_cfg<ROWS, STAGE, PPW * 4>(frames, items, n_items, counter, max_win, grid, s);
+    if (q <= 4) return batch_cfg<ROWS, STAGE, PPW * 4>(frames, vols, items, n_items, counter, max_win, grid, s);
   }
   if constexpr (PPW * 8 <= kMaxStagedEntries) {
-    if (q <= 8) return batch_cfg<ROWS, STAGE, PPW * 8>(frames, items, n_items, counter, max_win, grid, s);
+    if (q <= 8) return batch_cfg<ROWS, STAGE, PPW * 8>(frames, vols, items, n_items, counter, max_win, grid, s);
   }
   return cudaErrorInvalidConfiguration;
 }
 
-cudaError_t launch_kk_gather_batch(int rows, int stage, const GatherArgs *frames, const int2 *items,
-                                   int n_items, int *counter, int max_win, int grid,
+cudaError_t launch_kk_gather_batch(int rows, int stage, const GatherArgs *frames, const GatherVolArgs *vols,
+                                   const int2 *items, int n_items, int *counter, int max_win, int grid,
                                    cudaStream_t s) {
   switch (rows * 100 + stage) {
-    case 204: return batch_rs<2, 4>(frames, items, n_items, counter, max_win, grid, s);
-    case 208: return batch_rs<2, 8>(frames, items, n_items, counter, max_win, grid, s);
-    case 216: return batch_rs<2, 16>(frames, items, n_items, counter, max_win, grid, s);
-    case 404: return batch_rs<4, 4>(frames, items, n_items, counter, max_win, grid, s);
-    case 408: return batch_rs<4, 8>(frames, items, n_items, counter, max_win, grid, s);
-    case 416: return batch_rs<4, 16>(frames, items, n_items, counter, max_win, grid, s);
-    case 804: return batch_rs<8, 4>(frames, items, n_items, counter, max_win, grid, s);
-    case 808: return batch_rs<8, 8>(frames, items, n_items, counter, max_win, grid, s);
-    case 816: return batch_rs<8, 16>(frames, items, n_items, counter, max_win, grid, s);
+    case 204: return batch_rs<2, 4>(frames, vols, items, n_items, counter, max_win, grid, s);
+    case 208: return batch_rs<2, 8>(frames, vols, items, n_items, counter, max_win, grid, s);
+    case 216: return batch_rs<2, 16>(frames, vols, items, n_items, counter, max_win, grid, s);
+    case 404: return batch_rs<4, 4>(frames, vols, items, n_items, counter, max_win, grid, s);
+    case 408: return batch_rs<4, 8>(frames, vols, items, n_items, counter, max_win, grid, s);
+    case 416: return batch_rs<4, 16>(frames, vols, items, n_items, counter, max_win, grid, s);
+    case 804: return batch_rs<8, 4>(frames, vols, items, n_items, counter, max_win, grid, s);
+    case 808: return batch_rs<8, 8>(frames, vols, items, n_items, counter, max_win, grid, s);
+    case 816: return batch_rs<8, 16>(frames, vols, items, n_items, counter, max_win, grid, s);
     default: return cudaErrorInvalidConfiguration;
   }
 }

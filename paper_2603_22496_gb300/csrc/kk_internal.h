@@ -239,9 +239,11 @@ cudaError_t launch_kk_gather(const kk_plan &p, const float2 *rf_theta, float2 *B
                              float2 *partial, cudaStream_t s);
 GatherArgs gather_args(const kk_plan &p, const float2 *rf_theta, float2 *dst, float *I);
 GatherVolArgs gather_vol_args(const kk_plan &p);
-// persistent gather over n_items (frame, tile) items; *counter must be 0
-cudaError_t launch_kk_gather_batch(int rows, int stage, const GatherArgs *frames, const int2 *items,
-                                   int n_items, int *counter, int max_win, int grid,
+// persistent gather over n_items (frame, tile) items; *counter must be 0;
+// vols (per frame, indexed like frames) non-null: volumetric frames, whose
+// tiles run over every y slice
+cudaError_t launch_kk_gather_batch(int rows, int stage, const GatherArgs *frames, const GatherVolArgs *vols,
+                                   const int2 *items, int n_items, int *counter, int max_win, int grid,
                                    cudaStream_t s);
 cudaError_t launch_das_gather(const kk_plan &p, const float2 *y, float2 *B, float *I,
                               float2 *partial, cudaStream_t s);

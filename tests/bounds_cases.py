@@ -117,6 +117,10 @@ def main() -> int:
         frames.append({"plan": pl, "rf": kc.to_dev(ws_.rf), "rf_theta": pl.empty_rf_theta(),
                        "B": pl.empty_image(), "I": pl.empty_intensity(), "workspace": pl.empty_workspace()})
         refs.append(kk.kk_image(ws_.rf, ws_.elem_x, opsb, gg, fs, c))
+    # and the 4 x 3-array volume as the batch's volumetric list
+    frames.append({"plan": plan, "rf": kc.to_dev(wv.rf), "rf_theta": plan.empty_rf_theta(),
+                   "B": plan.empty_image(), "I": plan.empty_intensity(), "workspace": plan.empty_workspace()})
+    refs.append(V.kk_beamform3(y3, wv.elem_x, wv.elem_y, ps, wv.grid, wv.grid_y, fs, c))
     batch = kb.Batch(frames, shape=408)
     batch.run()
     torch.cuda.synchronize()

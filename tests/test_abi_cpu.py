@@ -113,6 +113,9 @@ int main(void) {
   P(kk_plan_desc, dy); P(kk_plan_info, ny); P(kk_plan_info, is_volume); P(kk_plan_info, sep_my);
   P(kk_plan_info, gather_rows); P(kk_plan_info, gather_split);
   P(kk_stream_info, n_groups); P(kk_stream_info, events_pushed); P(kk_stream_info, device_bytes);
+  printf("kk_batch_info %zu\\n", sizeof(kk_batch_info));
+  P(kk_batch_info, pixel_pairs); P(kk_batch_info, tuned_ms); P(kk_batch_info, n_volume_frames);
+  P(kk_batch_info, max_window_volume);
   return 0;
 }
 """)
@@ -144,7 +147,12 @@ int main(void) {
             "kk_plan_info.ny": kb.kk_plan_info.ny.offset, "kk_plan_info.is_volume": kb.kk_plan_info.is_volume.offset,
             "kk_plan_info.sep_my": kb.kk_plan_info.sep_my.offset,
             "kk_plan_info.gather_rows": kb.kk_plan_info.gather_rows.offset,
-            "kk_plan_info.gather_split": kb.kk_plan_info.gather_split.offset}
+            "kk_plan_info.gather_split": kb.kk_plan_info.gather_split.offset,
+            "kk_batch_info": ctypes.sizeof(kb.kk_batch_info),
+            "kk_batch_info.pixel_pairs": kb.kk_batch_info.pixel_pairs.offset,
+            "kk_batch_info.tuned_ms": kb.kk_batch_info.tuned_ms.offset,
+            "kk_batch_info.n_volume_frames": kb.kk_batch_info.n_volume_frames.offset,
+            "kk_batch_info.max_window_volume": kb.kk_batch_info.max_window_volume.offset}
     assert {k: int(v) for k, v in got.items()} == want
 
 

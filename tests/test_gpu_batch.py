@@ -88,6 +88,57 @@ def test_batch_matches_per_frame_and_oracle(frames, shape):
         assert kc.rel_l2(Bb, ref) <= 1e-5
 
 
+def _volume_frame(seed, lx, ly, nx, ny, nz, M, i16):
+    """A small matrix-array frame and its volumetric KK plan (M x M receive
+    waves over +-10 deg, coherent)."""
+    from oracle import volume as V
+    w = kksynth.volume_workload(seed=seed, lx=lx, ly=ly, nx=nx, ny=ny, nz=nz, n_samples=1024, speckle=150,
+                                rf_dtype="i16" if i16 else "f32", snr_db=30.0 if i16 else None)
+    rx1 = np.deg2rad(np.linspace(-10.0, 10.0, M))
+    ps = V.product_set(w.tx_ax, w.tx_ay, [(np.tile(rx1, M), np.repeat(rx1, M))])
+    pairs = np.stack([ps.tx_index, ps.rx_index], 1).astype(np.int32)
+    plan = kb.Plan(w.elem_x, w.tx_ax, w.grid, w.c, w.fs, w.n_samples, kc.rf_dtype_of(w), rx_angles=ps.rx_ax,
+                   pairs=pairs, group_of_pair=ps.group.astype(np.int32), n_groups=ps.n_groups,
+                   compound=kb.KK_COMPOUND_COHERENT, elem_y=w.elem_y, tx_angles_y=w.tx_ay, rx_angles_y=ps.rx_ay,
+                   grid_y=w.grid_y)
+    return w, ps, plan
+
+
+@pytest.mark.parametrize("shape", [0, 408])
+def test_batch_with_volumes_matches_per_frame_and_oracle(frames, shape):
+    """Two linear-array frames and two volumes (8 x 8 and 6 x 5 arrays, ragged
+    voxel grids, one int16) in one batch: the volumes form the second list,
+    with its own persistent launch; every frame equals its per-frame path and
+    the oracle."""
+    import torch
+    from oracle import volume as V
+    vols = [_volume_frame(3300, 8, 8, 40, 9, 52, 5, False), _volume_frame(3301, 6, 5, 37, 7, 45, 3, True)]
+    bufs = [_buffers(w, plan) for (w, ops, plan) in frames[:2]] + [_buffers(w, plan) for (w, ps, plan) in vols]
+    batch = kb.Batch(bufs, shape=shape)
+    info = batch.info
+    assert info.n_frames == 4 and info.n_volume_frames == 2
+    assert info.n_items > 0 and info.n_items_volume > 0
+    if shape:
+        assert info.rows_volume * 100 + info.stage_volume == shape
+    assert info.pixel_pairs == sum(float(b["plan"].info.n_pairs) * b["plan"].info.nx * b["plan"].info.nz
+                                   * b["plan"].info.ny for b in bufs)
+    for _ in range(2):
+        batch.run()
+        torch.cuda.synchronize()
+    for b in bufs:
+        plan = b["plan"]
+        assert plan.status() == kb.KK_OK
+        ws, rt, B1, I1 = plan.empty_workspace(), plan.empty_rf_theta(), plan.empty_image(), plan.empty_intensity()
+        plan.decompose(b["rf"], rt, ws)
+        plan.beamform(rt, B1, I1, ws)
+        torch.cuda.synchronize()
+        assert kc.rel_l2(kc.cplx(b["B"]), kc.cplx(B1)) <= 1e-6
+        assert kc.rel_l2(b["I"].cpu().numpy(), I1.cpu().numpy()) <= 2e-6
+    for (w, ps, plan), b in zip(vols, bufs[2:]):
+        ref = V.kk_volume(w.rf, w.elem_x, w.elem_y, ps, w.grid, w.grid_y, FS, C)
+        assert kc.rel_l2(kc.cplx(b["B"]), ref) <= 1e-5
+
+
 def test_batch_rejects_bad_frames(frames):
     w, ops, plan = frames[0]
     b = _buffers(w, plan)
@@ -135,6 +186,9 @@ def test_batch_full_256_uneven_frames_match_per_frame():
     for f in frames:
         plan = f["plan"]
         assert plan.status() == kb.KK_OK
+        # the per-frame path at the batch's launch shape, so that both sum each
+        # stage's pairs in the same order (the stage size sets the two-level sum)
+        plan.set_gather(batch.info.rows, batch.info.stage)
         ws, rt, B1, I1 = plan.empty_workspace(), plan.empty_rf_theta(), plan.empty_image(), plan.empty_intensity()
         plan.decompose(f["rf"], rt, ws)
         plan.beamform(rt, B1, I1, ws)

@@ -20,5 +20,5 @@ def test_bounds_checked_build_odd_shapes():
                        text=True, timeout=900)
     assert r.returncode == 0, (r.stdout[-3000:], r.stderr[-3000:])
     res = json.loads([ln for ln in r.stdout.splitlines() if ln.startswith("{")][-1])
-    assert len(res) >= 13
+    assert len(res) >= 14
     assert all(v["violations"] == 0 and v["rel_l2"] <= 1e-5 for v in res.values()), res

@@ -202,12 +202,6 @@ def test_volume_rejections(small):
             kb.Plan(w.elem_x, w.tx_ax, w.grid, w.c, w.fs, w.n_samples, kb.KK_RF_F32, rx_angles=ps.rx_ax,
                     pairs=pairs, **args)
         assert e.value.status == kb.KK_ERR_INVALID_ARG
-    plan = _plan(w, ps)
-    fr = [{"plan": plan, "rf": kc.to_dev(w.rf), "rf_theta": plan.empty_rf_theta(), "B": plan.empty_image(),
-           "I": plan.empty_intensity(), "workspace": plan.empty_workspace()}]
-    with pytest.raises(kb.KKError) as e:
-        kb.Batch(fr, shape=404)
-    assert e.value.status == kb.KK_ERR_UNSUPPORTED
     torch.cuda.synchronize()
 
 
