@@ -170,6 +170,8 @@ typedef struct kk_plan_info {
    * gather_rows), pairs (transmits, DAS) per stage, and the number of pair
    * (element, DAS) slices whose partial images are summed after the gather */
   int32_t gather_rows, gather_stage, gather_split;
+  int32_t records_trimmed;                 /* kk_plan_set_trim in force */
+  size_t rf_theta_stored_bytes;            /* bytes of rf_theta one decomposition stores */
 } kk_plan_info;
 
 /*
@@ -212,6 +214,20 @@ kk_status kk_plan_get_info(const kk_plan *p, kk_plan_info *info);
  * work is in flight.
  */
 kk_status kk_plan_set_gather(kk_plan *p, int32_t rows, int32_t stage);
+
+/*
+ * Records trimmed to the grid's reach (no counterpart in the paper: a store
+ * choice; images do not change, bit for bit).  With on = 1, kk_decompose,
+ * kk_inverse and streams of the plan store of each record y_p only the
+ * samples that Eq. (KK)'s interpolation can read for some pixel of the grid
+ * under any image-formation launch shape (the per-pair sample range the
+ * plan computes from its delay tables); the rest of rf_theta is left as it
+ * was.  On the 75-transmit x 128-angle frame on a 512 x 512 grid this skips
+ * about 45 % of the record stores.  Linear-array KK plans only (volumetric
+ * plans: KK_ERR_UNSUPPORTED; DAS plans: KK_ERR_INVALID_ARG); on = 0 restores
+ * full records.  Never call it while work is in flight.
+ */
+kk_status kk_plan_set_trim(kk_plan *p, int32_t on);
 
 /*
  * Device status word of the plan's kernels: KK_OK, or KK_ERR_TIMEOUT when a

@@ -33,7 +33,7 @@ _STATUS = {0: "KK_OK", 1: "KK_ERR_INVALID_ARG", 2: "KK_ERR_UNSUPPORTED", 3: "KK_
 
 # every symbol declared in include/kkbeam.h
 EXPORTS = ["kk_plan_create", "das_plan_create", "kk_plan_destroy", "kk_plan_get_info",
-           "kk_plan_set_gather", "kk_plan_status", "kk_plan_check_wait_timeout", "kk_debug_bounds",
+           "kk_plan_set_gather", "kk_plan_set_trim", "kk_plan_status", "kk_plan_check_wait_timeout", "kk_debug_bounds",
            "kk_plan_workspace_size", "kk_decompose", "kk_spectrum", "kk_shear", "kk_inverse",
            "kk_beamform", "kk_beamform_noalloc", "das_beamform", "kk_run_host_scratch_size", "kk_run_host",
            "kk_scheme_angles", "kk_last_error", "kk_version",
@@ -94,7 +94,8 @@ class kk_plan_info(ctypes.Structure):
                 ("ny", ctypes.c_int32), ("is_volume", ctypes.c_int32),
                 ("sep_lx", ctypes.c_int32), ("sep_ly", ctypes.c_int32), ("sep_mx", ctypes.c_int32),
                 ("sep_my", ctypes.c_int32), ("gather_rows", ctypes.c_int32), ("gather_stage", ctypes.c_int32),
-                ("gather_split", ctypes.c_int32)]
+                ("gather_split", ctypes.c_int32), ("records_trimmed", ctypes.c_int32),
+                ("rf_theta_stored_bytes", ctypes.c_size_t)]
 
 
 class kk_batch_frame(ctypes.Structure):
@@ -178,6 +179,7 @@ def load(build_if_missing: bool = False):
         "kk_plan_get_info": ([vp, ctypes.POINTER(kk_plan_info)], st),
         "kk_plan_workspace_size": ([vp, ctypes.POINTER(ctypes.c_size_t)], st),
         "kk_plan_set_gather": ([vp, ctypes.c_int32, ctypes.c_int32], st),
+        "kk_plan_set_trim": ([vp, ctypes.c_int32], st),
         "kk_plan_status": ([vp, ctypes.POINTER(ctypes.c_int32)], st),
         "kk_plan_check_wait_timeout": ([vp, ctypes.c_int64, vp], st),
         "kk_debug_bounds": ([ctypes.POINTER(ctypes.c_int64)], st),
@@ -369,6 +371,10 @@ def kk_plan_set_gather(h, rows: int, stage: int):
     _check(load().kk_plan_set_gather(h, int(rows), int(stage)))
 
 
+def kk_plan_set_trim(h, on: bool):
+    _check(load().kk_plan_set_trim(h, int(on)))
+
+
 
 def kk_plan_status(h) -> int:
     """Device status word (KK_OK or KK_ERR_TIMEOUT); synchronises and resets it."""
@@ -489,6 +495,11 @@ class Plan:
 
     def set_gather(self, rows: int, stage: int):
         kk_plan_set_gather(self.handle, rows, stage)
+        self.info = kk_plan_get_info(self.handle)
+
+    def set_trim(self, on: bool = True):
+        """Store only the record samples the grid's image formation can read."""
+        kk_plan_set_trim(self.handle, on)
         self.info = kk_plan_get_info(self.handle)
 
     def status(self) -> int:

@@ -441,8 +441,10 @@ __global__ void __launch_bounds__(NT, (F == 1024 || F == 2048) ? 2 : 1) k_spectr
 
 // ---- inverse of a half spectrum -------------------------------------------
 // out[row][t], row < nrow, from Y[k][col(row)] (col = identity if null).
+// rng (null: every sample): per output row, the samples [lo, hi) to store;
+// a 16-byte store of samples (2m, 2m + 1) happens when it overlaps them.
 template <int F, int C, int NT>
-__global__ void __launch_bounds__(NT) k_inverse(const float2 *__restrict__ Y, int ncol,
+__global__ void __launch_bounds__(NT) k_inverse(const int2 *__restrict__ rng, const float2 *__restrict__ Y, int ncol,
                                                 const int32_t *__restrict__ col_of_row, int nrow,
                                                 const float2 *__restrict__ tw,
                                                 const float2 *__restrict__ rw,
@@ -485,7 +487,8 @@ __global__ void __launch_bounds__(NT) k_inverse(const float2 *__restrict__ Y, in
     const float sc = row_w ? scale * __ldg(row_w + row) : scale;
     const float4 o = make_float4(ev.x * sc, -ev.y * sc, od.x * sc, -od.y * sc);
     const size_t orow = out_row ? (size_t)__ldg(out_row + row) : (size_t)row;
-    *reinterpret_cast<float4 *>(out + orow * T + 2 * m) = o;
+    const int2 rg = rng ? __ldg(rng + orow) : make_int2(0, T);
+    if (2 * m + 1 >= rg.x && 2 * m < rg.y) *reinterpret_cast<float4 *>(out + orow * T + 2 * m) = o;
   }
 }
 
@@ -525,7 +528,7 @@ __device__ __forceinline__ void first_pass_inverse(const float2 *stg, const floa
 template <int F, int FS, int C, int NT>
 __device__ __forceinline__ void last_pass_inverse(const float2 *buf, const float2 *tw, int r0, int nrow,
                                                   float2 *out, float scale, const float *row_w,
-                                                  const int32_t *out_row, int tid) {
+                                                  const int32_t *out_row, int tid, const int2 *rng) {
   constexpr int LAST = fft_npass(F) - 1;
   constexpr int R = fft_radix(F, LAST);
   constexpr int NS = fft_ns(F, LAST);
@@ -551,12 +554,15 @@ __device__ __forceinline__ void last_pass_inverse(const float2 *buf, const float
     dft<R>(ve);
     dft<R>(vo);
     const float sc = row_w ? scale * __ldg(row_w + row) : scale;
-    float2 *orow = out + (out_row ? (size_t)__ldg(out_row + row) : (size_t)row) * T;
+    const size_t orr = out_row ? (size_t)__ldg(out_row + row) : (size_t)row;
+    float2 *orow = out + orr * T;
+    const int2 rg = rng ? __ldg(rng + orr) : make_int2(0, T);  // samples to store
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       const int m = jj + r * NS;
-      *reinterpret_cast<float4 *>(orow + 2 * m) =
-          make_float4(ve[r].x * sc, -ve[r].y * sc, vo[r].x * sc, -vo[r].y * sc);
+      if (2 * m + 1 >= rg.x && 2 * m < rg.y)
+        *reinterpret_cast<float4 *>(orow + 2 * m) =
+            make_float4(ve[r].x * sc, -ve[r].y * sc, vo[r].x * sc, -vo[r].y * sc);
     }
   }
 }
@@ -576,7 +582,8 @@ __global__ void __launch_bounds__(NT, (F == 1024 || F == 2048) ? 2 : 1) k_invers
                                                     const float2 *__restrict__ rw,
                                                     float2 *__restrict__ out, float scale,
                                                     const float *__restrict__ row_w,
-                                                    const int32_t *__restrict__ out_row, int *status) {
+                                                    const int32_t *__restrict__ out_row, int *status,
+                                                    const int2 *__restrict__ rng) {
   constexpr int FS = fft_row(F);
   constexpr int BK = F < 256 ? F : 256;  // bins per box
   constexpr unsigned kTx = (unsigned)(C * F * sizeof(float2));
@@ -621,7 +628,7 @@ __global__ void __launch_bounds__(NT, (F == 1024 || F == 2048) ? 2 : 1) k_invers
     __syncthreads();  // staging consumed: prefetch the next group while transforming this one
     if (tid == 0 && g + (int)gridDim.x < n_groups) issue(g + gridDim.x);
     run_passes<F, FS, 2 * C, NT, 1, fft_npass(F) - 1>(buf, s_tw, tid);
-    last_pass_inverse<F, FS, C, NT>(buf, s_tw, r0, nrow, out, scale, row_w, out_row, tid);
+    last_pass_inverse<F, FS, C, NT>(buf, s_tw, r0, nrow, out, scale, row_w, out_row, tid, rng);
     __syncthreads();  // transforms stored: the buffers are free for the next group
   }
 }
@@ -701,6 +708,8 @@ static cudaError_t inverse_f(const kk_plan &p, const float2 *Y, int ncol, const 
                              int nrow, float2 *out, cudaStream_t s, const float *row_w,
                              const int32_t *out_row) {
   using Cfg = FftCfg<F>;
+  // KK plans with record trimming store only each record's reachable samples
+  const int2 *rng = (!p.is_das && p.trim) ? p.t.rec_range : nullptr;
   // TMA path: identity column map (col null, or rows reading columns 0..nrow-1
   // in order, flagged by the plan), even ncol, 16-byte aligned Y
   if (col == nullptr && ncol % 2 == 0 && nrow <= ncol && ((uintptr_t)Y % 16) == 0 && p.t.status) {
@@ -717,7 +726,7 @@ static cudaError_t inverse_f(const kk_plan &p, const float2 *Y, int ncol, const 
       const int groups = (nrow + Cfg::CI - 1) / Cfg::CI;
       const int grid = std::max(1, std::min(groups, sms * std::max(per_sm, 1)));
       k<<<grid, Cfg::NT, smem, s>>>(m, nrow, p.t.fft_tw, p.t.rfft_w, out, (float)(1.0 / (double)(2 * F)),
-                                    row_w, out_row, p.t.status);
+                                    row_w, out_row, p.t.status, rng);
       return cudaGetLastError();
     }
   }
@@ -725,7 +734,7 @@ static cudaError_t inverse_f(const kk_plan &p, const float2 *Y, int ncol, const 
   auto k = k_inverse<F, Cfg::CI, Cfg::NT>;
   cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   const dim3 grid((nrow + Cfg::CI - 1) / Cfg::CI);
-  k<<<grid, Cfg::NT, smem, s>>>(Y, ncol, col, nrow, p.t.fft_tw, p.t.rfft_w, out,
+  k<<<grid, Cfg::NT, smem, s>>>(rng, Y, ncol, col, nrow, p.t.fft_tw, p.t.rfft_w, out,
                                 (float)(1.0 / (double)(2 * F)), row_w, out_row);
   return cudaGetLastError();
 }

@@ -63,6 +63,9 @@ struct DevTables {
   float *bf_Af = nullptr, *bf_Bf = nullptr;                    // samples per pixel
   float *pair_w = nullptr;             // [P] pair weights, caller's order (null: all 1)
   int32_t *group_start = nullptr;      // [J+1]
+  // per rf_theta row (caller's pair order): the samples [lo, hi) the gather
+  // can stage under any launch shape (linear-array KK plans)
+  int2 *rec_range = nullptr;
   // DAS
   long long *das_A = nullptr, *das_B = nullptr, *das_C = nullptr; // [N] tau_in 32.32
   float *das_Af = nullptr, *das_Bf = nullptr;                     // [N]
@@ -103,6 +106,8 @@ struct kk_plan {
   int bf_win = 0;      // window entries staged per pair / channel
   int bf_stage = 0;    // pairs (KK) or transmits (DAS) per stage
   int bf_split = 1;    // pair-range splits (KK), partial images reduced after
+  bool trim = false;   // the inverse stores only each record's rec_range
+  size_t trim_bytes = 0;  // bytes the trimmed records store (16-byte sample pairs)
   int tiles_x = 0, tiles_z = 0;
   std::vector<double> h_bfA, h_bfB;  // per-pair delay slopes (samples per pixel)
   // workspace layout (bytes from the workspace base)

@@ -1,6 +1,7 @@
 // kk_plan.cpp -- host side of the C ABI: validation, FP64 plan tables,
 // workspace layout and the enqueue entry points.
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -526,6 +527,41 @@ kk_status make_kk(kk_plan &p, const kk_plan_desc *d) {
     Af[s] = (float)a;
     Bf[s] = (float)b;
   }
+  // Samples of each record the gather can stage, for record trimming.  A
+  // tile's window starts at W0 = floor(min over the tile of s) - 1 (the
+  // 32.32 tables, as the kernels compute it) and the staging reads y[k] and
+  // y[k+1] for k in [W0, W0 + win): samples [W0, W0 + win].  W0 is monotone
+  // in the tile's origin, so its extremes are at the corner tiles; every
+  // launch shape (4-, 8-, 16- and 32-row tiles) is covered.
+  std::vector<int2> rng(P, make_int2(0, 0));
+  if (!p.vol) {
+    const int tzs[3] = {8, 16, 32};
+    long long wins[3];
+    for (int v = 0; v < 3; ++v) {
+      double sp = 0;  // as configure_kk_gather: span over every pair
+      for (int q = 0; q < P; ++q) sp = std::max(sp, std::fabs(p.h_bfA[q]) * (kTileX - 1) + p.h_bfB[q] * (tzs[v] - 1));
+      wins[v] = (long long)std::ceil(sp) + 4;
+    }
+    const long long x_last = (long long)((g.nx + kTileX - 1) / kTileX - 1) * kTileX;
+    for (int s = 0; s < P; ++s) {
+      long long lo = LLONG_MAX, hi = LLONG_MIN;
+      for (int v = 0; v < 3; ++v) {
+        const long long z_last = (long long)((g.nz + tzs[v] - 1) / tzs[v] - 1) * tzs[v];
+        for (long long x0 : {0LL, x_last})
+          for (long long z0 : {0LL, z_last}) {
+            const long long smin = C[s] + Bv[s] * z0 + A[s] * (A[s] >= 0 ? x0 : x0 + kTileX - 1);
+            const long long w0 = (smin >> 32) - 1;
+            lo = std::min(lo, w0);
+            hi = std::max(hi, w0 + wins[v] + 1);
+          }
+      }
+      lo = std::max(0LL, std::min(lo, (long long)p.T));
+      hi = std::max(lo, std::min(hi, (long long)p.T));
+      rng[row[s]] = make_int2((int)lo, (int)hi);
+      if (hi > lo) p.trim_bytes += 16 * (size_t)((hi + 1) / 2 - lo / 2);  // sample pairs overlapping [lo, hi)
+    }
+  }
+  const size_t off_rng = blob.add(rng);
   const size_t off_row = blob.add(row), off_A = blob.add(A), off_B = blob.add(Bv), off_C = blob.add(C);
   const size_t off_Af = blob.add(Af), off_Bf = blob.add(Bf);
   const size_t off_Y = p.vol ? blob.add(Yv) : 0;
@@ -586,6 +622,7 @@ kk_status make_kk(kk_plan &p, const kk_plan_desc *d) {
   p.t.bf_Bf = at<float>(b, off_Bf);
   p.t.pair_w = d->pair_weight ? at<float>(b, off_W) : nullptr;
   p.t.group_start = at<int32_t>(b, off_gs);
+  p.t.rec_range = at<int2>(b, off_rng);
   p.t.status = at<int>(b, p.status_off);
   return KK_OK;
 }
@@ -862,6 +899,18 @@ kk_status kk_plan_set_gather(kk_plan *p, int32_t rows, int32_t stage) {
   return st;
 }
 
+kk_status kk_plan_set_trim(kk_plan *p, int32_t on) {
+  kk_status st = check_plan(p, false);
+  if (st != KK_OK) return st;
+  if (on != 0 && on != 1) { set_error("trim must be 0 or 1"); return KK_ERR_INVALID_ARG; }
+  if (on && p->vol) {
+    set_error("record trimming is for linear-array plans (volumetric plans keep full records)");
+    return KK_ERR_UNSUPPORTED;
+  }
+  p->trim = on != 0;
+  return KK_OK;
+}
+
 kk_status kk_plan_status(const kk_plan *p, int32_t *status) {
   if (!p || !status) { set_error("null argument"); return KK_ERR_INVALID_ARG; }
   DeviceGuard guard(p->device);
@@ -911,6 +960,8 @@ kk_status kk_plan_get_info(const kk_plan *p, kk_plan_info *info) {
   info->gather_rows = p->bf_rows;
   info->gather_stage = p->bf_stage;
   info->gather_split = p->bf_split;
+  info->records_trimmed = p->trim ? 1 : 0;
+  info->rf_theta_stored_bytes = p->is_das ? 0 : (p->trim ? p->trim_bytes : (size_t)p->P * p->T * 8);
   return KK_OK;
 }
 
