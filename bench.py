@@ -300,6 +300,26 @@ def refiner_conv_flops(batch, H=256, W=256):
     return fwd, 3 * fwd - first
 
 
+def refiner_conv_attainable_ms(batch, hbm_gbs, tflops, H=256, W=256):
+    """(forward, training-step) lower bounds of the convolutions' time: per
+    layer the larger of its HBM time (bf16 NHWC input and output activations,
+    bf16 weights) and its tensor time (2 x 9 cin cout per output pixel), summed
+    over layers.  A training step adds backward-data (all layers but the
+    first: read the output gradient, write the input gradient) and the weight
+    gradient (read the input and the output gradient) of the same FLOPs.
+    Pooling, upsampling, skips and the optimiser are left out, so the bound is
+    low."""
+    bw, pk = hbm_gbs * 1e9, tflops * 1e12
+    fwd = step = 0.0
+    for i, (ci, co, lv) in enumerate(REFINER_LAYERS):
+        px = batch * (H >> lv) * (W >> lv)
+        fl = 2.0 * 9 * ci * co * px
+        t = max((px * (ci + co) * 2 + 9 * ci * co * 2) / bw, fl / pk)
+        fwd += t
+        step += t + t + (t if i > 0 else 0.0)   # forward, weight gradient, backward-data
+    return fwd * 1e3, step * 1e3
+
+
 def _learned(kb, dev, peaks, peak_src, flush, train_frames=512, eval_frames=32, steps=400, batch=16):
     """Learned refiner on 256 x 256 images (6 x 12 vernier KK image in, full
     75 x 128 KK image as target): throughput of inference (network + judge)
@@ -367,6 +387,7 @@ def _learned(kb, dev, peaks, peak_src, flush, train_frames=512, eval_frames=32, 
     peak = float(peaks["bf16_tflops"])
     tf_fwd = fwd_flops / (ms_fwd / 1e3) / 1e12
     tf_step = step_flops / (ms_step / 1e3) / 1e12
+    att_fwd, att_step = refiner_conv_attainable_ms(batch, float(peaks["hbm_gbs"]), peak)
     return {
         "workload": "256 x 256 IQ, 6 x 12 vernier -> 75 x 128 full pair set; 1.58 M parameters",
         "batch": batch, "status": ref.net.status(),
@@ -378,7 +399,12 @@ def _learned(kb, dev, peaks, peak_src, flush, train_frames=512, eval_frames=32, 
                           "peak": peak, "frac_forward": round(tf_fwd / peak, 4),
                           "frac_train_step": round(tf_step / peak, 4),
                           "basis": f"convolution FLOPs (2 x 9 cin cout per pixel) over the whole pass; "
-                                   f"bf16_tflops burst ({peak_src})"},
+                                   f"bf16_tflops burst ({peak_src})",
+                          "per_layer_bound": {
+                              "forward_ms": round(att_fwd, 4), "train_step_ms": round(att_step, 4),
+                              "frac_forward": round(att_fwd / ms_fwd, 4), "frac_train_step": round(att_step / ms_step, 4),
+                              "basis": "sum over layers of max(HBM time of bf16 activations and weights, tensor time) "
+                                       f"at hbm_gbs and bf16_tflops ({peak_src}); the thin 256^2 layers are HBM-bound"}},
         "short_training": {"train_frames": train_frames, "steps": steps, "batch": batch,
                            "loss_first": round(float(losses[:20].mean()), 5),
                            "loss_last": round(float(losses[-20:].mean()), 5),

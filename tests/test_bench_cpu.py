@@ -55,3 +55,18 @@ def test_run_record_of_a_gpu_line(tmp_path):
     bench.append_record(str(tmp_path / "r.jsonl"), bench.run_record({"value": 1.0}, argv=[]))
     lines = (tmp_path / "r.jsonl").read_text().splitlines()
     assert len(lines) == 2 and json.loads(lines[1])["roofline"] is None
+
+
+def test_refiner_per_layer_bound_limits():
+    """The per-layer roofline bound reduces to the FLOP count over the peak
+    when bandwidth is unlimited, and exceeds each single-resource bound
+    otherwise."""
+    sys.path.insert(0, ROOT)
+    import bench
+    fwd_flops, step_flops = bench.refiner_conv_flops(16)
+    f_inf, s_inf = bench.refiner_conv_attainable_ms(16, 1e12, 1000.0)      # effectively unlimited HBM
+    assert abs(f_inf - fwd_flops / 1e15 * 1e3) / f_inf < 1e-6
+    assert abs(s_inf - step_flops / 1e15 * 1e3) / s_inf < 1e-6
+    f, s = bench.refiner_conv_attainable_ms(16, 6697.0, 1910.7)
+    assert f > fwd_flops / 1910.7e12 * 1e3 and s > step_flops / 1910.7e12 * 1e3
+    assert s > 2 * f
