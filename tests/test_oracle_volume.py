@@ -200,3 +200,28 @@ def test_v6_shear_separates_per_axis_on_a_grid():
     Z = np.einsum("iyx,ax->iya", X.reshape(3, ly, lx), Wx)                 # sum over lx
     Y2 = np.einsum("iya,by->iba", Z, Wy).reshape(3, -1)                    # sum over ly
     assert kk.rel_l2(Y2, X @ W.T) <= 1e-13
+
+
+def test_v7_das_volume_focus_and_transposition():
+    """The volumetric DAS oracle: isolated points off both axes focus within
+    one voxel of their positions (a wrong sign or a dropped y term in either
+    delay moves or smears them), and swapping x and y everywhere transposes
+    the volume (pins its y path against its x path)."""
+    tx1 = np.deg2rad(np.linspace(-6, 6, 3))
+    u, v, ax, ay = _small_matrix(10, 8, 0.3e-3, 0.25e-3, tx1, tx1[:2])
+    targets = [(0.9e-3, -0.6e-3, 6.5e-3), (-1.2e-3, 0.9e-3, 7.5e-3)]
+    pts = np.array([[x, y, z, 10.0] for x, y, z in targets])
+    rf = kksynth.simulate_rf3(pts, u, v, ax, ay, 512)
+    d = 0.15e-3
+    grid, gy = (25, 21, -1.8e-3, d, 5.5e-3, d), (21, -1.5e-3, d)
+    B = np.abs(V.das_volume(rf, ax, ay, u, v, grid, gy, FS, C))       # [ny][nz][nx]
+    for x, y, z in targets:
+        ix, iy, iz = round((x + 1.8e-3) / d), round((y + 1.5e-3) / d), round((z - 5.5e-3) / d)
+        win = B[iy - 3:iy + 4, iz - 3:iz + 4, ix - 3:ix + 4]
+        jy, jz, jx = np.unravel_index(np.argmax(win), win.shape)
+        assert max(abs(jy - 3), abs(jz - 3), abs(jx - 3)) <= 1, (jy, jz, jx)
+    # transposition
+    rf_t = kksynth.simulate_rf3(pts[:, [1, 0, 2, 3]], v, u, ay, ax, 512)
+    grid_t, gy_t = (21, 21, -1.5e-3, d, 5.5e-3, d), (25, -1.8e-3, d)
+    Bt = np.abs(V.das_volume(rf_t, ay, ax, v, u, grid_t, gy_t, FS, C))  # [nx][nz][ny]
+    assert kk.rel_l2(np.transpose(Bt, (2, 1, 0)), B) <= 1e-11
