@@ -21,7 +21,7 @@
 
 namespace {
 
-constexpr int kCaptureStreams = 32;
+constexpr int kCaptureStreams = 128;
 constexpr size_t kAlign = 256;
 
 size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
