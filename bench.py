@@ -1068,6 +1068,7 @@ def run_profile(args):
             args.profile, kb.KK_PREC_F32)
         plan = kb.Plan(w.elem_x, w.tx_angles, w.grid, w.c, w.fs, w.n_samples, kb.KK_RF_I16,
                        rx_angles=rx, pairs=pairs, compound=kb.KK_COMPOUND_COHERENT, precision=prec)
+        plan.set_trim(True)  # as the benchmark's plans
         ws, rt, B, I = plan.empty_workspace(), plan.empty_rf_theta(), plan.empty_image(), plan.empty_intensity()
         plan.decompose(d_rf, rt, ws)
         for _ in range(3):
