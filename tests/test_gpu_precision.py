@@ -117,6 +117,44 @@ def test_precision_forms_large_vernier(form):
     assert kc.rel_l2(B, ref) <= bound
 
 
+@pytest.mark.parametrize("form", ["bf16", "f16", "f8e4m3"])
+def test_precision_forms_odd_shapes(form):
+    """Odd element count (37: phases read one by one, a padded last K chunk),
+    int16 records, 9 transmits, a scattered pair subset with a repeated pair
+    (records through the inverse's column table) in two incoherently
+    compounded groups, and a ragged grid: image, intensity and the point
+    peaks against the oracle."""
+    import torch
+    from oracle import schemes
+    prec, bound = FORMS[form]
+    grid = (50, 44, -4e-3, 0.12e-3, 5e-3, 0.14e-3)
+    pts = [(0.5, 6.0), (-1.0, 8.0), (2.0, 9.5)]
+    w = kksynth.workload_custom("odd", 77, 37, 0.25e-3, 9, 12.0, 1024, grid, kksynth.point_phantom(pts),
+                                rf_dtype="i16")
+    rx = np.deg2rad(np.array([-9.0, -2.5, 0.0, 3.0, 11.0]))
+    pairs = np.array([[0, 1], [3, 4], [8, 0], [4, 2], [4, 2], [7, 3], [2, 2], [5, 0], [1, 1], [6, 4]],
+                     dtype=np.int32)
+    grp = np.array([0, 1, 0, 1, 0, 1, 1, 0, 1, 0], dtype=np.int32)
+    ops = schemes.PairSet(w.tx_angles, rx, pairs[:, 0].astype(np.int64), pairs[:, 1].astype(np.int64),
+                          grp.astype(np.int64), 2)
+    plan = _plan(w, rx, pairs, grp, 2, prec, kb.KK_COMPOUND_INCOHERENT)
+    ws, rt, B, I = plan.empty_workspace(), plan.empty_rf_theta(), plan.empty_image(), plan.empty_intensity()
+    plan.decompose(kc.to_dev(w.rf), rt, ws)
+    plan.beamform(rt, B, I, ws)
+    torch.cuda.synchronize()
+    assert plan.status() == kb.KK_OK
+    ref = kk.kk_image(w.rf, w.elem_x, ops, grid, FS, C)
+    Bg = kc.cplx(B)
+    assert kc.rel_l2(Bg, ref) <= bound
+    assert kc.rel_l2(I.cpu().numpy().astype(np.float64), kk.compound(ref, "incoherent")) <= 2 * bound
+    nx, nz, x0, dx, z0, dz = grid
+    A, Ar = np.abs(Bg).sum(0), np.abs(ref).sum(0)
+    for x, z in pts:
+        ix, iz = int(round((x * 1e-3 - x0) / dx)), int(round((z * 1e-3 - z0) / dz))
+        sub, subr = A[iz - 5:iz + 6, ix - 5:ix + 6], Ar[iz - 5:iz + 6, ix - 5:ix + 6]
+        assert np.argmax(sub) == np.argmax(subr), (form, x, z)
+
+
 def test_precision_plan_limits():
     w = kksynth.workload_custom("L160", 3, 160, 0.2e-3, 3, 8.0, 512, (8, 8, -1e-3, 0.2e-3, 5e-3, 0.2e-3),
                                 kksynth.point_phantom([(0.0, 6.0)]))
