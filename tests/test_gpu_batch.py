@@ -139,6 +139,38 @@ def test_batch_with_volumes_matches_per_frame_and_oracle(frames, shape):
         assert kc.rel_l2(kc.cplx(b["B"]), ref) <= 1e-5
 
 
+def test_batch_mixed_precision_forms(frames):
+    """Frames in the BF16, FP16 and FP8 tensor-core forms beside an FP32 one
+    in one graph (the persistent contraction of each form captured as a
+    node): every frame equals its per-frame path, and the oracle within the
+    forms' stated bound."""
+    import torch
+    forms = [kb.KK_PREC_BF16, kb.KK_PREC_F16, kb.KK_PREC_F8E4M3, kb.KK_PREC_F32]
+    made = []
+    for (w, ops, plan0), prec in zip(frames[:4], forms):
+        i0 = plan0.info
+        plan = kb.Plan(w.elem_x, w.tx_angles, w.grid, w.c, w.fs, w.n_samples, kc.rf_dtype_of(w),
+                       rx_angles=ops.rx_angles, pairs=np.stack([ops.tx_index, ops.rx_index], 1).astype(np.int32),
+                       group_of_pair=ops.group.astype(np.int32), n_groups=i0.n_groups,
+                       compound=kb.KK_COMPOUND_INCOHERENT if i0.n_groups > 1 else kb.KK_COMPOUND_COHERENT,
+                       precision=prec)
+        made.append((w, ops, plan, prec))
+    bufs = [_buffers(w, plan) for (w, ops, plan, prec) in made]
+    batch = kb.Batch(bufs, shape=0)
+    batch.run()
+    torch.cuda.synchronize()
+    for (w, ops, plan, prec), b in zip(made, bufs):
+        assert plan.status() == kb.KK_OK
+        plan.set_gather(batch.info.rows, batch.info.stage)
+        ws, rt, B1, I1 = plan.empty_workspace(), plan.empty_rf_theta(), plan.empty_image(), plan.empty_intensity()
+        plan.decompose(b["rf"], rt, ws)
+        plan.beamform(rt, B1, I1, ws)
+        torch.cuda.synchronize()
+        assert kc.rel_l2(kc.cplx(b["B"]), kc.cplx(B1)) <= 1e-6
+        ref = kk.kk_image(w.rf, w.elem_x, ops, w.grid, FS, C)
+        assert kc.rel_l2(kc.cplx(b["B"]), ref) <= (1e-5 if prec == kb.KK_PREC_F32 else 1e-2)
+
+
 def test_batch_rejects_bad_frames(frames):
     w, ops, plan = frames[0]
     b = _buffers(w, plan)
