@@ -121,12 +121,12 @@ __global__ void __launch_bounds__(256) k_shear_f32(const float2 *__restrict__ X,
 // chunk, later bins step W <- W E (one complex product), at most KB - 1
 // steps from an exact value.
 constexpr int kLCn = 32;   // elements per chunk
-constexpr int kKBn = 4;    // bins per CTA
+constexpr int kKBn = 4;    // bins per CTA, at most (fewer when the grid would not fill the GPU)
 
 template <int TN, int AG>
 __global__ void __launch_bounds__(TN * AG, 768 / (TN * AG)) k_shear_f32n(const float2 *__restrict__ X,
                                                     const unsigned long long *__restrict__ phase,
-                                                    int L, int Nu, int Mu, int F,
+                                                    int L, int Nu, int Mu, int F, int kbn,
                                                     float2 *__restrict__ Y) {
   constexpr int NT = TN * AG;    // threads: TN transmits x AG angle groups of 4
   constexpr int TO = 4 * AG;
@@ -134,8 +134,8 @@ __global__ void __launch_bounds__(TN * AG, 768 / (TN * AG)) k_shear_f32n(const f
   float2 (*Ws)[TO] = reinterpret_cast<float2 (*)[TO]>(n_smem);               // [kLCn][TO]
   float2 (*Es)[TO] = reinterpret_cast<float2 (*)[TO]>(n_smem + kLCn * TO);   // [kLCn][TO]
   float2 (*Xs)[TN + 1] = reinterpret_cast<float2 (*)[TN + 1]>(n_smem + 2 * kLCn * TO);
-  const int k0 = blockIdx.x * kKBn;
-  const int nk = min(kKBn, F - k0);
+  const int k0 = blockIdx.x * kbn;
+  const int nk = min(kbn, F - k0);
   const int o0 = blockIdx.y * TO;
   const int i0 = blockIdx.z * TN;
   const int tid = threadIdx.x;
@@ -227,8 +227,14 @@ cudaError_t launch_n(const kk_plan &p, const float2 *X, float2 *Y, cudaStream_t 
   cudaError_t e =
       cudaFuncSetAttribute(k_shear_f32n<TN, AG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  const dim3 grid((p.F + kKBn - 1) / kKBn, (p.Mu + TO - 1) / TO, (p.Nu + TN - 1) / TN);
-  k_shear_f32n<TN, AG><<<grid, TN * AG, smem, s>>>(X, p.t.phase, p.L, p.Nu, p.Mu, p.F, Y);
+  // bins per CTA: kKBn amortises each element chunk's sin/cos over four bins;
+  // a small problem takes one bin per CTA so that its grid spreads over the GPU
+  int sms = 148;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p.device);
+  const long long tiles = (long long)((p.Mu + TO - 1) / TO) * ((p.Nu + TN - 1) / TN);
+  const int kbn = tiles * ((p.F + kKBn - 1) / kKBn) >= (long long)sms ? kKBn : 1;
+  const dim3 grid((p.F + kbn - 1) / kbn, (p.Mu + TO - 1) / TO, (p.Nu + TN - 1) / TN);
+  k_shear_f32n<TN, AG><<<grid, TN * AG, smem, s>>>(X, p.t.phase, p.L, p.Nu, p.Mu, p.F, kbn, Y);
   return cudaGetLastError();
 }
 
