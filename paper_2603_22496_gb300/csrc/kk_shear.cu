@@ -228,11 +228,15 @@ cudaError_t launch_n(const kk_plan &p, const float2 *X, float2 *Y, cudaStream_t 
       cudaFuncSetAttribute(k_shear_f32n<TN, AG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   // bins per CTA: kKBn amortises each element chunk's sin/cos over four bins;
-  // a small problem takes one bin per CTA so that its grid spreads over the GPU
+  // a small problem takes one bin per CTA so that its grid spreads over the
+  // GPU.  The choice depends on the bins and receive angles only, never on
+  // the transmits in use: W of a bin is then formed the same way whatever
+  // transmit subset a call contracts (the streaming decomposition's groups
+  // equal the whole frame bit for bit).
   int sms = 148;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p.device);
-  const long long tiles = (long long)((p.Mu + TO - 1) / TO) * ((p.Nu + TN - 1) / TN);
-  const int kbn = tiles * ((p.F + kKBn - 1) / kKBn) >= (long long)sms ? kKBn : 1;
+  const long long nominal = (long long)((p.F + kKBn - 1) / kKBn) * ((p.Mu + 15) / 16);
+  const int kbn = nominal >= (long long)sms ? kKBn : 1;
   const dim3 grid((p.F + kbn - 1) / kbn, (p.Mu + TO - 1) / TO, (p.Nu + TN - 1) / TN);
   k_shear_f32n<TN, AG><<<grid, TN * AG, smem, s>>>(X, p.t.phase, p.L, p.Nu, p.Mu, p.F, kbn, Y);
   return cudaGetLastError();
