@@ -159,7 +159,8 @@ kk_status capture_graph(kk_batch &b, cudaStream_t s) {
   for (int k = 0; k < kCaptureStreams && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(b.streams[k], b.fork, 0);
   for (size_t f = 0; f < b.frames.size() && e == cudaSuccess && st == KK_OK; ++f) {
     const kk_batch_frame &fr = b.frames[f];
-    st = enqueue_decompose(fr.plan, fr.d_rf, fr.d_rf_theta, fr.d_workspace, b.streams[f % kCaptureStreams]);
+    st = enqueue_decompose(fr.plan, fr.d_rf, fr.d_rf_theta, fr.d_workspace, b.streams[f % kCaptureStreams],
+                           true);
   }
   for (int k = 0; k < kCaptureStreams && e == cudaSuccess; ++k) {
     e = cudaEventRecord(b.join[k], b.streams[k]);

@@ -209,11 +209,14 @@ struct DeviceGuard {
 kk_status check_beamform_args(const kk_plan *p, const void *rf_theta, const void *B, const float *I);
 
 // spectrum -> contraction -> inverse of one frame on stream s (no checks)
-kk_status enqueue_decompose(const kk_plan *p, const void *rf, void *rf_theta, void *ws, cudaStream_t s);
+// side_by_side: the launch shares the GPU with other frames' kernels (the
+// batched form's graph), so the contraction picks its throughput shape
+kk_status enqueue_decompose(const kk_plan *p, const void *rf, void *rf_theta, void *ws, cudaStream_t s,
+                            bool side_by_side = false);
 // KK image formation of one frame on stream s (no checks)
 kk_status enqueue_beamform(const kk_plan *p, const void *rf_theta, void *B, float *I, void *ws, cudaStream_t s);
 // the contraction of the plan's precision form: X [F][p.Nu][L] -> Y [F][p.Nu][Mu]
-cudaError_t launch_shear(const kk_plan &p, const void *X, float2 *Y, cudaStream_t s);
+cudaError_t launch_shear(const kk_plan &p, const void *X, float2 *Y, cudaStream_t s, bool side_by_side = false);
 
 // thread-local error message
 void set_error(const std::string &msg);
@@ -228,7 +231,8 @@ cudaError_t launch_spectrum(const kk_plan &p, const void *rf, void *X, int n_tx_
 cudaError_t launch_inverse(const kk_plan &p, const float2 *Y, int ncol, const int32_t *col_of_row,
                            int nrow, float2 *out, cudaStream_t s, const float *row_w = nullptr,
                            const int32_t *out_row = nullptr);
-cudaError_t launch_shear_f32(const kk_plan &p, const float2 *X, float2 *Y, cudaStream_t s);
+cudaError_t launch_shear_f32(const kk_plan &p, const float2 *X, float2 *Y, cudaStream_t s,
+                             bool side_by_side = false);
 cudaError_t launch_shear_sep(const kk_plan &p, const float2 *X, float2 *Y, cudaStream_t s);
 size_t sep_shear_smem_bytes(int L, int Lf, int Ls, int Mf, int Ms, int msp, int tpc, bool bulk);
 // separable contraction's split of the slow-axis waves over thread parts:

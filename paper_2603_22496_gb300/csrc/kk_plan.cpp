@@ -798,7 +798,8 @@ bool aligned(const void *ptr, size_t a) { return ((uintptr_t)ptr % a) == 0; }
 
 }  // namespace
 
-kk_status enqueue_decompose(const kk_plan *p, const void *rf, void *rf_theta, void *ws, cudaStream_t s) {
+kk_status enqueue_decompose(const kk_plan *p, const void *rf, void *rf_theta, void *ws, cudaStream_t s,
+                            bool side_by_side) {
   NvtxRange range("kk_decompose");
   void *X = at<unsigned char>(ws, p->ws_X);
   float2 *Y = at<float2>(ws, p->ws_Y);
@@ -810,7 +811,7 @@ kk_status enqueue_decompose(const kk_plan *p, const void *rf, void *rf_theta, vo
   if (e != cudaSuccess) return cuda_fail(e, "spectrum launch");
   {
     NvtxRange r("kk_decompose/contraction");
-    e = launch_shear(*p, X, Y, s);
+    e = launch_shear(*p, X, Y, s, side_by_side);
   }
   if (e != cudaSuccess) return cuda_fail(e, "shear launch");
   NvtxRange r("kk_decompose/inverse");
@@ -820,8 +821,8 @@ kk_status enqueue_decompose(const kk_plan *p, const void *rf, void *rf_theta, vo
   return KK_OK;
 }
 
-cudaError_t launch_shear(const kk_plan &p, const void *X, float2 *Y, cudaStream_t s) {
-  return (p.precision == KK_PREC_F32) ? launch_shear_f32(p, (const float2 *)X, Y, s)
+cudaError_t launch_shear(const kk_plan &p, const void *X, float2 *Y, cudaStream_t s, bool side_by_side) {
+  return (p.precision == KK_PREC_F32) ? launch_shear_f32(p, (const float2 *)X, Y, s, side_by_side)
                                       : launch_shear_tc(p, X, Y, s);
 }
 

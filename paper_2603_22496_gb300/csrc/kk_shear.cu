@@ -12,12 +12,15 @@
 // fixed-point phases (k * phi mod 2^64 is exact integer arithmetic), so the
 // contraction reads only X from HBM and writes only Y.
 //
-// Three kernels, chosen by launch_shear_f32:
-//   k_shear_sep   volumetric plans whose elements form a grid and whose receive
-//                 waves form a product of x and y tilts (W factors per axis);
-//   k_shear_f32n  up to 64 transmits in use (tile sized to Nu x Mu, the
-//                 phasor stepped across four bins);
-//   k_shear_f32   everything else.
+// Four kernels, chosen by launch_shear_f32:
+//   k_shear_sep         volumetric plans whose elements form a grid and whose
+//                       receive waves form a product of x and y tilts (W
+//                       factors per axis);
+//   k_shear_f32n        up to 64 transmits in use (tile sized to Nu x Mu, the
+//                       phasor stepped across four bins);
+//   k_shear_f32n_split  the same tile on a problem too small to fill the GPU:
+//                       one bin per CTA, the elements split over slices;
+//   k_shear_f32         everything else.
 #include "kk_internal.h"
 #include "kk_tc.h"
 #include "kk_tma.h"
@@ -122,6 +125,8 @@ __global__ void __launch_bounds__(256) k_shear_f32(const float2 *__restrict__ X,
 // steps from an exact value.
 constexpr int kLCn = 32;   // elements per chunk
 constexpr int kKBn = 4;    // bins per CTA, at most (fewer when the grid would not fill the GPU)
+constexpr int kKBnMinWaves = 8;   // four bins per CTA from this many CTAs per SM on (a lone frame)
+constexpr int kKSn = 4;    // element slices per CTA, at most, in the one-bin form
 
 template <int TN, int AG>
 __global__ void __launch_bounds__(TN * AG, 768 / (TN * AG)) k_shear_f32n(const float2 *__restrict__ X,
@@ -166,7 +171,7 @@ __global__ void __launch_bounds__(TN * AG, 768 / (TN * AG)) k_shear_f32n(const f
       if (o < Mu && l < L) {
         const unsigned long long ph = __ldg(phase + (size_t)o * L + l);
         w = phasor(ph * kk64);
-        r = phasor(ph);
+        if (kbn > 1) r = phasor(ph);
       }
       Ws[ll][oo] = w;
       Es[ll][oo] = r;
@@ -220,23 +225,126 @@ __global__ void __launch_bounds__(TN * AG, 768 / (TN * AG)) k_shear_f32n(const f
   }
 }
 
+// One bin per CTA with the elements split over KS slices of TN x AG
+// threads (KS = 2 .. 4): a problem too small to give every SM a few CTAs of
+// the form above (the 8 x 16 vernier frame: 1024 bins x one angle tile of 32
+// threads) spreads its sin/cos and products over KS times the warps.  Slice
+// s takes the element chunks s, s + KS, ... with its own W and X tiles and a
+// named barrier of its own; the partial sums are added in slice order.
 template <int TN, int AG>
-cudaError_t launch_n(const kk_plan &p, const float2 *X, float2 *Y, cudaStream_t s) {
+__global__ void __launch_bounds__(4 * TN * AG) k_shear_f32n_split(const float2 *__restrict__ X,
+                                                             const unsigned long long *__restrict__ phase,
+                                                             int L, int Nu, int Mu, int ks,
+                                                             float2 *__restrict__ Y) {
+  constexpr int NS = TN * AG;    // threads per slice
+  constexpr int TO = 4 * AG;
+  constexpr int SL = kLCn * TO + kLCn * (TN + 1);   // float2 per slice
+  extern __shared__ __align__(16) float2 n_smem[];
+  const int s = threadIdx.x / NS, t = threadIdx.x - s * NS;
+  float2 (*Ws)[TO] = reinterpret_cast<float2 (*)[TO]>(n_smem + s * SL);
+  float2 (*Xs)[TN + 1] = reinterpret_cast<float2 (*)[TN + 1]>(n_smem + s * SL + kLCn * TO);
+  const int k = blockIdx.x;
+  const int o0 = blockIdx.y * TO;
+  const int i0 = blockIdx.z * TN;
+  const int ty = t % TN, tx = t / TN;
+  const unsigned long long kk64 = (unsigned long long)k;
+  const float2 *Xk = X + (size_t)k * Nu * L;
+  auto slice_sync = [&]() { asm volatile("bar.sync %0, %1;" ::"r"(s + 1), "r"(NS) : "memory"); };
+
+  float2 acc[4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a) acc[a] = make_float2(0.f, 0.f);
+  for (int l0 = s * kLCn; l0 < L; l0 += ks * kLCn) {
+    for (int e = t; e < kLCn * TO; e += NS) {
+      const int ll = e / TO, oo = e - ll * TO;
+      const int o = o0 + oo, l = l0 + ll;
+      float2 w = make_float2(0.f, 0.f);
+      if (o < Mu && l < L) {
+        const int hi = (int)((__ldg(phase + (size_t)o * L + l) * kk64) >> 32);
+        sincospif((float)hi * 0x1p-31f, &w.y, &w.x);
+      }
+      Ws[ll][oo] = w;
+    }
+    for (int e = t; e < kLCn * TN; e += NS) {
+      const int ii = e / kLCn, ll = e - ii * kLCn;
+      const int i = i0 + ii, l = l0 + ll;
+      Xs[ll][ii] = (i < Nu && l < L) ? Xk[(size_t)i * L + l] : make_float2(0.f, 0.f);
+    }
+    slice_sync();
+    const int lmax = min(kLCn, L - l0);
+    for (int ll = 0; ll < lmax; ++ll) {
+      const float4 w01 = *reinterpret_cast<const float4 *>(&Ws[ll][tx * 4]);
+      const float4 w23 = *reinterpret_cast<const float4 *>(&Ws[ll][tx * 4 + 2]);
+      const float2 w[4] = {make_float2(w01.x, w01.y), make_float2(w01.z, w01.w),
+                           make_float2(w23.x, w23.y), make_float2(w23.z, w23.w)};
+      const float2 x = Xs[ll][ty];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        acc[a].x = fmaf(w[a].x, x.x, acc[a].x);
+        acc[a].x = fmaf(-w[a].y, x.y, acc[a].x);
+        acc[a].y = fmaf(w[a].x, x.y, acc[a].y);
+        acc[a].y = fmaf(w[a].y, x.x, acc[a].y);
+      }
+    }
+    slice_sync();
+  }
+  __syncthreads();   // every slice is done with its tiles: reuse them for the partial sums
+  float2 *part = n_smem;   // [ks - 1][NS][4]
+  if (s > 0) {
+#pragma unroll
+    for (int a = 0; a < 4; ++a) part[((size_t)(s - 1) * NS + t) * 4 + a] = acc[a];
+  }
+  __syncthreads();
+  if (s > 0) return;
+  for (int r = 1; r < ks; ++r)
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      const float2 q = part[((size_t)(r - 1) * NS + t) * 4 + a];
+      acc[a].x += q.x;
+      acc[a].y += q.y;
+    }
+  const int i = i0 + ty;
+  if (i >= Nu) return;
+  float2 *Yk = Y + ((size_t)k * Nu + i) * Mu;
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const int o = o0 + tx * 4 + a;
+    if (o < Mu) Yk[o] = acc[a];
+  }
+}
+
+template <int TN, int AG>
+cudaError_t launch_n(const kk_plan &p, const float2 *X, float2 *Y, cudaStream_t s, bool side_by_side) {
   constexpr int TO = 4 * AG;
   const size_t smem = sizeof(float2) * (2 * (size_t)kLCn * TO + (size_t)kLCn * (TN + 1));
   cudaError_t e =
       cudaFuncSetAttribute(k_shear_f32n<TN, AG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  // bins per CTA: kKBn amortises each element chunk's sin/cos over four bins;
-  // a small problem takes one bin per CTA so that its grid spreads over the
-  // GPU.  The choice depends on the bins and receive angles only, never on
-  // the transmits in use: W of a bin is then formed the same way whatever
-  // transmit subset a call contracts (the streaming decomposition's groups
-  // equal the whole frame bit for bit).
+  // bins per CTA: kKBn amortises each element chunk's sin/cos over four
+  // bins, which pays where throughput counts: in the batched form, whose
+  // frames' kernels share the GPU, from one four-bin CTA per SM, and for a
+  // lone frame from kKBnMinWaves per SM.  A smaller lone frame is latency
+  // bound: it takes one bin per CTA with the elements split over up to kKSn
+  // slices, so that its sin/cos and products spread over more warps.  Both
+  // choices depend on the bins, receive angles and elements only, never on
+  // the transmits in use: W of a bin is then formed and summed the same way
+  // whatever transmit subset a call contracts (the streaming decomposition's
+  // groups equal the whole frame bit for bit).
   int sms = 148;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p.device);
   const long long nominal = (long long)((p.F + kKBn - 1) / kKBn) * ((p.Mu + 15) / 16);
-  const int kbn = nominal >= (long long)sms ? kKBn : 1;
+  const int kbn = nominal >= (long long)(side_by_side ? 1 : kKBnMinWaves) * sms ? kKBn : 1;
+  const int ks = kbn == 1 ? std::min(kKSn, (p.L + kLCn - 1) / kLCn) : 1;
+  if (ks > 1) {
+    constexpr size_t sl = sizeof(float2) * ((size_t)kLCn * TO + (size_t)kLCn * (TN + 1));
+    const size_t smem_s = std::max(sl * ks, sizeof(float2) * 4 * TN * AG * (ks - 1));
+    e = cudaFuncSetAttribute(k_shear_f32n_split<TN, AG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem_s);
+    if (e != cudaSuccess) return e;
+    const dim3 grid_s(p.F, (p.Mu + TO - 1) / TO, (p.Nu + TN - 1) / TN);
+    k_shear_f32n_split<TN, AG><<<grid_s, TN * AG * ks, smem_s, s>>>(X, p.t.phase, p.L, p.Nu, p.Mu, ks, Y);
+    return cudaGetLastError();
+  }
   const dim3 grid((p.F + kbn - 1) / kbn, (p.Mu + TO - 1) / TO, (p.Nu + TN - 1) / TN);
   k_shear_f32n<TN, AG><<<grid, TN * AG, smem, s>>>(X, p.t.phase, p.L, p.Nu, p.Mu, p.F, kbn, Y);
   return cudaGetLastError();
@@ -477,7 +585,7 @@ cudaError_t launch_shear_sep(const kk_plan &p, const float2 *X, float2 *Y, cudaS
   return cudaGetLastError();
 }
 
-cudaError_t launch_shear_f32(const kk_plan &p, const float2 *X, float2 *Y, cudaStream_t s) {
+cudaError_t launch_shear_f32(const kk_plan &p, const float2 *X, float2 *Y, cudaStream_t s, bool side_by_side) {
   if (p.sep_Lx > 0) return launch_shear_sep(p, X, Y, s);
   if (p.Nu <= 64) {
     // the tile (TN transmits x AG groups of 4 angles, 32 .. 256 threads)
@@ -496,21 +604,21 @@ cudaError_t launch_shear_f32(const kk_plan &p, const float2 *X, float2 *Y, cudaS
         }
       }
     switch (bt * 100 + ba) {
-      case 804: return launch_n<8, 4>(p, X, Y, s);
-      case 808: return launch_n<8, 8>(p, X, Y, s);
-      case 816: return launch_n<8, 16>(p, X, Y, s);
-      case 832: return launch_n<8, 32>(p, X, Y, s);
-      case 1602: return launch_n<16, 2>(p, X, Y, s);
-      case 1604: return launch_n<16, 4>(p, X, Y, s);
-      case 1608: return launch_n<16, 8>(p, X, Y, s);
-      case 1616: return launch_n<16, 16>(p, X, Y, s);
-      case 3201: return launch_n<32, 1>(p, X, Y, s);
-      case 3202: return launch_n<32, 2>(p, X, Y, s);
-      case 3204: return launch_n<32, 4>(p, X, Y, s);
-      case 3208: return launch_n<32, 8>(p, X, Y, s);
-      case 6401: return launch_n<64, 1>(p, X, Y, s);
-      case 6402: return launch_n<64, 2>(p, X, Y, s);
-      default: return launch_n<64, 4>(p, X, Y, s);
+      case 804: return launch_n<8, 4>(p, X, Y, s, side_by_side);
+      case 808: return launch_n<8, 8>(p, X, Y, s, side_by_side);
+      case 816: return launch_n<8, 16>(p, X, Y, s, side_by_side);
+      case 832: return launch_n<8, 32>(p, X, Y, s, side_by_side);
+      case 1602: return launch_n<16, 2>(p, X, Y, s, side_by_side);
+      case 1604: return launch_n<16, 4>(p, X, Y, s, side_by_side);
+      case 1608: return launch_n<16, 8>(p, X, Y, s, side_by_side);
+      case 1616: return launch_n<16, 16>(p, X, Y, s, side_by_side);
+      case 3201: return launch_n<32, 1>(p, X, Y, s, side_by_side);
+      case 3202: return launch_n<32, 2>(p, X, Y, s, side_by_side);
+      case 3204: return launch_n<32, 4>(p, X, Y, s, side_by_side);
+      case 3208: return launch_n<32, 8>(p, X, Y, s, side_by_side);
+      case 6401: return launch_n<64, 1>(p, X, Y, s, side_by_side);
+      case 6402: return launch_n<64, 2>(p, X, Y, s, side_by_side);
+      default: return launch_n<64, 4>(p, X, Y, s, side_by_side);
     }
   }
   const int ri = (p.Nu + 15) / 16;

@@ -80,13 +80,15 @@ def test_stage_shear_matches_oracle():
     assert kc.rel_l2(kc.cplx(Y), ref) <= 2e-6
 
 
-@pytest.mark.parametrize("n_tx,M", [(5, 150), (11, 70), (24, 20), (40, 10)])
+@pytest.mark.parametrize("n_tx,M", [(5, 150), (11, 70), (24, 20), (40, 10), (12, 96), (33, 80)])
 def test_stage_shear_few_transmits_matches_oracle(n_tx, M, request):
-    """The few-transmit contraction (8 .. 64 transmits per CTA, four bins per
-    CTA with the phasor stepped bin to bin) on transmit subsets: two angle
-    tiles (5 x 150, 11 x 70), the 32- and 64-transmit tiles (24 x 20 and
-    40 x 10 on the 128-element, T = 2048 frame), against an FP64 einsum of
-    the same FP32 spectra."""
+    """The few-transmit contraction (8 .. 64 transmits per CTA) on transmit
+    subsets, against an FP64 einsum of the same FP32 spectra: one bin per CTA
+    with the elements split over slices, on two angle tiles (5 x 150,
+    11 x 70) and the 32- and 64-transmit tiles (24 x 20 and 40 x 10 on the
+    128-element, T = 2048 frame); four bins per CTA with the phasor stepped
+    bin to bin, the form of a lone frame with eight four-bin CTAs per SM
+    (12 x 96 and 33 x 80 on that frame)."""
     import torch
     w = kksynth.workload_small() if n_tx <= 11 else request.getfixturevalue("large")
     sub = np.arange(n_tx)
@@ -105,6 +107,40 @@ def test_stage_shear_few_transmits_matches_oracle(n_tx, M, request):
     W = np.exp(2j * np.pi * k[None, None, :] * (FS * d)[:, :, None] / w.n_samples)
     ref = np.einsum("ilk,olk->kio", Xf.transpose(1, 2, 0).astype(np.complex128), W)
     assert kc.rel_l2(kc.cplx(Y), ref) <= 2e-6
+
+
+@pytest.mark.parametrize("n_elem,n_tx,M", [(20, 9, 16), (64, 11, 11), (77, 9, 5), (128, 8, 16)])
+def test_stage_shear_element_slices_matches_oracle(n_elem, n_tx, M):
+    """The one-bin few-transmit contraction on 256-bin frames: the elements in
+    one chunk (20) or split over two, three (77, the last chunk ragged) and
+    four slices per CTA (128), against an FP64 einsum of the same FP32
+    spectra; the first three transmits contracted alone equal their rows of
+    the whole contraction bit for bit."""
+    import torch
+    grid = (32, 32, -3e-3, 0.2e-3, 5e-3, 0.2e-3)
+    ph = kksynth.point_phantom([(0.0, 8.0), (1.5, 12.0), (-2.0, 16.0)])
+    w = kksynth.workload_custom("slices", 31 + n_elem, n_elem, 0.3e-3, n_tx, 8.0, 512, grid, ph, snr_db=30.0)
+    rxa = schemes.even_receive_set(np.deg2rad(10.0), M)
+    Xo = kk.analytic_spectrum(np.asarray(w.rf, dtype=np.float64))       # [N][L][F]
+    Xf = np.transpose(Xo, (2, 0, 1)).astype(np.complex64)             # [F][N][L]
+    F = w.n_samples // 2
+    out = []
+    for n in (n_tx, 3):
+        rx, pairs, grp = kc.product_pairs(np.arange(n), [rxa])
+        plan = kc.kk_plan_for(w, rx, pairs, grp, 1)
+        assert plan.info.n_tx_used == n and plan.info.n_rx_used == M and plan.info.n_bins == F
+        Xn = np.ascontiguousarray(Xf[:, :n])
+        X = torch.from_numpy(np.ascontiguousarray(np.stack([Xn.real, Xn.imag], -1))).cuda()
+        Y = torch.full((F, n, M, 2), float("nan"), device="cuda:0")
+        plan.shear(X, Y)
+        torch.cuda.synchronize()
+        out.append(Y.cpu())
+    d = kk.shear_delays(w.elem_x, rxa, C)
+    k = np.arange(F)
+    W = np.exp(2j * np.pi * k[None, None, :] * (FS * d)[:, :, None] / w.n_samples)
+    ref = np.einsum("ilk,olk->kio", Xf.transpose(1, 2, 0).astype(np.complex128), W)
+    assert kc.rel_l2(kc.cplx(out[0]), ref) <= 2e-6
+    assert torch.equal(out[1], out[0][:, :3])
 
 
 def test_stage_inverse_matches_oracle():
