@@ -125,7 +125,7 @@ __global__ void __launch_bounds__(256) k_shear_f32(const float2 *__restrict__ X,
 // steps from an exact value.
 constexpr int kLCn = 32;   // elements per chunk
 constexpr int kKBn = 4;    // bins per CTA, at most (fewer when the grid would not fill the GPU)
-constexpr int kKBnMinWaves = 8;   // four bins per CTA from this many CTAs per SM on (a lone frame)
+constexpr int kKBnMinPerSM = 8;   // four bins per CTA from this many CTAs per SM on (a lone frame)
 constexpr int kKSn = 4;    // element slices per CTA, at most, in the one-bin form
 
 template <int TN, int AG>
@@ -229,8 +229,9 @@ __global__ void __launch_bounds__(TN * AG, 768 / (TN * AG)) k_shear_f32n(const f
 // threads (KS = 2 .. 4): a problem too small to give every SM a few CTAs of
 // the form above (the 8 x 16 vernier frame: 1024 bins x one angle tile of 32
 // threads) spreads its sin/cos and products over KS times the warps.  Slice
-// s takes the element chunks s, s + KS, ... with its own W and X tiles and a
-// named barrier of its own; the partial sums are added in slice order.
+// s takes the element chunks s, s + KS, ... with its own W and X tiles; the
+// slices step together between CTA barriers (named barriers per slice would
+// hold the SM to four CTAs), and the partial sums are added in slice order.
 template <int TN, int AG>
 __global__ void __launch_bounds__(4 * TN * AG) k_shear_f32n_split(const float2 *__restrict__ X,
                                                              const unsigned long long *__restrict__ phase,
@@ -249,12 +250,12 @@ __global__ void __launch_bounds__(4 * TN * AG) k_shear_f32n_split(const float2 *
   const int ty = t % TN, tx = t / TN;
   const unsigned long long kk64 = (unsigned long long)k;
   const float2 *Xk = X + (size_t)k * Nu * L;
-  auto slice_sync = [&]() { asm volatile("bar.sync %0, %1;" ::"r"(s + 1), "r"(NS) : "memory"); };
 
   float2 acc[4];
 #pragma unroll
   for (int a = 0; a < 4; ++a) acc[a] = make_float2(0.f, 0.f);
-  for (int l0 = s * kLCn; l0 < L; l0 += ks * kLCn) {
+  for (int c0 = 0; c0 * kLCn < L; c0 += ks) {
+    const int l0 = (c0 + s) * kLCn;   // this slice's chunk (none past the last)
     for (int e = t; e < kLCn * TO; e += NS) {
       const int ll = e / TO, oo = e - ll * TO;
       const int o = o0 + oo, l = l0 + ll;
@@ -270,7 +271,7 @@ __global__ void __launch_bounds__(4 * TN * AG) k_shear_f32n_split(const float2 *
       const int i = i0 + ii, l = l0 + ll;
       Xs[ll][ii] = (i < Nu && l < L) ? Xk[(size_t)i * L + l] : make_float2(0.f, 0.f);
     }
-    slice_sync();
+    __syncthreads();
     const int lmax = min(kLCn, L - l0);
     for (int ll = 0; ll < lmax; ++ll) {
       const float4 w01 = *reinterpret_cast<const float4 *>(&Ws[ll][tx * 4]);
@@ -286,9 +287,8 @@ __global__ void __launch_bounds__(4 * TN * AG) k_shear_f32n_split(const float2 *
         acc[a].y = fmaf(w[a].y, x.x, acc[a].y);
       }
     }
-    slice_sync();
-  }
-  __syncthreads();   // every slice is done with its tiles: reuse them for the partial sums
+    __syncthreads();
+  }   // every slice is done with its tiles: they now hold the partial sums
   float2 *part = n_smem;   // [ks - 1][NS][4]
   if (s > 0) {
 #pragma unroll
@@ -323,7 +323,7 @@ cudaError_t launch_n(const kk_plan &p, const float2 *X, float2 *Y, cudaStream_t 
   // bins per CTA: kKBn amortises each element chunk's sin/cos over four
   // bins, which pays where throughput counts: in the batched form, whose
   // frames' kernels share the GPU, from one four-bin CTA per SM, and for a
-  // lone frame from kKBnMinWaves per SM.  A smaller lone frame is latency
+  // lone frame from kKBnMinPerSM per SM.  A smaller lone frame is latency
   // bound: it takes one bin per CTA with the elements split over up to kKSn
   // slices, so that its sin/cos and products spread over more warps.  Both
   // choices depend on the bins, receive angles and elements only, never on
@@ -333,13 +333,18 @@ cudaError_t launch_n(const kk_plan &p, const float2 *X, float2 *Y, cudaStream_t 
   int sms = 148;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p.device);
   const long long nominal = (long long)((p.F + kKBn - 1) / kKBn) * ((p.Mu + 15) / 16);
-  const int kbn = nominal >= (long long)(side_by_side ? 1 : kKBnMinWaves) * sms ? kKBn : 1;
+  const int kbn = nominal >= (long long)(side_by_side ? 1 : kKBnMinPerSM) * sms ? kKBn : 1;
   const int ks = kbn == 1 ? std::min(kKSn, (p.L + kLCn - 1) / kLCn) : 1;
   if (ks > 1) {
     constexpr size_t sl = sizeof(float2) * ((size_t)kLCn * TO + (size_t)kLCn * (TN + 1));
     const size_t smem_s = std::max(sl * ks, sizeof(float2) * 4 * TN * AG * (ks - 1));
     e = cudaFuncSetAttribute(k_shear_f32n_split<TN, AG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem_s);
+    // all of the SM's shared memory for CTAs (the vernier frame's 1024 CTAs
+    // of 26 KB then fit in one wave, eight per SM)
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_shear_f32n_split<TN, AG>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                               (int)cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return e;
     const dim3 grid_s(p.F, (p.Mu + TO - 1) / TO, (p.Nu + TN - 1) / TN);
     k_shear_f32n_split<TN, AG><<<grid_s, TN * AG * ks, smem_s, s>>>(X, p.t.phase, p.L, p.Nu, p.Mu, ks, Y);
