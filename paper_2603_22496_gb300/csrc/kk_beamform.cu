@@ -433,8 +433,8 @@ __global__ void k_kk_reduce(const float2 *__restrict__ part, int split, int J, i
 template <int ROWS, int STAGE, int NPT>
 cudaError_t launch_cfg(const kk_plan &p, const float2 *rf_theta, float2 *dst, float *I,
                        cudaStream_t s) {
-  // registers held to 64 for ROWS <= 4 (8 CTAs of 128 threads per SM) and
-  // to 102 for ROWS = 8 (5 CTAs)
+  // registers held to 72 for ROWS <= 4 (7 CTAs of 128 threads per SM; 8
+  // CTAs at 64 registers spill) and to 102 for ROWS = 8 (5 CTAs)
   constexpr int MB = ROWS <= 4 ? 7 : 5;
   const size_t smem = sizeof(float4) * (size_t)STAGE * p.bf_win;
   const dim3 grid(p.tiles_x * p.tiles_z * p.ny, p.bf_split);
